@@ -1,0 +1,111 @@
+"""Planted mistakes in a copy of the oracle must be caught by the pins.
+
+Each case rewrites one line of the oracle's source (a dropped term, a wrong
+sign, index or factor), loads the result as a separate module on the CPU and
+runs the same kinds of checks the pin tests use.  A mutation that passes all
+checks would mean the pins leave that part of the oracle unchecked.
+"""
+import importlib.util
+import math
+import os
+import types
+
+import numpy as np
+import numpy.polynomial.chebyshev as C
+import pytest
+
+from paper_1105_5481_gb300 import inputs as I
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "kpm_oracle.py")
+
+MUTATIONS = {
+    "doubling_drops_mu0": ("- mu0\n", "\n"),
+    "doubling_wrong_vector": ("np.conj(nxt) * cur", "np.conj(nxt) * prev"),
+    "doubling_factor_two": ("out[:, 2 * n] = 2.0 *", "out[:, 2 * n] = 1.0 *"),
+    "direct_wrong_recursion": ("nxt = 2.0 * _rescaled_apply(H, a, b, cur) - prev\n            out",
+                               "nxt = 2.0 * _rescaled_apply(H, a, b, cur) + prev\n            out"),
+    "reverse_bond_not_conjugated": ("vals += [-h_k, -np.conj(h_k)]", "vals += [-h_k, -h_k]"),
+    "hopping_sign": ("vals += [-h_k, -np.conj(h_k)]", "vals += [h_k, np.conj(h_k)]"),
+    "rescale_shift_sign": ("return (H.matvec(X) - b * X) / a", "return (H.matvec(X) + b * X) / a"),
+    "rescale_no_padding": ("return (emax - emin) / (2.0 - eps)", "return (emax - emin) / 2.0"),
+    "jackson_off_by_one": ("((M - n + 1) * np.cos", "((M - n) * np.cos"),
+    "dos_missing_two": ("s += 2.0 * g[n]", "s += g[n]"),
+    "dos_missing_jacobian": ("return a * x + b, f / a", "return a * x + b, f"),
+    "dos_wrong_node": ("(np.arange(K) + 0.5) / K", "(np.arange(K) + 1.0) / K"),
+    "exact_missing_norm": (".mean(axis=1)", ".sum(axis=1)"),
+    "gershgorin_no_abs": ("np.abs(H.val[~on])", "H.val[~on].real"),
+    "lanczos_no_residual": ("emax = theta[-1] + bk * abs(S[m - 1, -1])", "emax = theta[-1]"),
+    "wrap_missing": ("xn = xn % L[d]", "xn = xn"),
+}
+
+
+def load_mutant(name):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, name
+    mod = types.ModuleType("oracle_mutant_" + name)
+    exec(compile(src.replace(old, new, 1), SRC, "exec"), mod.__dict__)
+    return mod
+
+
+def checks(O):
+    """Pin-style checks; returns the list of failures."""
+    fails = []
+
+    def check(label, ok):
+        if not ok:
+            fails.append(label)
+
+    def plane(L):
+        g = np.meshgrid(*[np.cos(2 * np.pi * np.arange(l) / l) for l in L], indexing="ij")
+        return np.sort((-2.0 * sum(g)).ravel())
+
+    try:
+        for L in [(7,), (3, 4, 5)]:
+            H = O.lattice_hamiltonian(L)
+            check("plane", np.allclose(np.linalg.eigvalsh(O.dense(H)), plane(L), atol=1e-12))
+        w = I.workload("cubic_spin_L4")
+        H = O.lattice_hamiltonian(w["L"], hop=w["hop"], onsite=I.onsite_disorder(1, 64, 1.0))
+        A = O.dense(H)
+        check("hermitian", np.abs(A - A.conj().T).max() == 0)
+        lam = np.linalg.eigvalsh(A)
+        gmin, gmax = O.gershgorin(H)
+        check("gersh", gmin <= lam[0] and lam[-1] <= gmax)
+        emin, emax, _ = O.lanczos_bounds(H, 12, I.lanczos_start(6, 64))
+        check("lanczos", emin <= lam[0] + 1e-9 and lam[-1] - 1e-9 <= emax)
+        a, b = O.rescale(gmin, gmax, 0.01)
+        check("rescale", abs(a - (gmax - gmin) / 1.99) < 1e-15)
+        x = (lam - b) / a
+        ex = O.exact_moments(H, a, b, 24)
+        check("exact", np.allclose(ex, [C.chebval(x, np.eye(n + 1)[n]).mean() for n in range(24)], atol=1e-12))
+        v0 = math.sqrt(64) * np.eye(64)
+        for f in (O.moments_direct, O.moments_doubling):
+            mu, _ = f(H, a, b, v0, 24)
+            check("fullbasis", np.allclose(mu, ex, atol=1e-12))
+        M, K = 20, 40
+        g = O.jackson_kernel(M)
+        av = np.sin(np.pi * (np.arange(M) + 1) / (M + 1))
+        av /= np.linalg.norm(av)
+        check("jackson", np.allclose(g, [np.dot(av[: M - n], av[n:]) for n in range(M)], atol=1e-14))
+        mu = np.linspace(1, -0.5, M)
+        E, rho = O.dos(mu, 2.0, 0.1, K)
+        xk = np.cos(np.pi * (np.arange(K) + 0.5) / K)
+        c = 2 * g * mu
+        c[0] = g[0] * mu[0]
+        check("dos", np.allclose(E, 2.0 * xk + 0.1) and
+              np.allclose(rho, C.chebval(xk, c) / (np.pi * np.sqrt(1 - xk * xk)) / 2.0, rtol=1e-12))
+    except Exception as e:  # a mutant that crashes is caught too
+        fails.append("exception:" + type(e).__name__)
+    return fails
+
+
+def test_unmutated_oracle_passes_checks():
+    spec = importlib.util.spec_from_file_location("oracle_copy", SRC)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    assert checks(mod) == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name):
+    assert checks(load_mutant(name)), f"mutation {name} passed every pin check"
