@@ -1,0 +1,197 @@
+/*
+ * kpm.h - C ABI of the GB300-native kernel polynomial method (KPM) library.
+ *
+ * The library computes the density of states (DOS) of a sparse Hermitian
+ * lattice Hamiltonian H with the kernel polynomial method of Zhang, Yamagiwa,
+ * Okumura and Yunoki, "Performance Acceleration of Kernel Polynomial Method
+ * Applying Graphics Processing Units" (arXiv:1105.5481), Sec. II-A:
+ *
+ *   H~ = (H - b) / a                                   Eq. (tilde)
+ *   v_0 = r,  v_1 = H~ v_0,  v_{n+1} = 2 H~ v_n - v_{n-1}   Eq. (rn)
+ *   mu_n ~ << (1/(N R)) sum_r <r|T_n(H~)|r> >>          Eq. (munr), stochastic trace
+ *   f(x) = [g_0 mu_0 + 2 sum_{n=1}^{M-1} g_n mu_n T_n(x)] / (pi sqrt(1-x^2))   Eq. (fKPM)
+ *
+ * with the moments gathered two per matrix product by the doubling identities
+ * mu_{2n} = 2<v_n|v_n> - mu_0 and mu_{2n+1} = 2<v_{n+1}|v_n> - mu_1 and the
+ * Jackson kernel g_n (the paper names both through its KPM reference).
+ *
+ * Notation: N = matrix dimension (the paper's D or H_SIZE), M = number of
+ * moments (the paper's N), R = random vectors per realisation, S = number of
+ * realisations (Sec. II-A-4).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a kpm_status; nothing aborts.  On failure the calling
+ *    thread's message is available from kpm_last_error().
+ *  - Host input arrays are copied; the caller keeps ownership.  Output arrays
+ *    are caller-owned and may be host or device pointers (the library tells
+ *    them apart with cudaPointerGetAttributes).
+ *  - Device memory for the Hamiltonian and the vector blocks is owned by the
+ *    handle and released by kpm_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls that write host outputs synchronise that stream before returning;
+ *    calls whose outputs are all device pointers are asynchronous.
+ *  - All compute runs in the library's CUDA kernels on the device that was
+ *    current when the handle was created; there is no CPU fallback.  A call on
+ *    a machine without a usable CUDA device returns KPM_ECUDA.
+ */
+#ifndef KPM_H
+#define KPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kpm_handle_s* kpm_handle;
+
+typedef enum {
+  KPM_OK = 0,
+  KPM_EINVAL = 1,    /* invalid argument (sizes, pointers, CSR structure, M odd ...) */
+  KPM_ENOMEM = 2,    /* device allocation failed or budget exceeded */
+  KPM_ECUDA = 3,     /* CUDA runtime error (message in kpm_last_error) */
+  KPM_ETIMEOUT = 4,  /* a bounded device wait gave up */
+  KPM_EDIVERGE = 5,  /* some |mu_n^r| > 1 + 1e-6 or non-finite: bounds do not
+                        enclose the spectrum.  Outputs are still written. */
+  KPM_EBUSY = 6,
+  KPM_ENOTREADY = 7
+} kpm_status;
+
+typedef enum { KPM_REAL = 0, KPM_COMPLEX = 1 } kpm_field;
+
+typedef enum {
+  KPM_FP64 = 0,               /* vectors, products and moment sums in FP64 */
+  KPM_FP32_VEC_FP64_MOM = 1   /* vectors stored/streamed and products in FP32;
+                                 moment dot products summed in FP64 from short
+                                 FP32 partial sums; bounds and DOS in FP64 */
+} kpm_precision;
+
+typedef enum { KPM_KERNEL_JACKSON = 0, KPM_KERNEL_NONE = 1 } kpm_kernel;
+
+/*
+ * Lattice stencil description (matrix-free Hamiltonian; the paper's
+ * evaluation lattice, Sec. IV-A, is dims=3, L={10,10,10}, periodic, t=1).
+ *
+ * Sites are numbered i = x0 + L[0]*(x1 + L[1]*x2).  Direction d joins site i
+ * to its forward neighbour x_d+1 (wrapping when periodic[d] != 0, no bond at
+ * the open edge otherwise).  The matrix is
+ *     H_ii = onsite[i],   H_{i,i+e_d} += -t_{i,d},   H_{i+e_d,i} += -conj(t_{i,d}),
+ * repeated pairs adding up (L[d] = 1 or 2 with wrap).
+ *   onsite     [N] FP64, NULL => 0.
+ *   hop        forward-bond hoppings t_{i,d}, layout [N][dims] (real field) or
+ *              [N][dims][2] (re, im) (complex field); NULL => uniform t.
+ *   t_re, t_im uniform hopping used when hop == NULL (t_im must be 0 for the
+ *              real field).
+ *   bond_mask  [N][dims] bytes, NULL => all bonds kept; 0 removes the bond.
+ */
+typedef struct {
+  int dims;            /* 1, 2 or 3 */
+  int64_t L[3];        /* extents, L[d] >= 1; entries beyond dims are ignored */
+  int periodic[3];     /* per-dimension wrap flag */
+  const double* onsite;
+  const double* hop;
+  double t_re, t_im;
+  const uint8_t* bond_mask;
+} kpm_stencil_desc;
+
+/* Builds a matrix-free stencil Hamiltonian (Sec. IV-A lattice model) on the
+ * current device.  Host arrays are copied.  N = prod L[d] must be < 2^31.
+ * Returns KPM_EINVAL for dims outside 1..3, L[d] < 1, a complex t with the
+ * real field, or N too large. */
+kpm_status kpm_create_stencil(const kpm_stencil_desc* desc, kpm_field field, kpm_handle* out);
+
+/* Builds a CSR Hamiltonian (the paper's CRS format, Sec. II-A-4) from host
+ * arrays: rowptr[n+1] (rowptr[0] = 0, non-decreasing, rowptr[n] = nnz),
+ * col[nnz] in [0, n), val[nnz] FP64 (real field) or [nnz][2] (re, im)
+ * (complex field).  H must be Hermitian (not checked); duplicate entries add.
+ * Returns KPM_EINVAL on a malformed structure. */
+kpm_status kpm_create_csr(int64_t n, const int64_t* rowptr, const int32_t* col,
+                          const double* val, kpm_field field, kpm_handle* out);
+
+/* Converts a stencil description into CSR arrays on the host (library-side
+ * builder; rows sorted by column, duplicates summed, zero-valued bonds from the
+ * mask dropped, diagonal stored only where onsite != NULL).  Call once with
+ * rowptr/col/val NULL to obtain *nnz, then again with rowptr[N+1], col[nnz],
+ * val[nnz] (or [nnz][2] complex) allocated by the caller. */
+kpm_status kpm_stencil_to_csr(const kpm_stencil_desc* desc, kpm_field field, int64_t* nnz,
+                              int64_t* rowptr, int32_t* col, double* val);
+
+/* Spectral bounds (Eq. (tilde) and the text below it): the Gershgorin
+ * enclosure [min_i(H_ii - sum_j|H_ij|), max_i(H_ii + sum_j|H_ij|)], tightened
+ * by a lanczos_steps-step FP64 Lanczos run with full reorthogonalisation from
+ * a Rademacher start vector drawn from (seed, stream 6): the extreme Ritz
+ * values widened by their residuals beta_k |s_k|, clamped to the Gershgorin
+ * enclosure (lanczos_steps = 0 gives Gershgorin alone).  Outputs (host
+ * pointers, any may be NULL): emin, emax, and the rescaling
+ *     a = (emax - emin) / (2 - pad_eps),  b = (emax + emin) / 2,
+ * pad_eps in [0, 1) (0 reproduces the paper's unpadded scaling).  Runs on
+ * `stream` and synchronises it. */
+kpm_status kpm_bounds(kpm_handle h, int lanczos_steps, double pad_eps, uint64_t seed,
+                      double* emin, double* emax, double* a, double* b, void* stream);
+
+typedef struct {
+  int M;                  /* number of moments, even, >= 2 */
+  int R;                  /* random vectors per realisation, >= 1 */
+  int S;                  /* realisations, >= 1 (0 is read as 1) */
+  uint64_t seed;          /* random vectors: entry (s, r, i) from (seed, stream 0,
+                             counter (s*R + r)*N + i): Rademacher +-1 (real field)
+                             or exp(2 pi i u) (complex field) */
+  int precision;          /* kpm_precision */
+  double a, b;            /* H~ = (H - b)/a, a > 0; never chosen implicitly */
+  const void* user_v0;    /* NULL, or an N x R start block (row-major, R
+                             contiguous; FP64 or interleaved complex FP64), host
+                             or device; requires S == 1.  The estimator uses the
+                             paper's 1/(N R) normalisation, so the full basis is
+                             sqrt(N) times the identity. */
+} kpm_params;
+
+/* Chebyshev moments mu[0..M) (Eqs. (rn), (munr), doubling form), averaged over
+ * the S*R vectors, and optionally the per-vector moments
+ * mu_per_vec[(s*R + r)*M + n] (NULL to skip).  One fused CUDA kernel per
+ * matrix product (v_{n+1} = 2 H~ v_n - v_{n-1} plus the two moment dots),
+ * replayed from a captured CUDA graph.  Returns KPM_EDIVERGE (after writing
+ * the outputs) when host outputs show |mu_n^r| > 1 + 1e-6 or a non-finite
+ * value. */
+kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu_per_vec,
+                       void* stream);
+
+/* Kernel-damped Chebyshev series on K Chebyshev nodes (Eq. (fKPM)):
+ *   x_k = cos(pi (k + 1/2) / K),  E[k] = a x_k + b,
+ *   rho[k] = [g_0 mu_0 + 2 sum_{n=1}^{M-1} g_n mu_n cos(pi n (k+1/2)/K)] / (pi a sqrt(1 - x_k^2))
+ * for k = 0 .. K-1 (E descending), g_n the Jackson kernel
+ *   g_n = [(M-n+1) cos(pi n/(M+1)) + sin(pi n/(M+1)) cot(pi/(M+1))] / (M+1)
+ * or 1 (KPM_KERNEL_NONE).  mu, E, rho host or device; computed in FP64 on the
+ * device.  1 <= M <= 1<<20, 1 <= K <= 1<<20. */
+kpm_status kpm_dos(const double* mu, int M, double a, double b, int K, int kernel,
+                   double* E, double* rho, void* stream);
+
+/* Device time of the fused-step chain of the most recent kpm_moments call on
+ * this handle: from the first fused step to the end of the last cross-CTA
+ * moment reduction of its last realisation, measured with two CUDA events
+ * recorded inside the replayed graph on the call's stream.  *step_launches
+ * receives the number of fused-step kernels in that chain (M/2), so ms /
+ * step_launches is the average duration of one fused step launch.  Call after
+ * the kpm_moments stream has completed; KPM_ENOTREADY if no call was made. */
+kpm_status kpm_step_timing(kpm_handle h, double* ms, int* step_launches);
+
+/* Handle properties (any output may be NULL): dimension, stored nonzeros of H
+ * (bonds in both directions plus stored diagonal entries), field, and
+ * stencil (1) or CSR (0). */
+kpm_status kpm_info(kpm_handle h, int64_t* n, int64_t* nnz, int* field, int* is_stencil);
+
+/* Releases the handle and its device memory (NULL is a no-op). */
+void kpm_destroy(kpm_handle h);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* kpm_last_error(void);
+
+/* Number of CUDA kernels the library has enqueued in this process (kernels in
+ * a replayed graph count once per replay). */
+uint64_t kpm_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KPM_H */

@@ -1,0 +1,744 @@
+// C ABI of the KPM library: handle creation (lattice stencil or CSR), spectral
+// bounds, Chebyshev moments and the DOS.  The host code here validates
+// arguments, owns device memory, captures the per-realisation kernel sequence
+// into a CUDA graph and replays it; every arithmetic step runs in the kernels
+// of kpm_step_*.cu and kpm_aux.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "kpm_internal.h"
+
+namespace kpm {
+
+static thread_local std::string t_err;
+std::atomic<uint64_t> g_launches{0};
+
+void set_error(const std::string& msg) { t_err = msg; }
+kpm_status fail(kpm_status st, const std::string& msg) {
+  t_err = msg;
+  return st;
+}
+kpm_status cuda_fail(cudaError_t e, const char* what) {
+  t_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return e == cudaErrorMemoryAllocation ? KPM_ENOMEM : KPM_ECUDA;
+}
+
+namespace {
+
+constexpr int RING = 64;          // step slots between two cross-CTA reductions
+constexpr int BLOCK = 256;
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+kpm_status dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return KPM_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, "cudaMalloc");
+  }
+  return KPM_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+// vector columns per 16-byte chunk
+int vec_per_chunk(bool fp32, bool cplx) { return fp32 ? (cplx ? 2 : 4) : (cplx ? 1 : 2); }
+
+void padded_width(int R, bool fp32, bool cplx, int* Rp, int* G) {
+  const int vec = vec_per_chunk(fp32, cplx);
+  int g = (R + vec - 1) / vec;
+  int p2 = 1;
+  while (p2 < g) p2 <<= 1;
+  *G = p2;
+  *Rp = p2 * vec;
+}
+
+size_t elem_bytes(bool fp32, bool cplx) { return (fp32 ? 4 : 8) * (cplx ? 2 : 1); }
+
+kpm_status check_device(int* dev) {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return fail(KPM_ECUDA, "no usable CUDA device");
+  }
+  KPM_CUDA(cudaGetDevice(dev));
+  return KPM_OK;
+}
+
+void free_work(kpm_handle_s* h) {
+  auto& w = h->work;
+  if (w.exec) cudaGraphExecDestroy(w.exec);
+  dfree(w.v[0]);
+  dfree(w.v[1]);
+  dfree(w.ring);
+  dfree(w.sums);
+  dfree(w.per_vec);  // w.mu points into per_vec
+  dfree(w.v0stage);
+  if (w.ev[0]) cudaEventDestroy(w.ev[0]);
+  if (w.ev[1]) cudaEventDestroy(w.ev[1]);
+  w = kpm_handle_s::Work{};
+}
+
+// Step arguments common to every step of a call.
+StepArgs base_args(const kpm_handle_s* h, int slot, int Rp, int G, int sites_per_cta) {
+  StepArgs a{};
+  a.n = h->n;
+  a.Rp = Rp;
+  a.G = G;
+  a.Gt = std::min(G, BLOCK);
+  a.sc = h->d_sc + slot;
+  a.geom = h->geom;
+  if (h->stencil) {
+    a.hs = h->has_hop ? h->d_hs[slot] : nullptr;
+    a.ds = h->has_onsite ? h->d_ds[slot] : nullptr;
+  } else {
+    a.rowptr = h->d_rowptr;
+    a.col = h->d_col;
+    a.vals = h->d_vals[slot];
+  }
+  a.sites_per_cta = sites_per_cta;
+  return a;
+}
+
+cudaError_t launch_step(bool stencil, bool fp32, bool cplx, StepMode mode, const StepArgs& a,
+                        const LaunchCfg& cfg, cudaStream_t st) {
+  return fp32 ? launch_step_f32(stencil, cplx, mode, a, cfg, st)
+              : launch_step_f64(stencil, cplx, mode, a, cfg, st);
+}
+
+// Grid of the fused step: at most (CTAs per SM x SMs) CTAs, each owning a
+// contiguous run of rows that is a multiple of the rows one pass covers.
+void plan_grid(const kpm_handle_s* h, bool fp32, const StepArgs& proto, int* block, int* grid,
+               int* sites_per_cta) {
+  const int G = proto.Gt;        // chunks per row handled by one CTA (<= BLOCK)
+  const int blk = BLOCK;
+  const int spi = blk / G;
+  int occ = fp32 ? occ_step_f32(h->stencil, h->cplx, proto, blk)
+                 : occ_step_f64(h->stencil, h->cplx, proto, blk);
+  occ = std::max(1, std::min(occ, 8));
+  const int64_t passes = (h->n + spi - 1) / spi;
+  int64_t g = std::min<int64_t>((int64_t)h->num_sms * occ, passes);
+  g = std::max<int64_t>(g, 1);
+  int64_t per = (passes + g - 1) / g;           // passes per CTA
+  g = (passes + per - 1) / per;
+  *block = blk;
+  *grid = (int)g;
+  *sites_per_cta = (int)(per * spi);
+}
+
+kpm_status ensure_scaled(kpm_handle_s* h, int slot, bool fp32) {
+  const size_t s = fp32 ? 4 : 8;
+  const size_t c = h->cplx ? 2 : 1;
+  if (h->stencil) {
+    if (h->has_hop && !h->d_hs[slot]) {
+      void* p = nullptr;
+      KPM_CUDA(cudaMalloc(&p, (size_t)h->n * h->geom.dims * c * s));
+      h->d_hs[slot] = p;
+    }
+    if (h->has_onsite && !h->d_ds[slot]) {
+      void* p = nullptr;
+      KPM_CUDA(cudaMalloc(&p, (size_t)h->n * s));
+      h->d_ds[slot] = p;
+    }
+  } else if (!h->d_vals[slot] && h->nnz > 0) {
+    void* p = nullptr;
+    KPM_CUDA(cudaMalloc(&p, (size_t)h->nnz * c * s));
+    h->d_vals[slot] = p;
+  }
+  return KPM_OK;
+}
+
+cudaError_t prescale(kpm_handle_s* h, int slot, bool fp32, bool lanczos, cudaStream_t st) {
+  if (h->stencil)
+    return launch_prescale_stencil(fp32, h->cplx, h->n, h->geom.dims, h->d_onsite, h->d_hop,
+                                   h->t_re, h->t_im, h->d_prm, lanczos, h->d_hs[slot],
+                                   h->d_ds[slot], h->d_sc + slot, st);
+  return launch_prescale_csr(fp32, h->cplx, h->nnz, h->d_val, h->d_prm, lanczos,
+                             h->d_vals[slot], h->d_sc + slot, st);
+}
+
+kpm_status common_init(kpm_handle_s* h) {
+  int dev = 0;
+  kpm_status st = check_device(&dev);
+  if (st != KPM_OK) return st;
+  h->device = dev;
+  KPM_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+  KPM_CUDA(cudaMalloc((void**)&h->d_sc, 3 * sizeof(ScalarBlock)));
+  KPM_CUDA(cudaMalloc((void**)&h->d_prm, sizeof(RunParams)));
+  KPM_CUDA(cudaMemset(h->d_prm, 0, sizeof(RunParams)));
+  KPM_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  return KPM_OK;
+}
+
+void destroy_handle(kpm_handle_s* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  free_work(h);
+  dfree(h->d_onsite);
+  dfree(h->d_hop);
+  dfree(h->d_rowptr);
+  dfree(h->d_col);
+  dfree(h->d_val);
+  for (int i = 0; i < 3; ++i) {
+    dfree(h->d_hs[i]);
+    dfree(h->d_ds[i]);
+    dfree(h->d_vals[i]);
+  }
+  dfree(h->d_sc);
+  dfree(h->d_prm);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+// Stencil validation shared by the handle builder and the CSR converter.
+kpm_status check_stencil(const kpm_stencil_desc* d, kpm_field field, int64_t* n_out) {
+  if (!d) return fail(KPM_EINVAL, "desc is NULL");
+  if (d->dims < 1 || d->dims > 3) return fail(KPM_EINVAL, "dims must be 1, 2 or 3");
+  if (field != KPM_REAL && field != KPM_COMPLEX) return fail(KPM_EINVAL, "bad field");
+  int64_t n = 1;
+  for (int k = 0; k < d->dims; ++k) {
+    if (d->L[k] < 1) return fail(KPM_EINVAL, "L[d] must be >= 1");
+    n *= d->L[k];
+    if (n >= (int64_t)1 << 31) return fail(KPM_EINVAL, "lattice too large (N must be < 2^31)");
+  }
+  if (field == KPM_REAL && !d->hop && d->t_im != 0.0)
+    return fail(KPM_EINVAL, "complex uniform hopping with the real field");
+  *n_out = n;
+  return KPM_OK;
+}
+
+// Row i of the stencil matrix as (column, value) pairs, merged by column and
+// sorted: H_ii = onsite_i; for each direction d the forward neighbour j gets
+// -t_{i,d} and the backward neighbour j' (whose forward bond ends at i) gets
+// -conj(t_{j',d}); absent bonds (open edge, mask 0) are skipped.
+struct RowEnt {
+  int64_t j;
+  double re, im;
+};
+int stencil_row(const kpm_stencil_desc* d, int c, int64_t i, RowEnt* out) {
+  int cnt = 0;
+  auto add = [&](int64_t j, double re, double im) {
+    for (int k = 0; k < cnt; ++k)
+      if (out[k].j == j) { out[k].re += re; out[k].im += im; return; }
+    out[cnt++] = RowEnt{j, re, im};
+  };
+  if (d->onsite) add(i, d->onsite[i], 0.0);
+  int64_t stride = 1;
+  for (int k = 0; k < d->dims; ++k) {
+    const int64_t L = d->L[k];
+    const int64_t x = (i / stride) % L;
+    const bool per = d->periodic[k] != 0;
+    const int64_t jf = x + 1 < L ? i + stride : (per ? i - (L - 1) * stride : -1);
+    const int64_t jb = x > 0 ? i - stride : (per ? i + (L - 1) * stride : -1);
+    auto hop = [&](int64_t site, double& re, double& im) {
+      const size_t o = (size_t)site * d->dims + k;
+      re = d->hop ? d->hop[o * c] : d->t_re;
+      im = c == 2 ? (d->hop ? d->hop[o * c + 1] : d->t_im) : 0.0;
+      return !d->bond_mask || d->bond_mask[o] != 0;
+    };
+    double re, im;
+    if (jf >= 0 && hop(i, re, im)) add(jf, -re, -im);
+    if (jb >= 0 && hop(jb, re, im)) add(jb, -re, im);
+    stride *= L;
+  }
+  std::sort(out, out + cnt, [](const RowEnt& a, const RowEnt& b) { return a.j < b.j; });
+  return cnt;
+}
+
+int64_t stencil_nnz(const kpm_stencil_desc* d, int c, int64_t n) {
+  RowEnt buf[8];
+  int64_t nnz = 0;
+  for (int64_t i = 0; i < n; ++i) nnz += stencil_row(d, c, i, buf);
+  return nnz;
+}
+
+}  // namespace
+}  // namespace kpm
+
+using namespace kpm;
+
+extern "C" {
+
+const char* kpm_last_error(void) { return t_err.c_str(); }
+
+uint64_t kpm_kernel_launches(void) { return g_launches.load(); }
+
+kpm_status kpm_create_stencil(const kpm_stencil_desc* d, kpm_field field, kpm_handle* out) {
+  if (!out) return fail(KPM_EINVAL, "out is NULL");
+  *out = nullptr;
+  int64_t n = 0;
+  kpm_status st = check_stencil(d, field, &n);
+  if (st != KPM_OK) return st;
+  auto* h = new kpm_handle_s();
+  h->stencil = true;
+  h->cplx = field == KPM_COMPLEX;
+  h->n = n;
+  h->geom.dims = d->dims;
+  int64_t stride = 1;
+  for (int k = 0; k < 3; ++k) {
+    h->geom.L[k] = k < d->dims ? (int)d->L[k] : 1;
+    h->geom.stride[k] = (int)stride;
+    h->geom.periodic[k] = k < d->dims ? (d->periodic[k] != 0) : 0;
+    stride *= h->geom.L[k];
+  }
+  h->t_re = d->t_re;
+  h->t_im = h->cplx ? d->t_im : 0.0;
+  h->nnz = stencil_nnz(d, field == KPM_COMPLEX ? 2 : 1, n);
+  if ((st = common_init(h)) != KPM_OK) {
+    destroy_handle(h);
+    return st;
+  }
+  const int c = h->cplx ? 2 : 1;
+  if (d->onsite) {
+    h->has_onsite = true;
+    if ((st = dalloc(&h->d_onsite, n)) != KPM_OK) { destroy_handle(h); return st; }
+    cudaError_t e = cudaMemcpy(h->d_onsite, d->onsite, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { destroy_handle(h); return cuda_fail(e, "copy onsite"); }
+  }
+  if (d->hop || d->bond_mask) {
+    h->has_hop = true;
+    std::vector<double> hop((size_t)n * d->dims * c);
+    for (int64_t i = 0; i < n; ++i)
+      for (int k = 0; k < d->dims; ++k) {
+        const size_t o = (size_t)i * d->dims + k;
+        const bool keep = !d->bond_mask || d->bond_mask[o] != 0;
+        for (int q = 0; q < c; ++q) {
+          const double v = d->hop ? d->hop[o * c + q] : (q == 0 ? d->t_re : d->t_im);
+          hop[o * c + q] = keep ? v : 0.0;
+        }
+      }
+    if ((st = dalloc(&h->d_hop, hop.size())) != KPM_OK) { destroy_handle(h); return st; }
+    cudaError_t e = cudaMemcpy(h->d_hop, hop.data(), hop.size() * sizeof(double),
+                               cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { destroy_handle(h); return cuda_fail(e, "copy hop"); }
+  }
+  *out = h;
+  return KPM_OK;
+}
+
+kpm_status kpm_create_csr(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                          kpm_field field, kpm_handle* out) {
+  if (!out) return fail(KPM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n >= ((int64_t)1 << 31)) return fail(KPM_EINVAL, "n must be in [1, 2^31)");
+  if (!rowptr) return fail(KPM_EINVAL, "rowptr is NULL");
+  if (field != KPM_REAL && field != KPM_COMPLEX) return fail(KPM_EINVAL, "bad field");
+  if (rowptr[0] != 0) return fail(KPM_EINVAL, "rowptr[0] must be 0");
+  for (int64_t i = 0; i < n; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return fail(KPM_EINVAL, "rowptr must be non-decreasing");
+  const int64_t nnz = rowptr[n];
+  if (nnz > 0 && (!col || !val)) return fail(KPM_EINVAL, "col/val NULL with nnz > 0");
+  for (int64_t k = 0; k < nnz; ++k)
+    if (col[k] < 0 || col[k] >= n) return fail(KPM_EINVAL, "column index out of range");
+  auto* h = new kpm_handle_s();
+  h->stencil = false;
+  h->cplx = field == KPM_COMPLEX;
+  h->n = n;
+  h->nnz = nnz;
+  kpm_status st = common_init(h);
+  if (st != KPM_OK) { destroy_handle(h); return st; }
+  const int c = h->cplx ? 2 : 1;
+  if ((st = dalloc(&h->d_rowptr, n + 1)) != KPM_OK ||
+      (st = dalloc(&h->d_col, std::max<int64_t>(nnz, 1))) != KPM_OK ||
+      (st = dalloc(&h->d_val, std::max<int64_t>(nnz * c, 1))) != KPM_OK) {
+    destroy_handle(h);
+    return st;
+  }
+  cudaError_t e = cudaMemcpy(h->d_rowptr, rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nnz)
+    e = cudaMemcpy(h->d_col, col, nnz * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nnz)
+    e = cudaMemcpy(h->d_val, val, nnz * c * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { destroy_handle(h); return cuda_fail(e, "copy CSR"); }
+  *out = h;
+  return KPM_OK;
+}
+
+kpm_status kpm_stencil_to_csr(const kpm_stencil_desc* d, kpm_field field, int64_t* nnz_out,
+                              int64_t* rowptr, int32_t* col, double* val) {
+  int64_t n = 0;
+  kpm_status st = check_stencil(d, field, &n);
+  if (st != KPM_OK) return st;
+  if (!nnz_out) return fail(KPM_EINVAL, "nnz is NULL");
+  const int c = field == KPM_COMPLEX ? 2 : 1;
+  if (!rowptr && !col && !val) {
+    *nnz_out = stencil_nnz(d, c, n);
+    return KPM_OK;
+  }
+  if (!rowptr || !col || !val) return fail(KPM_EINVAL, "rowptr/col/val must all be given");
+  RowEnt buf[8];
+  int64_t k = 0;
+  rowptr[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int cnt = stencil_row(d, c, i, buf);
+    for (int e = 0; e < cnt; ++e, ++k) {
+      col[k] = (int32_t)buf[e].j;
+      val[k * c] = buf[e].re;
+      if (c == 2) val[k * c + 1] = buf[e].im;
+    }
+    rowptr[i + 1] = k;
+  }
+  *nnz_out = k;
+  return KPM_OK;
+}
+
+kpm_status kpm_step_timing(kpm_handle h, double* ms, int* step_launches) {
+  if (!h) return fail(KPM_EINVAL, "handle is NULL");
+  if (!h->work.timed || !h->work.ev[0]) return fail(KPM_ENOTREADY, "no kpm_moments call yet");
+  KPM_CUDA(cudaSetDevice(h->device));
+  float t = 0.f;
+  KPM_CUDA(cudaEventElapsedTime(&t, h->work.ev[0], h->work.ev[1]));
+  if (ms) *ms = t;
+  if (step_launches) *step_launches = h->work.M / 2;
+  return KPM_OK;
+}
+
+kpm_status kpm_info(kpm_handle h, int64_t* n, int64_t* nnz, int* field, int* is_stencil) {
+  if (!h) return fail(KPM_EINVAL, "handle is NULL");
+  if (n) *n = h->n;
+  if (nnz) *nnz = h->nnz;
+  if (field) *field = h->cplx ? KPM_COMPLEX : KPM_REAL;
+  if (is_stencil) *is_stencil = h->stencil ? 1 : 0;
+  return KPM_OK;
+}
+
+void kpm_destroy(kpm_handle h) { destroy_handle(h); }
+
+kpm_status kpm_bounds(kpm_handle h, int lanczos_steps, double pad_eps, uint64_t seed,
+                      double* emin, double* emax, double* a_out, double* b_out, void* stream) {
+  if (!h) return fail(KPM_EINVAL, "handle is NULL");
+  if (lanczos_steps < 0 || lanczos_steps > 256)
+    return fail(KPM_EINVAL, "lanczos_steps must be in [0, 256]");
+  if (!(pad_eps >= 0.0 && pad_eps < 1.0)) return fail(KPM_EINVAL, "pad_eps must be in [0, 1)");
+  KPM_CUDA(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nblk = (int)std::min<int64_t>((h->n + 255) / 256, 4 * (int64_t)h->num_sms);
+  const int k = (int)std::min<int64_t>(lanczos_steps, h->n);
+  const int64_t len = 2 * h->n;  // flat FP64 scalars of one Lanczos vector
+  double *pmin = nullptr, *pmax = nullptr, *gersh = nullptr, *out = nullptr;
+  double *Q = nullptr, *y = nullptr, *part = nullptr, *coef = nullptr, *alpha = nullptr,
+         *beta = nullptr;
+  kpm_status st_ = KPM_OK;
+  auto cleanup = [&]() {
+    dfree(pmin); dfree(pmax); dfree(gersh); dfree(out); dfree(Q); dfree(y); dfree(part);
+    dfree(coef); dfree(alpha); dfree(beta);
+  };
+#define KPM_TRY(call)                                \
+  do {                                               \
+    cudaError_t e__ = (call);                        \
+    if (e__ != cudaSuccess) {                        \
+      cudaStreamSynchronize(st);                     \
+      cleanup();                                     \
+      return cuda_fail(e__, #call);                  \
+    }                                                \
+  } while (0)
+  if ((st_ = dalloc(&pmin, nblk)) || (st_ = dalloc(&pmax, nblk)) || (st_ = dalloc(&gersh, 2)) ||
+      (st_ = dalloc(&out, 8)) || (st_ = dalloc(&alpha, std::max(k, 1))) ||
+      (st_ = dalloc(&beta, std::max(k, 1)))) {
+    cleanup();
+    return st_;
+  }
+  if (h->stencil)
+    KPM_TRY(launch_gershgorin_stencil(h->cplx, h->n, h->geom, h->d_onsite, h->d_hop, h->t_re,
+                                      h->t_im, pmin, pmax, nblk, st));
+  else
+    KPM_TRY(launch_gershgorin_csr(h->cplx, h->n, h->d_rowptr, h->d_col, h->d_val, pmin, pmax,
+                                  nblk, st));
+  KPM_TRY(launch_minmax_final(pmin, pmax, nblk, gersh, st));
+  if (k > 0) {
+    if ((st_ = dalloc(&Q, (size_t)(k + 1) * len)) || (st_ = dalloc(&y, len)) ||
+        (st_ = dalloc(&part, (size_t)nblk * 2 * (k + 1))) || (st_ = dalloc(&coef, 2 * (k + 1)))) {
+      cudaStreamSynchronize(st);
+      cleanup();
+      return st_;
+    }
+    if ((st_ = ensure_scaled(h, 2, false)) != KPM_OK) {
+      cudaStreamSynchronize(st);
+      cleanup();
+      return st_;
+    }
+    KPM_TRY(prescale(h, 2, false, true, st));
+    int Rp, G;
+    padded_width(1, false, h->cplx, &Rp, &G);
+    StepArgs sa = base_args(h, 2, Rp, G, 0);
+    int block, grid, spc;
+    plan_grid(h, false, sa, &block, &grid, &spc);
+    sa.sites_per_cta = spc;
+    KPM_TRY(launch_lanczos_start(h->cplx, h->n, (unsigned long long)seed, Q, st));
+    for (int j = 0; j < k; ++j) {
+      sa.x = Q + (size_t)j * len;
+      sa.y = y;
+      sa.w = nullptr;
+      sa.partial = nullptr;
+      KPM_TRY(launch_step(h->stencil, false, h->cplx, MODE_SPMV, sa, LaunchCfg{block, grid}, st));
+      for (int pass = 0; pass < 2; ++pass) {
+        KPM_TRY(launch_dots(h->cplx, h->n, Q, len, j, y, part, nblk, st));
+        KPM_TRY(launch_dots_final(part, nblk, j, coef, st));
+        if (pass == 0) KPM_TRY(launch_store_alpha(coef, j, alpha, st));
+        KPM_TRY(launch_gs_update(h->cplx, h->n, Q, len, j, coef, y, st));
+      }
+      KPM_TRY(launch_norm2(h->n, y, part, nblk, st));
+      KPM_TRY(launch_norm_final(part, nblk, beta, j, st));
+      KPM_TRY(launch_lanczos_next(h->n, y, beta, j, Q + (size_t)(j + 1) * len, st));
+    }
+  }
+  KPM_TRY(launch_tridiag_bounds(alpha, beta, k, gersh, pad_eps, out, st));
+  double host[8];
+  KPM_TRY(cudaMemcpyAsync(host, out, sizeof(host), cudaMemcpyDeviceToHost, st));
+  KPM_TRY(cudaStreamSynchronize(st));
+#undef KPM_TRY
+  cleanup();
+  if (emin) *emin = host[0];
+  if (emax) *emax = host[1];
+  if (a_out) *a_out = host[2];
+  if (b_out) *b_out = host[3];
+  return KPM_OK;
+}
+
+kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu_per_vec,
+                       void* stream) {
+  if (!h) return fail(KPM_EINVAL, "handle is NULL");
+  if (!p) return fail(KPM_EINVAL, "params is NULL");
+  const int M = p->M, R = p->R, S = p->S > 0 ? p->S : 1;
+  if (M < 2 || (M & 1)) return fail(KPM_EINVAL, "M must be even and >= 2");
+  if (R < 1) return fail(KPM_EINVAL, "R must be >= 1");
+  if (!(p->a > 0.0) || !isfinite(p->a) || !isfinite(p->b))
+    return fail(KPM_EINVAL, "a must be > 0 and finite, b finite");
+  if (p->precision != KPM_FP64 && p->precision != KPM_FP32_VEC_FP64_MOM)
+    return fail(KPM_EINVAL, "bad precision");
+  if (p->user_v0 && S != 1) return fail(KPM_EINVAL, "user_v0 requires S == 1");
+  if (!mu && !mu_per_vec) return fail(KPM_EINVAL, "no output requested");
+  if ((int64_t)S * R * (int64_t)M > ((int64_t)1 << 40)) return fail(KPM_EINVAL, "S*R*M too large");
+  KPM_CUDA(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool fp32 = p->precision == KPM_FP32_VEC_FP64_MOM;
+  int Rp, G;
+  padded_width(R, fp32, h->cplx, &Rp, &G);
+  if (G > 1024) return fail(KPM_EINVAL, "R too large for one block of vectors");
+  const int slot = fp32 ? 1 : 0;
+  const bool user_v0 = p->user_v0 != nullptr;
+  const int steps = M / 2;
+  auto& w = h->work;
+  kpm_status s_ = ensure_scaled(h, slot, fp32);
+  if (s_ != KPM_OK) return s_;
+
+  const size_t sums_bytes = (size_t)S * steps * 2 * Rp * sizeof(double);
+  const size_t out_bytes = ((size_t)S * R * M + M) * sizeof(double);
+  const bool rebuild = w.Rp != Rp || w.prec != p->precision || w.M != M ||
+                       w.user_v0 != user_v0 || !w.exec || w.sums_bytes < sums_bytes;
+  if (rebuild) {
+    KPM_CUDA(cudaDeviceSynchronize());
+    if (w.exec) {
+      cudaGraphExecDestroy(w.exec);
+      w.exec = nullptr;
+    }
+    const size_t vbytes = (size_t)h->n * Rp * elem_bytes(fp32, h->cplx);
+    if (w.vbytes < vbytes) {
+      dfree(w.v[0]);
+      dfree(w.v[1]);
+      w.v[0] = w.v[1] = nullptr;
+      w.vbytes = 0;
+      KPM_CUDA(cudaMalloc(&w.v[0], vbytes));
+      KPM_CUDA(cudaMalloc(&w.v[1], vbytes));
+      w.vbytes = vbytes;
+    }
+    if (w.sums_bytes < sums_bytes) {
+      dfree(w.sums);
+      w.sums = nullptr;
+      w.sums_bytes = 0;
+      KPM_CUDA(cudaMalloc((void**)&w.sums, sums_bytes));
+      w.sums_bytes = sums_bytes;
+    }
+    StepArgs proto = base_args(h, slot, Rp, G, 0);
+    int block, grid, spc;
+    plan_grid(h, fp32, proto, &block, &grid, &spc);
+    dfree(w.ring);
+    w.ring = nullptr;
+    KPM_CUDA(cudaMalloc((void**)&w.ring, (size_t)RING * grid * 2 * Rp * sizeof(double)));
+    w.Rp = Rp;
+    w.prec = p->precision;
+    w.M = M;
+    w.user_v0 = user_v0;
+    w.nCTA = grid;
+    w.block = block;
+    w.sites_per_cta = spc;
+    if (!w.ev[0]) KPM_CUDA(cudaEventCreate(&w.ev[0]));
+    if (!w.ev[1]) KPM_CUDA(cudaEventCreate(&w.ev[1]));
+    w.timed = false;
+    // capture the kernel sequence of one realisation
+    const uint64_t before = g_launches.load();
+    KPM_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    const LaunchCfg cfg{block, grid};
+    if (!user_v0) e = launch_rng_init(fp32, h->cplx, h->n, Rp, h->d_prm, w.v[0], h->cap_stream);
+    StepArgs a = base_args(h, slot, Rp, G, spc);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(w.ev[0], h->cap_stream, cudaEventRecordExternal);
+    if (e == cudaSuccess) {
+      a.x = w.v[0];
+      a.y = w.v[1];
+      a.w = nullptr;
+      a.partial = w.ring;
+      e = launch_step(h->stencil, fp32, h->cplx, MODE_FIRST, a, cfg, h->cap_stream);
+    }
+    if (e == cudaSuccess && steps == 1)
+      e = launch_reduce_ring(w.ring, RING, 0, 1, grid, Rp, h->d_prm, steps, w.sums, h->cap_stream);
+    for (int n = 1; n < steps && e == cudaSuccess; ++n) {
+      a.x = w.v[n & 1];
+      a.y = w.v[(n + 1) & 1];
+      a.w = w.v[(n + 1) & 1];
+      a.partial = w.ring + (size_t)(n % RING) * grid * 2 * Rp;
+      e = launch_step(h->stencil, fp32, h->cplx, MODE_STEP, a, cfg, h->cap_stream);
+      if (e != cudaSuccess) break;
+      if ((n + 1) % RING == 0)
+        e = launch_reduce_ring(w.ring, RING, n + 1 - RING, RING, grid, Rp, h->d_prm, steps,
+                               w.sums, h->cap_stream);
+      else if (n == steps - 1)
+        e = launch_reduce_ring(w.ring, RING, steps - steps % RING, steps % RING, grid, Rp,
+                               h->d_prm, steps, w.sums, h->cap_stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(w.ev[1], h->cap_stream, cudaEventRecordExternal);
+    if (e == cudaSuccess) e = launch_advance_realisation(h->d_prm, h->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&w.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    w.kernels_per_replay = g_launches.load() - before;
+    g_launches.fetch_sub(w.kernels_per_replay);  // captured, not yet run
+    if (e != cudaSuccess) {
+      w.exec = nullptr;
+      cudaGetLastError();
+      return cuda_fail(e, "capture of the moment graph");
+    }
+  }
+  if (w.out_bytes < out_bytes) {
+    KPM_CUDA(cudaStreamSynchronize(st));
+    dfree(w.per_vec);
+    w.per_vec = nullptr;
+    w.mu = nullptr;
+    w.out_bytes = 0;
+    KPM_CUDA(cudaMalloc((void**)&w.per_vec, out_bytes));
+    w.mu = w.per_vec + (size_t)S * R * M;
+    w.out_bytes = out_bytes;
+  }
+  w.mu = w.per_vec + (size_t)S * R * M;
+
+  // per-call parameters (pageable source: staged before the call returns)
+  RunParams prm{};
+  prm.a = p->a;
+  prm.b = p->b;
+  prm.seed = (unsigned long long)p->seed;
+  prm.s = 0;
+  prm.R = R;
+  prm.S = S;
+  prm.M = M;
+  prm.flags = 0;
+  KPM_CUDA(cudaMemcpyAsync(h->d_prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st));
+  KPM_CUDA(prescale(h, slot, fp32, false, st));
+  if (user_v0) {
+    const size_t vb = (size_t)h->n * R * (h->cplx ? 2 : 1) * sizeof(double);
+    const double* src = (const double*)p->user_v0;
+    if (!is_device_ptr(p->user_v0)) {
+      if (w.v0stage_bytes < vb) {
+        KPM_CUDA(cudaStreamSynchronize(st));
+        dfree(w.v0stage);
+        w.v0stage = nullptr;
+        w.v0stage_bytes = 0;
+        KPM_CUDA(cudaMalloc((void**)&w.v0stage, vb));
+        w.v0stage_bytes = vb;
+      }
+      KPM_CUDA(cudaMemcpyAsync(w.v0stage, p->user_v0, vb, cudaMemcpyHostToDevice, st));
+      src = w.v0stage;
+    }
+    KPM_CUDA(launch_load_v0(fp32, h->cplx, h->n, R, Rp, src, w.v[0], st));
+  }
+  for (int s = 0; s < S; ++s) {
+    KPM_CUDA(cudaGraphLaunch(w.exec, st));
+    g_launches.fetch_add(w.kernels_per_replay);
+  }
+  w.timed = true;
+  KPM_CUDA(launch_finalize(w.sums, S, steps, R, Rp, h->n, M, w.per_vec, w.mu, h->d_prm, st));
+  bool host_out = false;
+  if (mu) {
+    const bool dev = is_device_ptr(mu);
+    host_out |= !dev;
+    KPM_CUDA(cudaMemcpyAsync(mu, w.mu, M * sizeof(double),
+                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  if (mu_per_vec) {
+    const bool dev = is_device_ptr(mu_per_vec);
+    host_out |= !dev;
+    KPM_CUDA(cudaMemcpyAsync(mu_per_vec, w.per_vec, (size_t)S * R * M * sizeof(double),
+                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  if (host_out) {
+    int flags = 0;
+    KPM_CUDA(cudaMemcpyAsync(&flags, &h->d_prm->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KPM_CUDA(cudaStreamSynchronize(st));
+    if (flags & 1)
+      return fail(KPM_EDIVERGE,
+                  "a moment left [-1, 1]: the bounds (a, b) do not enclose the spectrum");
+  }
+  return KPM_OK;
+}
+
+kpm_status kpm_dos(const double* mu, int M, double a, double b, int K, int kernel, double* E,
+                   double* rho, void* stream) {
+  if (!mu || !E || !rho) return fail(KPM_EINVAL, "NULL pointer");
+  if (M < 1 || M > (1 << 20) || K < 1 || K > (1 << 20)) return fail(KPM_EINVAL, "bad M or K");
+  if (!(a > 0.0) || !isfinite(a) || !isfinite(b)) return fail(KPM_EINVAL, "bad a or b");
+  if (kernel != KPM_KERNEL_JACKSON && kernel != KPM_KERNEL_NONE)
+    return fail(KPM_EINVAL, "bad kernel");
+  int dev = 0;
+  kpm_status s_ = check_device(&dev);
+  if (s_ != KPM_OK) return s_;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dmu = is_device_ptr(mu), dE = is_device_ptr(E), drho = is_device_ptr(rho);
+  // work: coef[M] table[4K] (+ mu[M] E[K] rho[K] staging)
+  const size_t nwork = (size_t)M + 4 * (size_t)K + (dmu ? 0 : M) + (dE ? 0 : K) + (drho ? 0 : K);
+  double* work = nullptr;
+  KPM_CUDA(cudaMallocAsync((void**)&work, nwork * sizeof(double), st));
+  double* cur = work + M + 4 * (size_t)K;
+  const double* mu_d = mu;
+  if (!dmu) {
+    KPM_CUDA(cudaMemcpyAsync(cur, mu, M * sizeof(double), cudaMemcpyHostToDevice, st));
+    mu_d = cur;
+    cur += M;
+  }
+  double* E_d = E;
+  if (!dE) { E_d = cur; cur += K; }
+  double* rho_d = rho;
+  if (!drho) { rho_d = cur; cur += K; }
+  cudaError_t e = launch_dos(mu_d, M, a, b, K, kernel, E_d, rho_d, work, st);
+  if (e == cudaSuccess && !dE)
+    e = cudaMemcpyAsync(E, E_d, K * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && !drho)
+    e = cudaMemcpyAsync(rho, rho_d, K * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(work, st);
+  if (e != cudaSuccess) return cuda_fail(e, "kpm_dos");
+  if (!dE || !drho) KPM_CUDA(cudaStreamSynchronize(st));
+  return KPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,802 @@
+// Auxiliary kernels of the KPM path: operator rescaling (Eq. (tilde)),
+// random start vectors (stochastic trace, Sec. II-A-3), the deterministic
+// moment reduction and doubling (Eq. (munr)), Gershgorin and Lanczos spectral
+// bounds, and the Jackson-damped Chebyshev series of Eq. (fKPM).
+#include <math.h>
+
+#include "kpm_internal.h"
+
+namespace kpm {
+
+namespace {
+
+inline unsigned blocks_for(int64_t n, int block) {
+  int64_t b = (n + block - 1) / block;
+  if (b < 1) b = 1;
+  if (b > 65535LL * 32) b = 65535LL * 32;
+  return (unsigned)b;
+}
+
+inline cudaError_t counted(cudaError_t e) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return e;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): counter-based draw for (seed, stream, counter).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long draw(unsigned long long seed, int stream,
+                                                   unsigned long long counter) {
+  const unsigned long long key = seed ^ (0x9E3779B97F4A7C15ULL * (unsigned long long)(1 + stream));
+  return splitmix64(key + counter);
+}
+
+// ------------------------------------------------------------------ prescale
+// S = scale (H - shift): scaled hoppings -scale*t, scaled diagonal scale*(eps - shift).
+template <typename T, bool CPLX>
+__global__ void prescale_stencil_kernel(int64_t n, int dims, const double* __restrict__ onsite,
+                                        const double* __restrict__ hop, double t_re, double t_im,
+                                        const RunParams* prm, bool lanczos, T* hs, T* ds,
+                                        ScalarBlock* sc) {
+  __shared__ double s_scale, s_shift;
+  if (threadIdx.x == 0) {
+    s_scale = lanczos ? 1.0 : 2.0 / prm->a;
+    s_shift = lanczos ? 0.0 : prm->b;
+  }
+  __syncthreads();
+  const double scale = s_scale, shift = s_shift;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    sc->hu_re = -scale * t_re;
+    sc->hu_im = -scale * t_im;
+    sc->du = -scale * shift;
+    sc->hu_re_f = (float)sc->hu_re;
+    sc->hu_im_f = (float)sc->hu_im;
+    sc->du_f = (float)sc->du;
+  }
+  for (int64_t s = i; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    if (ds) ds[s] = (T)(scale * (onsite[s] - shift));
+    if (hs) {
+      for (int d = 0; d < dims; ++d) {
+        if (CPLX) {
+          hs[2 * (s * dims + d)] = (T)(-scale * hop[2 * (s * dims + d)]);
+          hs[2 * (s * dims + d) + 1] = (T)(-scale * hop[2 * (s * dims + d) + 1]);
+        } else {
+          hs[s * dims + d] = (T)(-scale * hop[s * dims + d]);
+        }
+      }
+    }
+  }
+}
+
+template <typename T, bool CPLX>
+__global__ void prescale_csr_kernel(int64_t nnz, const double* __restrict__ val,
+                                    const RunParams* prm, bool lanczos, T* vals, ScalarBlock* sc) {
+  __shared__ double s_scale, s_shift;
+  if (threadIdx.x == 0) {
+    s_scale = lanczos ? 1.0 : 2.0 / prm->a;
+    s_shift = lanczos ? 0.0 : prm->b;
+  }
+  __syncthreads();
+  const double scale = s_scale, shift = s_shift;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    sc->hu_re = 0.0;
+    sc->hu_im = 0.0;
+    sc->du = -scale * shift;
+    sc->hu_re_f = 0.f;
+    sc->hu_im_f = 0.f;
+    sc->du_f = (float)sc->du;
+  }
+  const int64_t m = CPLX ? 2 * nnz : nnz;
+  for (int64_t s = i; s < m; s += (int64_t)gridDim.x * blockDim.x) vals[s] = (T)(scale * val[s]);
+}
+
+// ------------------------------------------------------------------ random vectors
+// Entry (s, r, i): counter (s R + r) N + i of stream 0; Rademacher (top bit) or
+// exp(2 pi i u), u = (u64 >> 11) 2^-53.  Padded columns r >= R are zero.
+template <typename T, bool CPLX>
+__global__ void rng_init_kernel(int64_t n, int Rp, const RunParams* __restrict__ prm, T* v0) {
+  const int R = prm->R;
+  const unsigned long long seed = prm->seed;
+  const unsigned long long s = (unsigned long long)prm->s;
+  const int64_t total = n * Rp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / Rp;
+    const int r = (int)(e % Rp);
+    if (r >= R) {
+      if (CPLX) { v0[2 * e] = T(0); v0[2 * e + 1] = T(0); }
+      else v0[e] = T(0);
+      continue;
+    }
+    const unsigned long long ctr = (s * (unsigned long long)R + (unsigned long long)r) *
+                                       (unsigned long long)n + (unsigned long long)i;
+    const unsigned long long z = draw(seed, 0, ctr);
+    if (CPLX) {
+      const double u = (double)(z >> 11) * 0x1.0p-53;
+      if (sizeof(T) == 8) {
+        double sv, cv;
+        sincospi(2.0 * u, &sv, &cv);
+        v0[2 * e] = (T)cv;
+        v0[2 * e + 1] = (T)sv;
+      } else {
+        float sv, cv;
+        sincospif(2.0f * (float)u, &sv, &cv);
+        v0[2 * e] = (T)cv;
+        v0[2 * e + 1] = (T)sv;
+      }
+    } else {
+      v0[e] = (z >> 63) ? T(-1) : T(1);
+    }
+  }
+}
+
+template <typename T, bool CPLX>
+__global__ void load_v0_kernel(int64_t n, int R, int Rp, const double* __restrict__ src, T* v0) {
+  const int64_t total = n * Rp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / Rp;
+    const int r = (int)(e % Rp);
+    if (CPLX) {
+      v0[2 * e] = r < R ? (T)src[2 * (i * R + r)] : T(0);
+      v0[2 * e + 1] = r < R ? (T)src[2 * (i * R + r) + 1] : T(0);
+    } else {
+      v0[e] = r < R ? (T)src[i * R + r] : T(0);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ moment reduction
+// ring[slot][cta][2*Rp] -> sums[s][step][2*Rp], fixed CTA order.
+__global__ void reduce_ring_kernel(const double* __restrict__ ring, int ring_slots, int first_step,
+                                   int count, int nCTA, int Rp, const RunParams* __restrict__ prm,
+                                   int steps_per_real, double* sums) {
+  const int w = 2 * Rp;
+  const int64_t total = (int64_t)count * w;
+  const int s = prm->s;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / w), o = (int)(e % w);
+    const int step = first_step + k;
+    const double* src = ring + (size_t)(step % ring_slots) * nCTA * w + o;
+    double acc = 0.0;
+    for (int c = 0; c < nCTA; ++c) acc += src[(size_t)c * w];
+    sums[((size_t)s * steps_per_real + step) * w + o] = acc;
+  }
+}
+
+__global__ void advance_realisation_kernel(RunParams* prm) { prm->s += 1; }
+
+// Doubling identities per vector, then the average over all S*R vectors.
+__global__ void finalize_pervec_kernel(const double* __restrict__ sums, int S, int steps, int R,
+                                       int Rp, int64_t n, int M, double* per_vec, RunParams* prm) {
+  const int64_t total = (int64_t)S * R * steps;
+  const int w = 2 * Rp;
+  const double inv_n = 1.0 / (double)n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int step = (int)(e % steps);
+    const int64_t sr = e / steps;
+    const int r = (int)(sr % R), s = (int)(sr / R);
+    const double* base = sums + (size_t)s * steps * w;
+    const double mu0 = base[r] * inv_n, mu1 = base[Rp + r] * inv_n;
+    double me, mo;
+    if (step == 0) {
+      me = mu0;
+      mo = mu1;
+    } else {
+      me = 2.0 * base[(size_t)step * w + r] * inv_n - mu0;
+      mo = 2.0 * base[(size_t)step * w + Rp + r] * inv_n - mu1;
+    }
+    per_vec[(size_t)sr * M + 2 * step] = me;
+    per_vec[(size_t)sr * M + 2 * step + 1] = mo;
+    const double lim = 1.0 + 1e-6;
+    if (!(fabs(me) <= lim) || !(fabs(mo) <= lim)) atomicOr(&prm->flags, 1);
+  }
+}
+
+__global__ void finalize_mean_kernel(const double* __restrict__ per_vec, int cols, int M,
+                                     double* mu) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < cols; ++c) acc += per_vec[(size_t)c * M + m];
+    mu[m] = acc / (double)cols;
+  }
+}
+
+// ------------------------------------------------------------------ Gershgorin
+__device__ __forceinline__ double cabs2(double re, double im) { return hypot(re, im); }
+
+__global__ void gershgorin_stencil_kernel(bool cplx, int64_t n, StencilGeom g,
+                                          const double* __restrict__ onsite,
+                                          const double* __restrict__ hop, double t_re,
+                                          double t_im, double* pmin, double* pmax) {
+  double lo = INFINITY, hi = -INFINITY;
+  for (int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i64 < n;
+       i64 += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)i64;
+    double center = onsite ? onsite[i] : 0.0, rad = 0.0;
+    int rem = i;
+    for (int d = 0; d < g.dims; ++d) {
+      const int L = g.L[d], s = g.stride[d];
+      const int x = rem % L;
+      rem /= L;
+      const bool per = g.periodic[d] != 0;
+      auto hopv = [&](int site, double& re, double& im) {
+        if (hop) {
+          re = cplx ? hop[2 * ((size_t)site * g.dims + d)] : hop[(size_t)site * g.dims + d];
+          im = cplx ? hop[2 * ((size_t)site * g.dims + d) + 1] : 0.0;
+        } else {
+          re = t_re;
+          im = t_im;
+        }
+      };
+      double fr, fi, br, bi;
+      if (L == 1) {
+        if (per) {  // the bond joins the site to itself: H_ii += -t - conj(t)
+          hopv(i, fr, fi);
+          center += -2.0 * fr;
+        }
+        continue;
+      }
+      const bool hasf = (x + 1 < L) || per, hasb = (x > 0) || per;
+      const int jf = (x + 1 < L) ? i + s : i - (L - 1) * s;
+      const int jb = (x > 0) ? i - s : i + (L - 1) * s;
+      if (L == 2 && per) {  // both bonds join the same pair: |H_ij| = |t_f + conj(t_b)|
+        hopv(i, fr, fi);
+        hopv(jb, br, bi);
+        rad += cabs2(fr + br, fi - bi);
+        continue;
+      }
+      if (hasf) { hopv(i, fr, fi); rad += cabs2(fr, fi); }
+      if (hasb) { hopv(jb, br, bi); rad += cabs2(br, bi); }
+      (void)jf;
+    }
+    lo = fmin(lo, center - rad);
+    hi = fmax(hi, center + rad);
+  }
+  __shared__ double smin[256], smax[256];
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + o]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pmin[blockIdx.x] = smin[0];
+    pmax[blockIdx.x] = smax[0];
+  }
+}
+
+__global__ void gershgorin_csr_kernel(bool cplx, int64_t n, const int64_t* __restrict__ rowptr,
+                                      const int32_t* __restrict__ col,
+                                      const double* __restrict__ val, double* pmin, double* pmax) {
+  double lo = INFINITY, hi = -INFINITY;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double center = 0.0, rad = 0.0;
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const double re = cplx ? val[2 * k] : val[k];
+      const double im = cplx ? val[2 * k + 1] : 0.0;
+      if (col[k] == i) center += re;
+      else rad += cabs2(re, im);
+    }
+    lo = fmin(lo, center - rad);
+    hi = fmax(hi, center + rad);
+  }
+  __shared__ double smin[256], smax[256];
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + o]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pmin[blockIdx.x] = smin[0];
+    pmax[blockIdx.x] = smax[0];
+  }
+}
+
+__global__ void minmax_final_kernel(const double* pmin, const double* pmax, int nblk, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int b = 0; b < nblk; ++b) {
+      lo = fmin(lo, pmin[b]);
+      hi = fmax(hi, pmax[b]);
+    }
+    out[0] = lo;
+    out[1] = hi;
+  }
+}
+
+// ------------------------------------------------------------------ Lanczos pieces
+// Vectors are flat FP64 arrays of `len` scalars (complex: interleaved pairs).
+__global__ void lanczos_start_kernel(bool cplx, int64_t n, int stride_scal,
+                                     unsigned long long seed, double* q) {
+  const double inv = rsqrt((double)n);
+  const int64_t total = n * stride_scal;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / stride_scal;
+    const int o = (int)(e % stride_scal);
+    double v = 0.0;
+    if (o == 0) v = (draw(seed, 6, (unsigned long long)i) >> 63) ? -inv : inv;
+    q[e] = v;
+  }
+}
+
+// part[blk][l][2] = partial <q_l | y> for l = 0..j  (complex: re, im; real: re, 0)
+__global__ void dots_kernel(bool cplx, int64_t len, const double* __restrict__ Q, int64_t ldq,
+                            int j, const double* __restrict__ y, double* part) {
+  extern __shared__ double sh[];
+  const int nl = j + 1;
+  for (int l = 0; l < nl; ++l) {
+    double re = 0.0, im = 0.0;
+    const double* q = Q + (size_t)l * ldq;
+    if (cplx) {
+      for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len / 2;
+           e += (int64_t)gridDim.x * blockDim.x) {
+        const double qr = q[2 * e], qi = q[2 * e + 1], yr = y[2 * e], yi = y[2 * e + 1];
+        re += qr * yr + qi * yi;
+        im += qr * yi - qi * yr;
+      }
+    } else {
+      for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+           e += (int64_t)gridDim.x * blockDim.x)
+        re += q[e] * y[e];
+    }
+    sh[threadIdx.x] = re;
+    sh[blockDim.x + threadIdx.x] = im;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) {
+        sh[threadIdx.x] += sh[threadIdx.x + o];
+        sh[blockDim.x + threadIdx.x] += sh[blockDim.x + threadIdx.x + o];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      part[((size_t)blockIdx.x * nl + l) * 2] = sh[0];
+      part[((size_t)blockIdx.x * nl + l) * 2 + 1] = sh[blockDim.x];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void dots_final_kernel(const double* part, int nblk, int j, double* out) {
+  const int nl = j + 1;
+  for (int o = threadIdx.x; o < 2 * nl; o += blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * 2 * nl + o];
+    out[o] = acc;
+  }
+}
+
+// y -= sum_l coef_l q_l  (complex coefficients)
+__global__ void gs_update_kernel(bool cplx, int64_t len, const double* __restrict__ Q, int64_t ldq,
+                                 int j, const double* __restrict__ coef, double* y) {
+  const int nl = j + 1;
+  if (cplx) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len / 2;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      double yr = y[2 * e], yi = y[2 * e + 1];
+      for (int l = 0; l < nl; ++l) {
+        const double cr = coef[2 * l], ci = coef[2 * l + 1];
+        const double qr = Q[(size_t)l * ldq + 2 * e], qi = Q[(size_t)l * ldq + 2 * e + 1];
+        yr -= cr * qr - ci * qi;
+        yi -= cr * qi + ci * qr;
+      }
+      y[2 * e] = yr;
+      y[2 * e + 1] = yi;
+    }
+  } else {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      double yv = y[e];
+      for (int l = 0; l < nl; ++l) yv -= coef[2 * l] * Q[(size_t)l * ldq + e];
+      y[e] = yv;
+    }
+  }
+}
+
+__global__ void store_alpha_kernel(const double* coef, int j, double* alpha) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) alpha[j] = coef[2 * j];
+}
+
+__global__ void norm_partial_kernel(int64_t len, const double* __restrict__ y, double* part) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+       e += (int64_t)gridDim.x * blockDim.x)
+    acc += y[e] * y[e];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void norm_final_kernel(const double* part, int nblk, double* beta, int j) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double acc = 0.0;
+    for (int b = 0; b < nblk; ++b) acc += part[b];
+    beta[j] = sqrt(acc);
+  }
+}
+
+__global__ void lanczos_next_kernel(int64_t len, const double* __restrict__ y,
+                                    const double* __restrict__ beta, int j, double* qnext) {
+  const double b = beta[j];
+  const double inv = b > 0.0 ? 1.0 / b : 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+       e += (int64_t)gridDim.x * blockDim.x)
+    qnext[e] = y[e] * inv;
+}
+
+// ------------------------------------------------------------------ tridiagonal bounds
+// Number of eigenvalues of the m x m symmetric tridiagonal T below x (Sturm count
+// from the signs of the LDL^T pivots of T - x I).
+__device__ int sturm_count(const double* al, const double* be, int m, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int j = 0; j < m; ++j) {
+    const double b2 = j > 0 ? be[j - 1] * be[j - 1] : 0.0;
+    d = (al[j] - x) - (j > 0 ? b2 / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// k-th smallest eigenvalue (0-based) by bisection to full precision.
+__device__ double bisect_eig(const double* al, const double* be, int m, int k, double lo,
+                             double hi) {
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(al, be, m, mid) > k) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// |last component| of the normalised eigenvector of T for eigenvalue theta, by
+// two steps of inverse iteration with a tridiagonal LU with partial pivoting.
+__device__ double last_component(const double* al, const double* be, int m, double theta,
+                                 double scale) {
+  constexpr int MAXM = 256;
+  double dl[MAXM], d[MAXM], du[MAXM], du2[MAXM], x[MAXM];
+  int piv[MAXM];
+  const double sh = theta + 1e-13 * scale;  // keep T - sh I nonsingular
+  for (int j = 0; j < m; ++j) {
+    d[j] = al[j] - sh;
+    du[j] = j + 1 < m ? be[j] : 0.0;
+    dl[j] = j + 1 < m ? be[j] : 0.0;
+    du2[j] = 0.0;
+    x[j] = 1.0;
+  }
+  // factorisation (row interchanges between j and j+1)
+  for (int j = 0; j < m - 1; ++j) {
+    if (fabs(d[j]) >= fabs(dl[j])) {
+      piv[j] = 0;
+      const double f = d[j] != 0.0 ? dl[j] / d[j] : 0.0;
+      dl[j] = f;
+      d[j + 1] -= f * du[j];
+      du2[j] = 0.0;
+    } else {
+      piv[j] = 1;
+      const double f = d[j] / dl[j];
+      d[j] = dl[j];
+      dl[j] = f;
+      const double tmp = du[j];
+      du[j] = d[j + 1];
+      d[j + 1] = tmp - f * d[j + 1];
+      if (j + 1 < m - 1) {
+        du2[j] = du[j + 1];
+        du[j + 1] = -f * du[j + 1];
+      }
+    }
+  }
+  if (d[m - 1] == 0.0) d[m - 1] = 1e-300;
+  for (int iter = 0; iter < 3; ++iter) {
+    // forward: apply L^-1 P
+    for (int j = 0; j < m - 1; ++j) {
+      if (piv[j] == 0) {
+        x[j + 1] -= dl[j] * x[j];
+      } else {
+        const double tmp = x[j];
+        x[j] = x[j + 1];
+        x[j + 1] = tmp - dl[j] * x[j];
+      }
+    }
+    // back substitution with U (diagonal d, super du, super-super du2)
+    for (int j = m - 1; j >= 0; --j) {
+      double v = x[j];
+      if (j + 1 < m) v -= du[j] * x[j + 1];
+      if (j + 2 < m) v -= du2[j] * x[j + 2];
+      x[j] = v / (d[j] != 0.0 ? d[j] : 1e-300);
+    }
+    double nrm = 0.0;
+    for (int j = 0; j < m; ++j) nrm = fmax(nrm, fabs(x[j]));
+    for (int j = 0; j < m; ++j) x[j] /= nrm;
+  }
+  double n2 = 0.0;
+  for (int j = 0; j < m; ++j) n2 += x[j] * x[j];
+  return fabs(x[m - 1]) / sqrt(n2);
+}
+
+// out = [emin, emax, a, b, theta_min, theta_max, beta_k, m]
+__global__ void tridiag_bounds_kernel(const double* alpha, const double* beta, int kmax,
+                                      const double* gersh, double pad_eps, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double gmin = gersh[0], gmax = gersh[1];
+  double emin = gmin, emax = gmax, tmin = gmin, tmax = gmax, bk = 0.0;
+  int m = 0;
+  if (kmax > 0) {
+    m = kmax;
+    for (int j = 0; j < kmax; ++j) {
+      if (beta[j] <= 1e-12 * fmax(1.0, fabs(alpha[j]))) {
+        m = j + 1;
+        break;
+      }
+    }
+    bk = beta[m - 1];
+    double lo = INFINITY, hi = -INFINITY;
+    for (int j = 0; j < m; ++j) {
+      const double r = (j > 0 ? fabs(beta[j - 1]) : 0.0) + (j + 1 < m ? fabs(beta[j]) : 0.0);
+      lo = fmin(lo, alpha[j] - r);
+      hi = fmax(hi, alpha[j] + r);
+    }
+    const double span = fmax(hi - lo, 1e-300);
+    lo -= 1e-3 * span;
+    hi += 1e-3 * span;
+    tmin = bisect_eig(alpha, beta, m, 0, lo, hi);
+    tmax = bisect_eig(alpha, beta, m, m - 1, lo, hi);
+    const double smin = m > 1 ? last_component(alpha, beta, m, tmin, span) : 1.0;
+    const double smax = m > 1 ? last_component(alpha, beta, m, tmax, span) : 1.0;
+    emin = fmax(gmin, tmin - bk * smin);
+    emax = fmin(gmax, tmax + bk * smax);
+  }
+  out[0] = emin;
+  out[1] = emax;
+  out[2] = (emax - emin) / (2.0 - pad_eps);
+  out[3] = 0.5 * (emax + emin);
+  out[4] = tmin;
+  out[5] = tmax;
+  out[6] = bk;
+  out[7] = (double)m;
+}
+
+// ------------------------------------------------------------------ DOS (Eq. (fKPM))
+// coef[n] = c_n g_n mu_n with c_0 = 1, c_n = 2; Jackson g_n from the closed form.
+__global__ void dos_coef_kernel(const double* __restrict__ mu, int M, int kernel, double* coef) {
+  const double q = M_PI / (double)(M + 1);
+  const double cotq = cos(q) / sin(q);
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < M; n += gridDim.x * blockDim.x) {
+    double g = 1.0;
+    if (kernel == KPM_KERNEL_JACKSON) {
+      double sn, cn;
+      sincospi((double)n / (double)(M + 1), &sn, &cn);
+      g = ((double)(M - n + 1) * cn + sn * cotq) / (double)(M + 1);
+    }
+    coef[n] = (n == 0 ? 1.0 : 2.0) * g * mu[n];
+  }
+}
+
+// table[j] = cos(pi j / (2K)), j = 0 .. 4K-1 (exact argument reduction for the DCT)
+__global__ void cos_table_kernel(int K, double* table) {
+  const int64_t n4 = 4LL * K;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n4;
+       j += (int64_t)gridDim.x * blockDim.x)
+    table[j] = cospi((double)j / (2.0 * (double)K));
+}
+
+// One warp per node k: lanes stride over n; cos(pi n (2k+1)/(2K)) = table[n(2k+1) mod 4K].
+__global__ void dct_kernel(const double* __restrict__ coef, int M, double a, double b, int K,
+                           const double* __restrict__ table, double* E, double* rho) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= K) return;
+  const int64_t step = 2LL * warp + 1, n4 = 4LL * K;
+  double acc = 0.0;
+  for (int n = lane; n < M; n += 32) {
+    const int64_t j = ((int64_t)n * step) % n4;
+    acc = fma(coef[n], table[j], acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    double sx, cx;
+    sincospi(((double)warp + 0.5) / (double)K, &sx, &cx);
+    E[warp] = a * cx + b;
+    rho[warp] = acc / (M_PI * sx) / a;
+  }
+}
+
+}  // namespace
+
+// ================================================================== launchers
+cudaError_t launch_prescale_stencil(bool fp32, bool cplx, int64_t n, int dims, const double* onsite,
+                                    const double* hop, double t_re, double t_im,
+                                    const RunParams* prm, bool lanczos, void* hs, void* ds,
+                                    ScalarBlock* sc, cudaStream_t st) {
+  const unsigned g = blocks_for(n, 256);
+#define KPM_PS(T, C) \
+  prescale_stencil_kernel<T, C><<<g, 256, 0, st>>>(n, dims, onsite, hop, t_re, t_im, prm, lanczos, \
+                                                   (T*)hs, (T*)ds, sc)
+  if (fp32) { if (cplx) KPM_PS(float, true); else KPM_PS(float, false); }
+  else { if (cplx) KPM_PS(double, true); else KPM_PS(double, false); }
+#undef KPM_PS
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_prescale_csr(bool fp32, bool cplx, int64_t nnz, const double* val,
+                                const RunParams* prm, bool lanczos, void* vals, ScalarBlock* sc,
+                                cudaStream_t st) {
+  const unsigned g = blocks_for((cplx ? 2 : 1) * nnz, 256);
+#define KPM_PC(T, C) \
+  prescale_csr_kernel<T, C><<<g, 256, 0, st>>>(nnz, val, prm, lanczos, (T*)vals, sc)
+  if (fp32) { if (cplx) KPM_PC(float, true); else KPM_PC(float, false); }
+  else { if (cplx) KPM_PC(double, true); else KPM_PC(double, false); }
+#undef KPM_PC
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_rng_init(bool fp32, bool cplx, int64_t n, int Rp, const RunParams* prm, void* v0,
+                            cudaStream_t st) {
+  const unsigned g = blocks_for(n * Rp, 256);
+  if (fp32) {
+    if (cplx) rng_init_kernel<float, true><<<g, 256, 0, st>>>(n, Rp, prm, (float*)v0);
+    else rng_init_kernel<float, false><<<g, 256, 0, st>>>(n, Rp, prm, (float*)v0);
+  } else {
+    if (cplx) rng_init_kernel<double, true><<<g, 256, 0, st>>>(n, Rp, prm, (double*)v0);
+    else rng_init_kernel<double, false><<<g, 256, 0, st>>>(n, Rp, prm, (double*)v0);
+  }
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_load_v0(bool fp32, bool cplx, int64_t n, int R, int Rp, const double* src,
+                           void* v0, cudaStream_t st) {
+  const unsigned g = blocks_for(n * Rp, 256);
+  if (fp32) {
+    if (cplx) load_v0_kernel<float, true><<<g, 256, 0, st>>>(n, R, Rp, src, (float*)v0);
+    else load_v0_kernel<float, false><<<g, 256, 0, st>>>(n, R, Rp, src, (float*)v0);
+  } else {
+    if (cplx) load_v0_kernel<double, true><<<g, 256, 0, st>>>(n, R, Rp, src, (double*)v0);
+    else load_v0_kernel<double, false><<<g, 256, 0, st>>>(n, R, Rp, src, (double*)v0);
+  }
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_reduce_ring(const double* ring, int ring_slots, int first_step, int count,
+                               int nCTA, int Rp, const RunParams* prm, int steps_per_real,
+                               double* sums, cudaStream_t st) {
+  const unsigned g = blocks_for((int64_t)count * 2 * Rp, 128);
+  reduce_ring_kernel<<<g, 128, 0, st>>>(ring, ring_slots, first_step, count, nCTA, Rp, prm,
+                                        steps_per_real, sums);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_advance_realisation(RunParams* prm, cudaStream_t st) {
+  advance_realisation_kernel<<<1, 1, 0, st>>>(prm);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_finalize(const double* sums, int S, int steps, int R, int Rp, int64_t n, int M,
+                            double* per_vec, double* mu, RunParams* prm, cudaStream_t st) {
+  const unsigned g = blocks_for((int64_t)S * R * steps, 256);
+  finalize_pervec_kernel<<<g, 256, 0, st>>>(sums, S, steps, R, Rp, n, M, per_vec, prm);
+  counted(cudaSuccess);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  finalize_mean_kernel<<<blocks_for(M, 128), 128, 0, st>>>(per_vec, S * R, M, mu);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_gershgorin_stencil(bool cplx, int64_t n, const StencilGeom& g,
+                                      const double* onsite, const double* hop, double t_re,
+                                      double t_im, double* part_min, double* part_max, int nblk,
+                                      cudaStream_t st) {
+  gershgorin_stencil_kernel<<<nblk, 256, 0, st>>>(cplx, n, g, onsite, hop, t_re, t_im, part_min,
+                                                  part_max);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_gershgorin_csr(bool cplx, int64_t n, const int64_t* rowptr, const int32_t* col,
+                                  const double* val, double* part_min, double* part_max, int nblk,
+                                  cudaStream_t st) {
+  gershgorin_csr_kernel<<<nblk, 256, 0, st>>>(cplx, n, rowptr, col, val, part_min, part_max);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_minmax_final(const double* part_min, const double* part_max, int nblk,
+                                double* out2, cudaStream_t st) {
+  minmax_final_kernel<<<1, 32, 0, st>>>(part_min, part_max, nblk, out2);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_lanczos_start(bool cplx, int64_t n, unsigned long long seed, double* q,
+                                 cudaStream_t st) {
+  // real: a zero pad column beside each value; complex: (re, 0)
+  lanczos_start_kernel<<<blocks_for(2 * n, 256), 256, 0, st>>>(cplx, n, 2, seed, q);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_dots(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
+                        const double* y, double* part, int nblk, cudaStream_t st) {
+  dots_kernel<<<nblk, 256, 2 * 256 * sizeof(double), st>>>(cplx, 2 * n, Q, ldq, j, y, part);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_dots_final(const double* part, int nblk, int j, double* out, cudaStream_t st) {
+  dots_final_kernel<<<1, 128, 0, st>>>(part, nblk, j, out);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_gs_update(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
+                             const double* coef, double* y, cudaStream_t st) {
+  gs_update_kernel<<<blocks_for(n, 256), 256, 0, st>>>(cplx, 2 * n, Q, ldq, j, coef, y);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_store_alpha(const double* coef, int j, double* alpha, cudaStream_t st) {
+  store_alpha_kernel<<<1, 32, 0, st>>>(coef, j, alpha);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_norm2(int64_t n, const double* y, double* part, int nblk, cudaStream_t st) {
+  norm_partial_kernel<<<nblk, 256, 0, st>>>(2 * n, y, part);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_norm_final(const double* part, int nblk, double* beta, int j,
+                              cudaStream_t st) {
+  norm_final_kernel<<<1, 32, 0, st>>>(part, nblk, beta, j);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_lanczos_next(int64_t n, const double* y, const double* beta, int j,
+                                double* qnext, cudaStream_t st) {
+  lanczos_next_kernel<<<blocks_for(2 * n, 256), 256, 0, st>>>(2 * n, y, beta, j, qnext);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, int m,
+                                  const double* gersh, double pad_eps, double* out,
+                                  cudaStream_t st) {
+  tridiag_bounds_kernel<<<1, 32, 0, st>>>(alpha, beta, m, gersh, pad_eps, out);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_dos(const double* mu, int M, double a, double b, int K, int kernel, double* E,
+                       double* rho, double* work, cudaStream_t st) {
+  double* coef = work;
+  double* table = work + M;
+  dos_coef_kernel<<<blocks_for(M, 256), 256, 0, st>>>(mu, M, kernel, coef);
+  counted(cudaSuccess);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  cos_table_kernel<<<blocks_for(4LL * K, 256), 256, 0, st>>>(K, table);
+  counted(cudaSuccess);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dct_kernel<<<blocks_for(32LL * K, 256), 256, 0, st>>>(coef, M, a, b, K, table, E, rho);
+  return counted(cudaGetLastError());
+}
+
+}  // namespace kpm

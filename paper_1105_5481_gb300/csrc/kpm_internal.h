@@ -1,0 +1,192 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "kpm.h"
+
+namespace kpm {
+
+// ----------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+kpm_status fail(kpm_status st, const std::string& msg);
+kpm_status cuda_fail(cudaError_t e, const char* what);
+extern std::atomic<uint64_t> g_launches;
+
+#define KPM_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e__ = (call);                            \
+    if (e__ != cudaSuccess) return ::kpm::cuda_fail(e__, #call); \
+  } while (0)
+
+// ----------------------------------------------------------------- operator descriptions
+// Scaled operator applied by the fused step:  (S x)_i = d_i x_i + sum_j h_ij x_j
+// where S = scale * (H - shift) (scale = 2/a, shift = b for the KPM step;
+// scale = 1, shift = 0 for the Lanczos product).
+struct ScalarBlock {        // written by the prescale kernel, read by every step
+  double hu_re, hu_im;      // uniform scaled hopping -scale*t (stencil, hop == NULL)
+  double du;                // uniform scaled diagonal -scale*shift (+ scale*0 onsite)
+  float hu_re_f, hu_im_f, du_f, pad_f;
+};
+
+struct StencilGeom {
+  int dims;
+  int L[3];
+  int stride[3];
+  int periodic[3];
+};
+
+// Per-call parameters that live in device memory so that a captured graph
+// can be replayed with new values.
+struct RunParams {
+  double a, b;              // rescaling of the current call
+  unsigned long long seed;  // random-vector seed
+  int s;                    // current realisation (advanced by the graph)
+  int R;                    // vectors per realisation
+  int S;
+  int M;
+  int flags;                // bit0: diverged
+  int pad;
+};
+
+// ----------------------------------------------------------------- kernel launchers
+// Step modes
+enum StepMode { MODE_FIRST = 0, MODE_STEP = 1, MODE_SPMV = 2 };
+
+struct StepArgs {
+  // vectors: N x Rp (row-major, Rp contiguous), element T or complex<T>
+  const void* x;     // v_n
+  void* y;           // v_{n+1} (may alias w: written in place over v_{n-1})
+  const void* w;     // v_{n-1} (MODE_STEP only)
+  double* partial;   // [nCTA][2][Rp] for this step (NULL in MODE_SPMV)
+  int64_t n;         // sites / rows
+  int Rp;            // padded vector count
+  int G;             // 16-byte chunks per row (row stride)
+  int Gt;            // chunks per row handled by one CTA (G = Gt * gridDim.y)
+  // operator
+  const ScalarBlock* sc;
+  const void* hs;    // stencil scaled hoppings [N][dims] (T or complex<T>), NULL => uniform
+  const void* ds;    // stencil scaled diagonal [N] (T), NULL => uniform
+  StencilGeom geom;
+  const int64_t* rowptr;  // CSR
+  const int32_t* col;
+  const void* vals;       // CSR scaled values (T or complex<T>)
+  int sites_per_cta;      // contiguous rows per CTA
+};
+
+struct LaunchCfg {
+  int block;
+  int grid;
+};
+
+// is_stencil, fp32, complex -> launches one fused step.
+cudaError_t launch_step_f32(bool stencil, bool cplx, StepMode mode, const StepArgs& a,
+                            const LaunchCfg& cfg, cudaStream_t st);
+cudaError_t launch_step_f64(bool stencil, bool cplx, StepMode mode, const StepArgs& a,
+                            const LaunchCfg& cfg, cudaStream_t st);
+// occupancy-derived CTAs per SM of the step variant selected by `a`
+int occ_step_f32(bool stencil, bool cplx, const StepArgs& a, int block);
+int occ_step_f64(bool stencil, bool cplx, const StepArgs& a, int block);
+
+// auxiliary kernels (kpm_aux.cu)
+cudaError_t launch_prescale_stencil(bool fp32, bool cplx, int64_t n, int dims, const double* onsite,
+                                    const double* hop, double t_re, double t_im,
+                                    const RunParams* prm, bool lanczos, void* hs, void* ds,
+                                    ScalarBlock* sc, cudaStream_t st);
+cudaError_t launch_prescale_csr(bool fp32, bool cplx, int64_t nnz, const double* val,
+                                const RunParams* prm, bool lanczos, void* vals, ScalarBlock* sc,
+                                cudaStream_t st);
+cudaError_t launch_rng_init(bool fp32, bool cplx, int64_t n, int Rp, const RunParams* prm, void* v0,
+                            cudaStream_t st);
+cudaError_t launch_load_v0(bool fp32, bool cplx, int64_t n, int R, int Rp, const double* src,
+                           void* v0, cudaStream_t st);
+cudaError_t launch_reduce_ring(const double* ring, int ring_slots, int first_step, int count,
+                               int nCTA, int Rp, const RunParams* prm, int steps_per_real,
+                               double* sums, cudaStream_t st);
+cudaError_t launch_advance_realisation(RunParams* prm, cudaStream_t st);
+cudaError_t launch_finalize(const double* sums, int S, int steps, int R, int Rp, int64_t n, int M,
+                            double* per_vec, double* mu, RunParams* prm, cudaStream_t st);
+cudaError_t launch_gershgorin_stencil(bool cplx, int64_t n, const StencilGeom& g,
+                                      const double* onsite, const double* hop, double t_re,
+                                      double t_im, double* part_min, double* part_max, int nblk,
+                                      cudaStream_t st);
+cudaError_t launch_gershgorin_csr(bool cplx, int64_t n, const int64_t* rowptr, const int32_t* col,
+                                  const double* val, double* part_min, double* part_max, int nblk,
+                                  cudaStream_t st);
+cudaError_t launch_minmax_final(const double* part_min, const double* part_max, int nblk,
+                                double* out2, cudaStream_t st);
+// Lanczos helpers (FP64; vectors are flat arrays of 2N doubles: real values
+// with a zero pad column, or interleaved complex pairs)
+cudaError_t launch_lanczos_start(bool cplx, int64_t n, unsigned long long seed, double* q,
+                                 cudaStream_t st);
+cudaError_t launch_dots(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
+                        const double* y, double* part, int nblk, cudaStream_t st);
+cudaError_t launch_dots_final(const double* part, int nblk, int j, double* out, cudaStream_t st);
+cudaError_t launch_gs_update(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
+                             const double* coef, double* y, cudaStream_t st);
+cudaError_t launch_store_alpha(const double* coef, int j, double* alpha, cudaStream_t st);
+cudaError_t launch_norm2(int64_t n, const double* y, double* part, int nblk, cudaStream_t st);
+cudaError_t launch_norm_final(const double* part, int nblk, double* beta, int j,
+                              cudaStream_t st);
+cudaError_t launch_lanczos_next(int64_t n, const double* y, const double* beta, int j,
+                                double* qnext, cudaStream_t st);
+cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, int m,
+                                  const double* gersh, double pad_eps, double* out,
+                                  cudaStream_t st);
+cudaError_t launch_dos(const double* mu, int M, double a, double b, int K, int kernel,
+                       double* E, double* rho, double* work, cudaStream_t st);
+
+}  // namespace kpm
+
+// The handle (opaque to callers).
+struct kpm_handle_s {
+  int device = 0;
+  bool cplx = false;
+  bool stencil = false;
+  int64_t n = 0;
+  int64_t nnz = 0;
+  // stencil
+  kpm::StencilGeom geom{};
+  bool has_onsite = false, has_hop = false;
+  double t_re = 1.0, t_im = 0.0;
+  double* d_onsite = nullptr;   // FP64 raw
+  double* d_hop = nullptr;      // FP64 raw (masked bonds zeroed)
+  // CSR
+  int64_t* d_rowptr = nullptr;
+  int32_t* d_col = nullptr;
+  double* d_val = nullptr;      // FP64 raw
+  // scaled operator copies: [0] = KPM FP64, [1] = KPM FP32, [2] = Lanczos FP64
+  void* d_hs[3] = {nullptr, nullptr, nullptr};
+  void* d_ds[3] = {nullptr, nullptr, nullptr};
+  void* d_vals[3] = {nullptr, nullptr, nullptr};
+  kpm::ScalarBlock* d_sc = nullptr;  // [3]
+  kpm::RunParams* d_prm = nullptr;
+  // moments workspace
+  struct Work {
+    int Rp = 0, prec = -1, M = 0, nCTA = 0, block = 0, sites_per_cta = 0;
+    bool user_v0 = false;
+    void* v[2] = {nullptr, nullptr};
+    size_t vbytes = 0;
+    double* ring = nullptr;
+    double* sums = nullptr;
+    size_t sums_bytes = 0;
+    double* per_vec = nullptr;
+    double* mu = nullptr;
+    size_t out_bytes = 0;
+    double* v0stage = nullptr;
+    size_t v0stage_bytes = 0;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t kernels_per_replay = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};  // recorded around the step chain in the graph
+    bool timed = false;
+  } work;
+  cudaStream_t cap_stream = nullptr;
+  int num_sms = 0;
+};

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libkpm.so (include/kpm.h); argument marshalling only.
+
+Every function keeps the C name and returns what the C call writes.  Host
+inputs are numpy arrays; outputs are numpy arrays unless the caller passes
+preallocated torch CUDA tensors (``out=``), in which case the library writes
+device memory directly and the call is asynchronous on ``stream``.  There is
+no fallback: if the library is missing or a call fails, an exception is
+raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libkpm.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "kpm.h")
+
+KPM_OK, KPM_EINVAL, KPM_ENOMEM, KPM_ECUDA, KPM_ETIMEOUT, KPM_EDIVERGE, KPM_EBUSY, KPM_ENOTREADY = range(8)
+KPM_REAL, KPM_COMPLEX = 0, 1
+KPM_FP64, KPM_FP32_VEC_FP64_MOM = 0, 1
+KPM_KERNEL_JACKSON, KPM_KERNEL_NONE = 0, 1
+PRECISIONS = {"fp64": KPM_FP64, "fp32": KPM_FP32_VEC_FP64_MOM, KPM_FP64: KPM_FP64,
+              KPM_FP32_VEC_FP64_MOM: KPM_FP32_VEC_FP64_MOM}
+STATUS_NAMES = {0: "KPM_OK", 1: "KPM_EINVAL", 2: "KPM_ENOMEM", 3: "KPM_ECUDA", 4: "KPM_ETIMEOUT",
+                5: "KPM_EDIVERGE", 6: "KPM_EBUSY", 7: "KPM_ENOTREADY"}
+
+
+class KPMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class kpm_stencil_desc(C.Structure):
+    _fields_ = [("dims", C.c_int), ("L", C.c_int64 * 3), ("periodic", C.c_int * 3),
+                ("onsite", C.c_void_p), ("hop", C.c_void_p), ("t_re", C.c_double),
+                ("t_im", C.c_double), ("bond_mask", C.c_void_p)]
+
+
+class kpm_params(C.Structure):
+    _fields_ = [("M", C.c_int), ("R", C.c_int), ("S", C.c_int), ("seed", C.c_uint64),
+                ("precision", C.c_int), ("a", C.c_double), ("b", C.c_double),
+                ("user_v0", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Loads libkpm.so (built in-tree by paper_1105_5481_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1105_5481_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        h = C.c_void_p
+        L.kpm_create_stencil.argtypes = [C.POINTER(kpm_stencil_desc), C.c_int, C.POINTER(h)]
+        L.kpm_create_csr.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(h)]
+        L.kpm_stencil_to_csr.argtypes = [C.POINTER(kpm_stencil_desc), C.c_int, C.POINTER(C.c_int64),
+                                         C.c_void_p, C.c_void_p, C.c_void_p]
+        L.kpm_bounds.argtypes = [h, C.c_int, C.c_double, C.c_uint64] + [C.POINTER(C.c_double)] * 4 + [C.c_void_p]
+        L.kpm_moments.argtypes = [h, C.POINTER(kpm_params), C.c_void_p, C.c_void_p, C.c_void_p]
+        L.kpm_dos.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                              C.c_void_p, C.c_void_p, C.c_void_p]
+        L.kpm_info.argtypes = [h, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                               C.POINTER(C.c_int)]
+        L.kpm_step_timing.argtypes = [h, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+        L.kpm_destroy.argtypes = [h]
+        L.kpm_destroy.restype = None
+        L.kpm_last_error.restype = C.c_char_p
+        L.kpm_kernel_launches.restype = C.c_uint64
+        for name in ("kpm_create_stencil", "kpm_create_csr", "kpm_stencil_to_csr", "kpm_bounds",
+                     "kpm_moments", "kpm_dos", "kpm_info", "kpm_step_timing"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def declared_functions() -> list[str]:
+    """Entry points declared in include/kpm.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(kpm_\w+)\s*\(", text, re.M)))
+
+
+def _check(status: int):
+    if status != KPM_OK:
+        raise KPMError(status, lib().kpm_last_error().decode())
+
+
+def _ptr(a):
+    """Pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensor must be contiguous"
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _f64(a, complex_=False):
+    if a is None:
+        return None
+    a = np.asarray(a)
+    if complex_:
+        a = np.ascontiguousarray(a, dtype=np.complex128)
+        return a.view(np.float64)
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Handle:
+    """Owning wrapper of a kpm_handle."""
+
+    def __init__(self, raw: C.c_void_p, complex_: bool, keep=()):
+        self.raw = raw
+        self.complex = complex_
+        self._keep = keep
+
+    def close(self):
+        if self.raw:
+            lib().kpm_destroy(self.raw)
+            self.raw = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _desc(dims, L, periodic, onsite, hop, t, bond_mask, complex_):
+    d = kpm_stencil_desc()
+    d.dims = int(dims)
+    L = list(L) + [1] * (3 - len(L))
+    periodic = [True] * dims if periodic is None else list(periodic)
+    periodic = list(periodic) + [True] * (3 - len(periodic))
+    for k in range(3):
+        d.L[k] = int(L[k])
+        d.periodic[k] = 1 if periodic[k] else 0
+    on = _f64(onsite)
+    hp = _f64(hop, complex_)
+    mk = None if bond_mask is None else np.ascontiguousarray(np.asarray(bond_mask, dtype=np.uint8))
+    d.onsite = _ptr(on)
+    d.hop = _ptr(hp)
+    t = complex(t)
+    d.t_re, d.t_im = t.real, t.imag
+    d.bond_mask = _ptr(mk)
+    return d, (on, hp, mk)
+
+
+def kpm_create_stencil(dims, L, periodic=None, onsite=None, hop=None, t=1.0, bond_mask=None,
+                       complex_=False) -> Handle:
+    d, keep = _desc(dims, L, periodic, onsite, hop, t, bond_mask, complex_)
+    raw = C.c_void_p()
+    _check(lib().kpm_create_stencil(C.byref(d), KPM_COMPLEX if complex_ else KPM_REAL, C.byref(raw)))
+    return Handle(raw, complex_)
+
+
+def kpm_create_csr(n, rowptr, col, val, complex_=False) -> Handle:
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    vl = _f64(val, complex_)
+    raw = C.c_void_p()
+    _check(lib().kpm_create_csr(int(n), _ptr(rp), _ptr(cl), _ptr(vl),
+                                KPM_COMPLEX if complex_ else KPM_REAL, C.byref(raw)))
+    return Handle(raw, complex_)
+
+
+def kpm_stencil_to_csr(dims, L, periodic=None, onsite=None, hop=None, t=1.0, bond_mask=None,
+                       complex_=False):
+    d, keep = _desc(dims, L, periodic, onsite, hop, t, bond_mask, complex_)
+    f = KPM_COMPLEX if complex_ else KPM_REAL
+    nnz = C.c_int64()
+    _check(lib().kpm_stencil_to_csr(C.byref(d), f, C.byref(nnz), None, None, None))
+    n = int(np.prod([d.L[k] for k in range(dims)]))
+    rowptr = np.zeros(n + 1, np.int64)
+    col = np.zeros(nnz.value, np.int32)
+    val = np.zeros(nnz.value, np.complex128 if complex_ else np.float64)
+    _check(lib().kpm_stencil_to_csr(C.byref(d), f, C.byref(nnz), _ptr(rowptr), _ptr(col),
+                                    _ptr(val.view(np.float64) if complex_ else val)))
+    return rowptr, col, val
+
+
+def kpm_bounds(h: Handle, lanczos_steps=30, pad_eps=0.01, seed=0, stream=None):
+    """Returns (emin, emax, a, b)."""
+    out = [C.c_double() for _ in range(4)]
+    _check(lib().kpm_bounds(h.raw, int(lanczos_steps), float(pad_eps), int(seed),
+                            *[C.byref(o) for o in out], _stream(stream)))
+    return tuple(o.value for o in out)
+
+
+def kpm_moments(h: Handle, M, R, a, b, seed=0, S=1, precision="fp64", user_v0=None, per_vec=False,
+                out=None, out_per_vec=None, stream=None, check=True):
+    """Chebyshev moments.  Returns mu (and mu_per_vec[S*R, M] if per_vec).
+
+    ``out``/``out_per_vec`` may be preallocated float64 arrays or CUDA tensors
+    (then the call does not synchronise).  With check=False a KPM_EDIVERGE
+    status is returned in place of an exception as the last element."""
+    p = kpm_params()
+    p.M, p.R, p.S, p.seed = int(M), int(R), int(S), int(seed) & 0xFFFFFFFFFFFFFFFF
+    p.precision = PRECISIONS[precision]
+    p.a, p.b = float(a), float(b)
+    v0 = None
+    if user_v0 is not None:
+        if hasattr(user_v0, "data_ptr"):
+            v0 = user_v0
+        else:
+            v0 = _f64(user_v0, h.complex)
+        p.user_v0 = _ptr(v0)
+    mu = out if out is not None else np.zeros(int(M))
+    pv = out_per_vec
+    if pv is None and per_vec:
+        pv = np.zeros((max(int(S), 1) * int(R), int(M)))
+    st = lib().kpm_moments(h.raw, C.byref(p), _ptr(mu), _ptr(pv), _stream(stream))
+    if st == KPM_EDIVERGE and not check:
+        return (mu, pv, st) if per_vec or out_per_vec is not None else (mu, st)
+    _check(st)
+    return (mu, pv) if per_vec or out_per_vec is not None else mu
+
+
+def kpm_dos(mu, a, b, K, kernel="jackson", E=None, rho=None, stream=None):
+    """Returns (E[K], rho[K]); host arrays unless device tensors are passed."""
+    if not hasattr(mu, "data_ptr"):
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+    M = int(mu.shape[0])
+    E = np.zeros(int(K)) if E is None else E
+    rho = np.zeros(int(K)) if rho is None else rho
+    k = KPM_KERNEL_JACKSON if kernel == "jackson" else KPM_KERNEL_NONE
+    _check(lib().kpm_dos(_ptr(mu), M, float(a), float(b), int(K), k, _ptr(E), _ptr(rho),
+                         _stream(stream)))
+    return E, rho
+
+
+def kpm_info(h: Handle):
+    n, nnz = C.c_int64(), C.c_int64()
+    field, st = C.c_int(), C.c_int()
+    _check(lib().kpm_info(h.raw, C.byref(n), C.byref(nnz), C.byref(field), C.byref(st)))
+    return dict(n=n.value, nnz=nnz.value, complex=field.value == KPM_COMPLEX, stencil=bool(st.value))
+
+
+def kpm_step_timing(h: Handle):
+    """(ms of the fused-step chain of the last kpm_moments call, fused-step launches)."""
+    ms, n = C.c_double(), C.c_int()
+    _check(lib().kpm_step_timing(h.raw, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def kpm_destroy(h: Handle):
+    h.close()
+
+
+def kpm_last_error() -> str:
+    return lib().kpm_last_error().decode()
+
+
+def kpm_kernel_launches() -> int:
+    return int(lib().kpm_kernel_launches())
