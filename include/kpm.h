@@ -175,6 +175,37 @@ kpm_status kpm_dos(const double* mu, int M, double a, double b, int K, int kerne
  * the kpm_moments stream has completed; KPM_ENOTREADY if no call was made. */
 kpm_status kpm_step_timing(kpm_handle h, double* ms, int* step_launches);
 
+/* Size of the fixed device scratch array behind kpm_moments_csr_noalloc. */
+#define KPM_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* kpm_moments without any device allocation (the paper has no counterpart;
+ * this is a library service).  Some callers cannot allocate device memory
+ * during a call: they run with a frozen or exhausted memory pool, budget all
+ * device memory at start-up, or cannot afford the device synchronisation and
+ * locking that cudaMalloc/cudaFree may cause.  This entry point computes the
+ * FP64 Chebyshev moments mu[0..M) of a CSR matrix that is already in device
+ * memory (d_rowptr[n+1] int64, d_col[nnz] int32, d_val[nnz] FP64 or [nnz][2]
+ * complex FP64, same layout and meaning as kpm_create_csr) with the same
+ * kernels and the same random vectors as kpm_moments with S = 1 and
+ * precision KPM_FP64, and allocates nothing: all of its scratch (two N x R
+ * vector blocks, the scaled matrix values, partial and moment sums) lives in
+ * one file-scope device array of KPM_NOALLOC_SCRATCH_BYTES bytes that every
+ * GPU loading the library holds until the process exits.
+ *   mu: M doubles, device (asynchronous on `stream`) or host (synchronises and
+ *       reports KPM_EDIVERGE like kpm_moments).
+ * Returns KPM_EINVAL, naming the bytes it would need, when the problem does
+ * not fit in the scratch (roughly 16 N R + 16 nnz bytes for real FP64; R up
+ * to 512 real or 256 complex).  The first call on a device looks up the
+ * scratch's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the
+ * scratch and each leaves its contents behind: calls whose work can overlap
+ * on the GPU (other streams, other host threads) race and must be serialised
+ * by the caller. */
+kpm_status kpm_moments_csr_noalloc(int64_t n, int64_t nnz, const int64_t* d_rowptr,
+                                   const int32_t* d_col, const double* d_val, kpm_field field,
+                                   int M, int R, uint64_t seed, double a, double b, double* mu,
+                                   void* stream);
+
 /* Handle properties (any output may be NULL): dimension, stored nonzeros of H
  * (bonds in both directions plus stored diagonal entries), field, and
  * stencil (1) or CSR (0). */

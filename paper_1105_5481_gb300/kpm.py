@@ -69,12 +69,16 @@ def lib() -> C.CDLL:
         L.kpm_info.argtypes = [h, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int),
                                C.POINTER(C.c_int)]
         L.kpm_step_timing.argtypes = [h, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+        L.kpm_moments_csr_noalloc.argtypes = [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_double,
+                                              C.c_double, C.c_void_p, C.c_void_p]
         L.kpm_destroy.argtypes = [h]
         L.kpm_destroy.restype = None
         L.kpm_last_error.restype = C.c_char_p
         L.kpm_kernel_launches.restype = C.c_uint64
         for name in ("kpm_create_stencil", "kpm_create_csr", "kpm_stencil_to_csr", "kpm_bounds",
-                     "kpm_moments", "kpm_dos", "kpm_info", "kpm_step_timing"):
+                     "kpm_moments", "kpm_dos", "kpm_info", "kpm_step_timing",
+                     "kpm_moments_csr_noalloc"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -268,6 +272,20 @@ def kpm_step_timing(h: Handle):
     ms, n = C.c_double(), C.c_int()
     _check(lib().kpm_step_timing(h.raw, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def kpm_moments_csr_noalloc(n, nnz, d_rowptr, d_col, d_val, M, R, a, b, seed=0, complex_=False,
+                            out=None, stream=None):
+    """FP64 moments of a device-resident CSR matrix using only the library's
+    fixed scratch array (no device allocation inside the call).  d_* are
+    contiguous CUDA tensors (int64, int32, float64 [or float64 pairs]); ``out``
+    a float64 CUDA tensor of M entries (asynchronous) or None (host result)."""
+    mu = np.zeros(int(M)) if out is None else out
+    _check(lib().kpm_moments_csr_noalloc(int(n), int(nnz), _ptr(d_rowptr), _ptr(d_col), _ptr(d_val),
+                                         KPM_COMPLEX if complex_ else KPM_REAL, int(M), int(R),
+                                         int(seed) & 0xFFFFFFFFFFFFFFFF, float(a), float(b), _ptr(mu),
+                                         _stream(stream)))
+    return mu
 
 
 def kpm_destroy(h: Handle):
