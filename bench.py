@@ -166,6 +166,26 @@ def reference_arm(args):
     return 0
 
 
+def profile_run(prec):
+    """Two solves of the workload with Gershgorin bounds (no Lanczos products, so
+    the only fused-step launches are those of the two solves)."""
+    import torch
+
+    from paper_1105_5481_gb300 import build as B
+    from paper_1105_5481_gb300 import inputs as I
+    from paper_1105_5481_gb300 import kpm as K
+
+    B.build()
+    w = I.workload("cubic_spin_L64")
+    with K.kpm_create_stencil(3, w["L"], hop=w["hop"], complex_=True) as h:
+        _, _, a, b = K.kpm_bounds(h, 0, WORKLOAD["pad_eps"])
+        for i in range(2):
+            mu = K.kpm_moments(h, WORKLOAD["M"], WORKLOAD["R"], a, b, seed=1000 + i, precision=prec)
+        torch.cuda.synchronize()
+    print(json.dumps({"profile": prec, "mu0": float(mu[0]), "mu2": float(mu[2])}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -174,9 +194,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", default=None, choices=["fp32", "fp64"],
+                    help="run two solves of the workload at the given precision and exit "
+                         "(a short command for ncu captures of the fused step)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile:
+        return profile_run(args.profile)
 
     import torch
 

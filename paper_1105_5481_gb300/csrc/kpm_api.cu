@@ -60,8 +60,8 @@ void dfree(void* p) {
   if (p) cudaFree(p);
 }
 
-// vector columns per 16-byte chunk
-int vec_per_chunk(bool fp32, bool cplx) { return fp32 ? (cplx ? 2 : 4) : (cplx ? 1 : 2); }
+// vector columns per chunk (FP32: 32-byte chunks; FP64: 16-byte chunks)
+int vec_per_chunk(bool fp32, bool cplx) { return fp32 ? (cplx ? 4 : 8) : (cplx ? 1 : 2); }
 
 void padded_width(int R, bool fp32, bool cplx, int* Rp, int* G) {
   const int vec = vec_per_chunk(fp32, cplx);
@@ -100,7 +100,7 @@ void free_work(kpm_handle_s* h) {
 }
 
 // Step arguments common to every step of a call.
-StepArgs base_args(const kpm_handle_s* h, int slot, int Rp, int G, int sites_per_cta) {
+StepArgs base_args(const kpm_handle_s* h, int slot, int Rp, int G) {
   StepArgs a{};
   a.n = h->n;
   a.Rp = Rp;
@@ -116,7 +116,6 @@ StepArgs base_args(const kpm_handle_s* h, int slot, int Rp, int G, int sites_per
     a.col = h->d_col;
     a.vals = h->d_vals[slot];
   }
-  a.sites_per_cta = sites_per_cta;
   return a;
 }
 
@@ -126,24 +125,40 @@ cudaError_t launch_step(bool stencil, bool fp32, bool cplx, StepMode mode, const
               : launch_step_f64(stencil, cplx, mode, a, cfg, st);
 }
 
-// Grid of the fused step: at most (CTAs per SM x SMs) CTAs, each owning a
-// contiguous run of rows that is a multiple of the rows one pass covers.
-void plan_grid(const kpm_handle_s* h, bool fp32, const StepArgs& proto, int* block, int* grid,
-               int* sites_per_cta) {
-  const int G = proto.Gt;        // chunks per row handled by one CTA (<= BLOCK)
+// Traversal and grid of the fused step (see StepArgs).  Stencils with enough
+// lattice lines are walked in line blocks so that the rows of one pass are
+// each other's y-neighbours; CSR matrices and small or 1D lattices use the
+// natural row order.  CTAs: at most (CTAs per SM x SMs), each taking chunks
+// of STEP_CHUNK passes in a grid-stride loop.
+#ifndef KPM_STEP_CHUNK
+#define KPM_STEP_CHUNK 4   // passes per chunk; 0 = one whole lattice line
+#endif
+
+void plan_grid(const kpm_handle_s* h, bool fp32, StepArgs& a, int* block, int* grid) {
+  const int G = a.Gt;            // chunks per row handled by one CTA (<= BLOCK)
   const int blk = BLOCK;
   const int spi = blk / G;
-  int occ = fp32 ? occ_step_f32(h->stencil, h->cplx, proto, blk)
-                 : occ_step_f64(h->stencil, h->cplx, proto, blk);
+  int occ = fp32 ? occ_step_f32(h->stencil, h->cplx, a, blk)
+                 : occ_step_f64(h->stencil, h->cplx, a, blk);
   occ = std::max(1, std::min(occ, 8));
-  const int64_t passes = (h->n + spi - 1) / spi;
-  int64_t g = std::min<int64_t>((int64_t)h->num_sms * occ, passes);
-  g = std::max<int64_t>(g, 1);
-  int64_t per = (passes + g - 1) / g;           // passes per CTA
-  g = (passes + per - 1) / per;
+  a.line_len = 0;
+  a.lines = 0;
+  a.line_L1 = h->geom.L[1];
+  a.passes = (h->n + spi - 1) / spi;
+  if (h->stencil && h->geom.dims >= 2 && h->geom.L[0] >= 4) {
+    const int64_t lines = h->n / h->geom.L[0];
+    const int64_t padded = (lines + spi - 1) / spi * spi;
+    if (lines >= spi && 8 * (padded - lines) <= lines) {
+      a.line_len = h->geom.L[0];
+      a.lines = (int)lines;
+      a.passes = padded / spi * (int64_t)h->geom.L[0];
+    }
+  }
+  a.chunk = KPM_STEP_CHUNK > 0 ? KPM_STEP_CHUNK : (a.line_len > 0 ? a.line_len : 4);
+  const int64_t nchunks = (a.passes + a.chunk - 1) / a.chunk;
+  int64_t g = std::min<int64_t>((int64_t)h->num_sms * occ, nchunks);
   *block = blk;
-  *grid = (int)g;
-  *sites_per_cta = (int)(per * spi);
+  *grid = (int)std::max<int64_t>(g, 1);
 }
 
 kpm_status ensure_scaled(kpm_handle_s* h, int slot, bool fp32) {
@@ -481,10 +496,9 @@ kpm_status kpm_bounds(kpm_handle h, int lanczos_steps, double pad_eps, uint64_t 
     KPM_TRY(prescale(h, 2, false, true, st));
     int Rp, G;
     padded_width(1, false, h->cplx, &Rp, &G);
-    StepArgs sa = base_args(h, 2, Rp, G, 0);
-    int block, grid, spc;
-    plan_grid(h, false, sa, &block, &grid, &spc);
-    sa.sites_per_cta = spc;
+    StepArgs sa = base_args(h, 2, Rp, G);
+    int block, grid;
+    plan_grid(h, false, sa, &block, &grid);
     KPM_TRY(launch_lanczos_start(h->cplx, h->n, (unsigned long long)seed, Q, st));
     for (int j = 0; j < k; ++j) {
       sa.x = Q + (size_t)j * len;
@@ -570,9 +584,10 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
       KPM_CUDA(cudaMalloc((void**)&w.sums, sums_bytes));
       w.sums_bytes = sums_bytes;
     }
-    StepArgs proto = base_args(h, slot, Rp, G, 0);
-    int block, grid, spc;
-    plan_grid(h, fp32, proto, &block, &grid, &spc);
+    StepArgs proto = base_args(h, slot, Rp, G);
+    int block, grid;
+    plan_grid(h, fp32, proto, &block, &grid);
+    w.proto = proto;
     dfree(w.ring);
     w.ring = nullptr;
     KPM_CUDA(cudaMalloc((void**)&w.ring, (size_t)RING * grid * 2 * Rp * sizeof(double)));
@@ -582,7 +597,6 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
     w.user_v0 = user_v0;
     w.nCTA = grid;
     w.block = block;
-    w.sites_per_cta = spc;
     if (!w.ev[0]) KPM_CUDA(cudaEventCreate(&w.ev[0]));
     if (!w.ev[1]) KPM_CUDA(cudaEventCreate(&w.ev[1]));
     w.timed = false;
@@ -592,7 +606,7 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
     cudaError_t e = cudaSuccess;
     const LaunchCfg cfg{block, grid};
     if (!user_v0) e = launch_rng_init(fp32, h->cplx, h->n, Rp, h->d_prm, w.v[0], h->cap_stream);
-    StepArgs a = base_args(h, slot, Rp, G, spc);
+    StepArgs a = proto;
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(w.ev[0], h->cap_stream, cudaEventRecordExternal);
     if (e == cudaSuccess) {
       a.x = w.v[0];

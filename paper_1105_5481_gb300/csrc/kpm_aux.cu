@@ -97,6 +97,20 @@ __global__ void prescale_csr_kernel(int64_t nnz, const double* __restrict__ val,
 }
 
 // ------------------------------------------------------------------ random vectors
+// Scalar offsets of the real and imaginary parts of entry (i, r) of an N x Rp
+// complex block.  FP64 blocks interleave (re, im); FP32 blocks store 32-byte
+// chunks of 4 columns split as (re0..re3, im0..im3).
+template <typename T>
+__device__ __forceinline__ void cplx_offsets(int64_t i, int r, int Rp, int64_t& re, int64_t& im) {
+  if (sizeof(T) == 8) {
+    re = 2 * (i * Rp + r);
+    im = re + 1;
+  } else {
+    re = i * 2 * Rp + (r / 4) * 8 + (r % 4);
+    im = re + 4;
+  }
+}
+
 // Entry (s, r, i): counter (s R + r) N + i of stream 0; Rademacher (top bit) or
 // exp(2 pi i u), u = (u64 >> 11) 2^-53.  Padded columns r >= R are zero.
 template <typename T, bool CPLX>
@@ -109,8 +123,10 @@ __global__ void rng_init_kernel(int64_t n, int Rp, const RunParams* __restrict__
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / Rp;
     const int r = (int)(e % Rp);
+    int64_t ore = e, oim = e;
+    if (CPLX) cplx_offsets<T>(i, r, Rp, ore, oim);
     if (r >= R) {
-      if (CPLX) { v0[2 * e] = T(0); v0[2 * e + 1] = T(0); }
+      if (CPLX) { v0[ore] = T(0); v0[oim] = T(0); }
       else v0[e] = T(0);
       continue;
     }
@@ -122,13 +138,13 @@ __global__ void rng_init_kernel(int64_t n, int Rp, const RunParams* __restrict__
       if (sizeof(T) == 8) {
         double sv, cv;
         sincospi(2.0 * u, &sv, &cv);
-        v0[2 * e] = (T)cv;
-        v0[2 * e + 1] = (T)sv;
+        v0[ore] = (T)cv;
+        v0[oim] = (T)sv;
       } else {
         float sv, cv;
         sincospif(2.0f * (float)u, &sv, &cv);
-        v0[2 * e] = (T)cv;
-        v0[2 * e + 1] = (T)sv;
+        v0[ore] = (T)cv;
+        v0[oim] = (T)sv;
       }
     } else {
       v0[e] = (z >> 63) ? T(-1) : T(1);
@@ -144,8 +160,10 @@ __global__ void load_v0_kernel(int64_t n, int R, int Rp, const double* __restric
     const int64_t i = e / Rp;
     const int r = (int)(e % Rp);
     if (CPLX) {
-      v0[2 * e] = r < R ? (T)src[2 * (i * R + r)] : T(0);
-      v0[2 * e + 1] = r < R ? (T)src[2 * (i * R + r) + 1] : T(0);
+      int64_t ore, oim;
+      cplx_offsets<T>(i, r, Rp, ore, oim);
+      v0[ore] = r < R ? (T)src[2 * (i * R + r)] : T(0);
+      v0[oim] = r < R ? (T)src[2 * (i * R + r) + 1] : T(0);
     } else {
       v0[e] = r < R ? (T)src[i * R + r] : T(0);
     }
@@ -153,21 +171,29 @@ __global__ void load_v0_kernel(int64_t n, int R, int Rp, const double* __restric
 }
 
 // ------------------------------------------------------------------ moment reduction
-// ring[slot][cta][2*Rp] -> sums[s][step][2*Rp], fixed CTA order.
+// ring[slot][cta][2*Rp] -> sums[s][step][2*Rp].  Block (k, g) sums 32 output
+// columns of step first+k: warp w adds CTAs w, w+8, w+16, ... in order, then
+// the 8 warp sums are added in warp order (a fixed order for a given grid).
 __global__ void reduce_ring_kernel(const double* __restrict__ ring, int ring_slots, int first_step,
-                                   int count, int nCTA, int Rp, const RunParams* __restrict__ prm,
+                                   int nCTA, int Rp, const RunParams* __restrict__ prm,
                                    int steps_per_real, double* sums) {
+  __shared__ double part[8][33];
   const int w = 2 * Rp;
-  const int64_t total = (int64_t)count * w;
-  const int s = prm->s;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(e / w), o = (int)(e % w);
-    const int step = first_step + k;
+  const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+  const int o = blockIdx.y * 32 + lane;
+  const int step = first_step + blockIdx.x;
+  double acc = 0.0;
+  if (o < w) {
     const double* src = ring + (size_t)(step % ring_slots) * nCTA * w + o;
-    double acc = 0.0;
-    for (int c = 0; c < nCTA; ++c) acc += src[(size_t)c * w];
-    sums[((size_t)s * steps_per_real + step) * w + o] = acc;
+#pragma unroll 4
+    for (int c = slice; c < nCTA; c += 8) acc += src[(size_t)c * w];
+  }
+  part[slice][lane] = acc;
+  __syncthreads();
+  if (slice == 0 && o < w) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += part[k][lane];
+    sums[((size_t)prm->s * steps_per_real + step) * w + o] = t;
   }
 }
 
@@ -686,9 +712,9 @@ cudaError_t launch_load_v0(bool fp32, bool cplx, int64_t n, int R, int Rp, const
 cudaError_t launch_reduce_ring(const double* ring, int ring_slots, int first_step, int count,
                                int nCTA, int Rp, const RunParams* prm, int steps_per_real,
                                double* sums, cudaStream_t st) {
-  const unsigned g = blocks_for((int64_t)count * 2 * Rp, 128);
-  reduce_ring_kernel<<<g, 128, 0, st>>>(ring, ring_slots, first_step, count, nCTA, Rp, prm,
-                                        steps_per_real, sums);
+  const dim3 grid((unsigned)count, (unsigned)((2 * Rp + 31) / 32));
+  reduce_ring_kernel<<<grid, 256, 0, st>>>(ring, ring_slots, first_step, nCTA, Rp, prm,
+                                           steps_per_real, sums);
   return counted(cudaGetLastError());
 }
 

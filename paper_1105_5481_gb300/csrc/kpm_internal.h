@@ -78,7 +78,19 @@ struct StepArgs {
   const int64_t* rowptr;  // CSR
   const int32_t* col;
   const void* vals;       // CSR scaled values (T or complex<T>)
-  int sites_per_cta;      // contiguous rows per CTA
+  // Traversal.  The rows are visited in passes of Q = (threads / Gt) rows,
+  // one row per thread group.  line_len == 0: pass P covers rows P*Q .. P*Q+Q-1
+  // (natural order).  Otherwise pass P covers x = P % line_len on the Q
+  // adjacent lattice lines (a line = the line_len sites sharing y, z)
+  // (P / line_len)*Q .. +Q-1, so that the rows of one pass are each other's
+  // y-neighbours.  CTAs take chunks of `chunk` consecutive passes in a
+  // grid-stride loop, so all CTAs sweep one compact front of passes and every
+  // neighbour row is reused within about one chunk round.
+  int line_len;
+  int lines;
+  int line_L1;            // L[1] (3D: line -> y = line % L1, z = line / L1)
+  int64_t passes;         // total passes
+  int chunk;              // passes per chunk
 };
 
 struct LaunchCfg {
@@ -170,7 +182,7 @@ struct kpm_handle_s {
   kpm::RunParams* d_prm = nullptr;
   // moments workspace
   struct Work {
-    int Rp = 0, prec = -1, M = 0, nCTA = 0, block = 0, sites_per_cta = 0;
+    int Rp = 0, prec = -1, M = 0, nCTA = 0, block = 0;
     bool user_v0 = false;
     void* v[2] = {nullptr, nullptr};
     size_t vbytes = 0;
@@ -184,6 +196,7 @@ struct kpm_handle_s {
     size_t v0stage_bytes = 0;
     cudaGraphExec_t exec = nullptr;
     uint64_t kernels_per_replay = 0;
+    kpm::StepArgs proto{};                    // launch arguments common to all steps
     cudaEvent_t ev[2] = {nullptr, nullptr};  // recorded around the step chain in the graph
     bool timed = false;
   } work;

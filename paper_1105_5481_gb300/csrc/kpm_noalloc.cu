@@ -97,11 +97,11 @@ extern "C" kpm_status kpm_moments_csr_noalloc(int64_t n, int64_t nnz, const int6
   a0.G = G;
   a0.Gt = G;
   const int spi = NA_BLOCK / G;
+  a0.passes = (n + spi - 1) / spi;  // natural row order (CSR)
+  a0.chunk = 4;
   int occ = std::max(1, std::min(occ_step_f64(false, cplx, a0, NA_BLOCK), 8));
-  const int64_t passes = (n + spi - 1) / spi;
-  int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * occ, passes));
-  const int64_t per = (passes + grid - 1) / grid;
-  grid = (passes + per - 1) / per;
+  const int64_t nchunks = (a0.passes + a0.chunk - 1) / a0.chunk;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * occ, nchunks));
 
   // scratch layout, checked against the fixed size before anything is launched
   size_t off = 0;
@@ -152,7 +152,6 @@ extern "C" kpm_status kpm_moments_csr_noalloc(int64_t n, int64_t nnz, const int6
   sa.rowptr = d_rowptr;
   sa.col = d_col;
   sa.vals = vals;
-  sa.sites_per_cta = (int)(per * spi);
   const LaunchCfg cfg{NA_BLOCK, (int)grid};
   void* v[2] = {v0, v1};
   sa.x = v0;

@@ -1,77 +1,212 @@
 // Fused Chebyshev step: v_{n+1} = 2 H~ v_n - v_{n-1} (Eq. (rn)) with the two
 // moment dot products of the doubling identities, one pass over the vectors.
 //
-// Vector blocks are N x Rp, row-major with the Rp vectors of a site contiguous
-// (complex entries interleaved re, im).  A row is split into G 16-byte chunks;
-// a group of Gt consecutive threads owns one row (Gt = G, or a slice of a
-// wider row selected by blockIdx.y), each thread one chunk, so every load and
-// store of a vector is a coalesced 128-bit access.  Each CTA
-// walks a contiguous range of rows, so the lattice neighbours at +-1 and
-// +-L_x rows are re-read from L1 while the far neighbours (+-L_x L_y rows)
-// come from L2; v_n is read through the read-only path, v_{n-1} is streamed
-// and v_{n+1} is written over it in place.
+// Vector blocks are N x Rp, row-major with the Rp vectors of a site
+// contiguous.  A row is split into G chunks; a group of Gt consecutive threads
+// owns one row (Gt = G, or a slice of a wider row selected by blockIdx.y),
+// each thread one chunk, so every access to a vector is one coalesced vector
+// load or store per thread:
+//   FP64 path (ChunkF64): 16-byte chunks, 2 real columns or 1 complex column
+//     stored (re, im).
+//   FP32 path (ChunkF32): 32-byte chunks moved with 256-bit loads/stores, 8
+//     real columns or 4 complex columns stored split as (re0..re3, im0..im3),
+//     so that the complex arithmetic runs on packed f32x2 FMAs.
+// v_n is read through the read-only path, v_{n-1} is streamed and v_{n+1} is
+// written over it in place.  The traversal (StepArgs) makes every neighbour
+// row of v_n come from L1/L2 within about one pass of its first use.
 //
 // Moments: per vector column, A = <v_n|v_n> and B = Re<v_{n+1}|v_n> are
-// accumulated per thread (FP64 on the FP64 path; FP32 partial sums over
-// PROMOTE rows promoted into FP64 on the FP32 path), reduced over the lanes
+// accumulated per thread (FP64 on the FP64 path; Kahan-compensated f32x2 sums
+// promoted to FP64 once per thread on the FP32 path), reduced over the lanes
 // that share a column with warp shuffles, over the warps in shared memory in a
 // fixed order, and written as one [2][Rp] FP64 partial per CTA.  The cross-CTA
 // sum is done later by a separate fixed-order kernel, so results are bitwise
 // reproducible for a given launch shape.
 #pragma once
 
+#include <type_traits>
+
 #include "kpm_internal.h"
+
+// Minimum resident CTAs per SM requested from the register allocator.
+#ifndef KPM_STEP_MIN_BLOCKS
+#define KPM_STEP_MIN_BLOCKS 2
+#endif
 
 namespace kpm {
 
-constexpr int PROMOTE = 8;  // FP32 rows summed before promotion to FP64
+// ================================================================ chunk policies
+// FP64: 16 bytes = 2 doubles.
+template <bool CPLX_>
+struct ChunkF64 {
+  using T = double;
+  static constexpr bool CPLX = CPLX_;
+  static constexpr int SC = 2;                // scalars per chunk
+  static constexpr int VEC = CPLX ? 1 : 2;    // vector columns per chunk
+  double v[2];
 
-__device__ __forceinline__ void ld16_nc(const float* p, float (&r)[4]) {
-  float4 q = __ldg(reinterpret_cast<const float4*>(p));
-  r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
-}
-__device__ __forceinline__ void ld16_nc(const double* p, double (&r)[2]) {
-  double2 q = __ldg(reinterpret_cast<const double2*>(p));
-  r[0] = q.x; r[1] = q.y;
-}
-__device__ __forceinline__ void ld16_cs(const float* p, float (&r)[4]) {
-  float4 q = __ldcs(reinterpret_cast<const float4*>(p));
-  r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
-}
-__device__ __forceinline__ void ld16_cs(const double* p, double (&r)[2]) {
-  double2 q = __ldcs(reinterpret_cast<const double2*>(p));
-  r[0] = q.x; r[1] = q.y;
-}
-__device__ __forceinline__ void st16(float* p, const float (&r)[4]) {
-  *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
-}
-__device__ __forceinline__ void st16(double* p, const double (&r)[2]) {
-  *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
-}
-
-template <typename T>
-struct Traits {
-  static constexpr int SC = 16 / sizeof(T);  // scalars per chunk
+  __device__ __forceinline__ void ld_nc(const double* p) {
+    const double2 q = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = q.x; v[1] = q.y;
+  }
+  __device__ __forceinline__ void ld_cs(const double* p) {
+    const double2 q = __ldcs(reinterpret_cast<const double2*>(p));
+    v[0] = q.x; v[1] = q.y;
+  }
+  __device__ __forceinline__ void st(double* p) const {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+  __device__ __forceinline__ void zero() { v[0] = v[1] = 0.0; }
+  __device__ __forceinline__ void set_neg(const ChunkF64& w) { v[0] = -w.v[0]; v[1] = -w.v[1]; }
+  __device__ __forceinline__ void half() { v[0] *= 0.5; v[1] *= 0.5; }
+  // this += d x (real d)
+  __device__ __forceinline__ void axpy(double d, const ChunkF64& x) {
+    v[0] = fma(d, x.v[0], v[0]);
+    v[1] = fma(d, x.v[1], v[1]);
+  }
+  // this += h x (h = hr + i hi; the real field ignores hi)
+  __device__ __forceinline__ void cmac(double hr, double hi, const ChunkF64& x) {
+    if constexpr (CPLX) {
+      v[0] = fma(hr, x.v[0], v[0]);
+      v[0] = fma(-hi, x.v[1], v[0]);
+      v[1] = fma(hr, x.v[1], v[1]);
+      v[1] = fma(hi, x.v[0], v[1]);
+    } else {
+      axpy(hr, x);
+    }
+  }
+  struct Acc {
+    double a[VEC], b[VEC];
+  };
+  static __device__ __forceinline__ void acc_zero(Acc& s) {
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) s.a[k] = s.b[k] = 0.0;
+  }
+  // s.a_k += |x_k|^2,  s.b_k += Re(conj(y_k) x_k)
+  static __device__ __forceinline__ void acc_add(Acc& s, const ChunkF64& x, const ChunkF64& y) {
+    if constexpr (CPLX) {
+      s.a[0] += fma(x.v[0], x.v[0], x.v[1] * x.v[1]);
+      s.b[0] += fma(y.v[0], x.v[0], y.v[1] * x.v[1]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        s.a[k] += x.v[k] * x.v[k];
+        s.b[k] += y.v[k] * x.v[k];
+      }
+    }
+  }
+  static __device__ __forceinline__ void acc_out(const Acc& s, double (&A)[VEC], double (&B)[VEC]) {
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) { A[k] = s.a[k]; B[k] = s.b[k]; }
+  }
 };
 
-// acc += h * x for one chunk (h complex when CPLX; conj handled by caller via hi sign)
-template <typename T, bool CPLX>
-__device__ __forceinline__ void mac(T (&acc)[Traits<T>::SC], T hr, T hi, const T (&x)[Traits<T>::SC]) {
-  constexpr int SC = Traits<T>::SC;
-  if constexpr (CPLX) {
-#pragma unroll
-    for (int k = 0; k < SC / 2; ++k) {
-      const T xr = x[2 * k], xi = x[2 * k + 1];
-      acc[2 * k] = fma(hr, xr, acc[2 * k]);
-      acc[2 * k] = fma(-hi, xi, acc[2 * k]);
-      acc[2 * k + 1] = fma(hr, xi, acc[2 * k + 1]);
-      acc[2 * k + 1] = fma(hi, xr, acc[2 * k + 1]);
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < SC; ++k) acc[k] = fma(hr, x[k], acc[k]);
-  }
+// FP32: 32 bytes = 8 floats held as 4 packed pairs.  Complex: p[0] = (re0,
+// re1), p[1] = (re2, re3), p[2] = (im0, im1), p[3] = (im2, im3); real: p[j] =
+// columns (2j, 2j+1).
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {  // a - b
+  return __ffma2_rn(b, f2(-1.0f), a);
 }
+// Kahan step: s += v with compensation c
+__device__ __forceinline__ void kahan2(float2& s, float2& c, float2 v) {
+  const float2 y = sub2(v, c);
+  const float2 t = __fadd2_rn(s, y);
+  c = sub2(sub2(t, s), y);
+  s = t;
+}
+
+template <bool CPLX_>
+struct ChunkF32 {
+  using T = float;
+  static constexpr bool CPLX = CPLX_;
+  static constexpr int SC = 8;
+  static constexpr int VEC = CPLX ? 4 : 8;
+  float2 p[4];
+
+  __device__ __forceinline__ void ld_nc(const float* a) {
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(p[0].x), "=f"(p[0].y), "=f"(p[1].x), "=f"(p[1].y), "=f"(p[2].x),
+                   "=f"(p[2].y), "=f"(p[3].x), "=f"(p[3].y)
+                 : "l"(a));
+  }
+  __device__ __forceinline__ void ld_cs(const float* a) {
+    asm volatile("ld.global.cs.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(p[0].x), "=f"(p[0].y), "=f"(p[1].x), "=f"(p[1].y), "=f"(p[2].x),
+                   "=f"(p[2].y), "=f"(p[3].x), "=f"(p[3].y)
+                 : "l"(a));
+  }
+  __device__ __forceinline__ void st(float* a) const {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(a), "f"(p[0].x),
+                 "f"(p[0].y), "f"(p[1].x), "f"(p[1].y), "f"(p[2].x), "f"(p[2].y), "f"(p[3].x),
+                 "f"(p[3].y)
+                 : "memory");
+  }
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) p[j] = f2(0.0f);
+  }
+  __device__ __forceinline__ void set_neg(const ChunkF32& w) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) p[j] = make_float2(-w.p[j].x, -w.p[j].y);
+  }
+  __device__ __forceinline__ void half() {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) p[j] = __fmul2_rn(p[j], f2(0.5f));
+  }
+  __device__ __forceinline__ void axpy(float d, const ChunkF32& x) {
+    const float2 D = f2(d);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) p[j] = __ffma2_rn(D, x.p[j], p[j]);
+  }
+  __device__ __forceinline__ void cmac(float hr, float hi, const ChunkF32& x) {
+    if constexpr (CPLX) {
+      const float2 H = f2(hr), Hp = f2(hi), Hn = f2(-hi);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        p[j] = __ffma2_rn(H, x.p[j], p[j]);              // re += hr re_x
+        p[j] = __ffma2_rn(Hn, x.p[j + 2], p[j]);         // re -= hi im_x
+        p[j + 2] = __ffma2_rn(H, x.p[j + 2], p[j + 2]);  // im += hr im_x
+        p[j + 2] = __ffma2_rn(Hp, x.p[j], p[j + 2]);     // im += hi re_x
+      }
+    } else {
+      axpy(hr, x);
+    }
+  }
+  struct Acc {
+    float2 a[VEC / 2], ca[VEC / 2], b[VEC / 2], cb[VEC / 2];
+  };
+  static __device__ __forceinline__ void acc_zero(Acc& s) {
+#pragma unroll
+    for (int j = 0; j < VEC / 2; ++j) s.a[j] = s.ca[j] = s.b[j] = s.cb[j] = f2(0.0f);
+  }
+  static __device__ __forceinline__ void acc_add(Acc& s, const ChunkF32& x, const ChunkF32& y) {
+    if constexpr (CPLX) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const float2 a2 = __ffma2_rn(x.p[j + 2], x.p[j + 2], __fmul2_rn(x.p[j], x.p[j]));
+        const float2 b2 = __ffma2_rn(y.p[j + 2], x.p[j + 2], __fmul2_rn(y.p[j], x.p[j]));
+        kahan2(s.a[j], s.ca[j], a2);
+        kahan2(s.b[j], s.cb[j], b2);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        kahan2(s.a[j], s.ca[j], __fmul2_rn(x.p[j], x.p[j]));
+        kahan2(s.b[j], s.cb[j], __fmul2_rn(y.p[j], x.p[j]));
+      }
+    }
+  }
+  static __device__ __forceinline__ void acc_out(const Acc& s, double (&A)[VEC], double (&B)[VEC]) {
+#pragma unroll
+    for (int j = 0; j < VEC / 2; ++j) {
+      A[2 * j] = (double)s.a[j].x - (double)s.ca[j].x;
+      A[2 * j + 1] = (double)s.a[j].y - (double)s.ca[j].y;
+      B[2 * j] = (double)s.b[j].x - (double)s.cb[j].x;
+      B[2 * j + 1] = (double)s.b[j].y - (double)s.cb[j].y;
+    }
+  }
+};
 
 template <typename T>
 __device__ __forceinline__ void scal_from_block(const ScalarBlock* sc, T& hr, T& hi, T& du);
@@ -86,19 +221,117 @@ __device__ __forceinline__ void scal_from_block<double>(const ScalarBlock* sc, d
   hr = sc->hu_re; hi = sc->hu_im; du = sc->du;
 }
 
-// ---------------------------------------------------------------- operators
+// ================================================================ operators
 // Matrix-free hypercubic stencil: forward bond (i, i+e_d) carries the scaled
 // hopping h_{i,d}; the backward bond (i, i-e_d) carries conj(h_{i-e_d,d}).
-template <typename T, bool CPLX, int DIMS, bool HAS_HOP, bool HAS_DS>
+template <class CH, int DIMS, bool HAS_HOP, bool HAS_DS>
 struct StencilOp {
-  static constexpr int SC = Traits<T>::SC;
-  __device__ __forceinline__ void apply(const StepArgs& a, int64_t i64, int c, const T* __restrict__ X,
-                                        const T (&xi)[SC], T (&acc)[SC], T hu_r, T hu_i,
-                                        T du) const {
-    const int i = (int)i64;
-    const T d = HAS_DS ? __ldg(reinterpret_cast<const T*>(a.ds) + i) : du;
+  using T = typename CH::T;
+  static constexpr bool CPLX = CH::CPLX;
+  static constexpr bool kLines = DIMS >= 2;
+
+  // Neighbour offsets along d >= 1 depend only on the lattice line (y, z):
+  // computed once per chunk of passes.
+  struct LineCtx {
+    int row0;                // row of x = 0 on this line
+    int df[DIMS], db[DIMS];  // row deltas of the forward / backward neighbour
+    bool hf[DIMS], hb[DIMS];
+    bool valid;
+  };
+
+  __device__ __forceinline__ LineCtx line_ctx(const StepArgs& a, int line) const {
+    LineCtx k{};
+    k.valid = line < a.lines;
+    k.row0 = line * a.line_len;
+    int co[3] = {0, 0, 0};
+    if constexpr (DIMS == 2) co[1] = line;
+    if constexpr (DIMS == 3) {
+      co[1] = line % a.line_L1;
+      co[2] = line / a.line_L1;
+    }
 #pragma unroll
-    for (int k = 0; k < SC; ++k) acc[k] = fma(d, xi[k], acc[k]);
+    for (int d2 = 1; d2 < DIMS; ++d2) {
+      const int L = a.geom.L[d2], s = a.geom.stride[d2], x = co[d2];
+      const bool per = a.geom.periodic[d2] != 0;
+      k.hf[d2] = (x + 1 < L) || per;
+      k.df[d2] = (x + 1 < L) ? s : (per ? -(L - 1) * s : 0);
+      k.hb[d2] = (x > 0) || per;
+      k.db[d2] = (x > 0) ? -s : (per ? (L - 1) * s : 0);
+    }
+    return k;
+  }
+
+  // The shared core: diagonal, hoppings and the 2*DIMS neighbour rows.
+  __device__ __forceinline__ void core(const StepArgs& a, int i, const int (&jf)[DIMS],
+                                       const int (&jb)[DIMS], const bool (&hf)[DIMS],
+                                       const bool (&hb)[DIMS], const T* __restrict__ Xc,
+                                       const CH& xi, CH& acc, T hu_r, T hu_i, T du) const {
+    const T d = HAS_DS ? __ldg(reinterpret_cast<const T*>(a.ds) + i) : du;
+    acc.axpy(d, xi);
+    T fr[DIMS], fi[DIMS], br[DIMS], bi[DIMS];
+#pragma unroll
+    for (int d2 = 0; d2 < DIMS; ++d2) {
+      if constexpr (HAS_HOP) {
+        const T* hs = reinterpret_cast<const T*>(a.hs);
+        if constexpr (CPLX) {
+          using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+          const T2 f = __ldg(reinterpret_cast<const T2*>(hs) + ((size_t)i * DIMS + d2));
+          const T2 bk = __ldg(reinterpret_cast<const T2*>(hs) + ((size_t)jb[d2] * DIMS + d2));
+          fr[d2] = f.x;
+          fi[d2] = f.y;
+          br[d2] = bk.x;
+          bi[d2] = -bk.y;
+        } else {
+          fr[d2] = __ldg(hs + (size_t)i * DIMS + d2);
+          br[d2] = __ldg(hs + (size_t)jb[d2] * DIMS + d2);
+          fi[d2] = bi[d2] = T(0);
+        }
+      } else {
+        fr[d2] = hu_r; fi[d2] = hu_i; br[d2] = hu_r; bi[d2] = -hu_i;
+      }
+      if (!hf[d2]) { fr[d2] = T(0); fi[d2] = T(0); }
+      if (!hb[d2]) { br[d2] = T(0); bi[d2] = T(0); }
+    }
+    const size_t rowS = (size_t)a.G * CH::SC;
+    CH xf[DIMS], xb[DIMS];
+#pragma unroll
+    for (int d2 = 0; d2 < DIMS; ++d2) {
+      xf[d2].ld_nc(Xc + (size_t)jf[d2] * rowS);
+      xb[d2].ld_nc(Xc + (size_t)jb[d2] * rowS);
+    }
+#pragma unroll
+    for (int d2 = 0; d2 < DIMS; ++d2) {
+      acc.cmac(fr[d2], fi[d2], xf[d2]);
+      acc.cmac(br[d2], bi[d2], xb[d2]);
+    }
+  }
+
+  // Row i at position cx on a line described by k (line traversal).
+  __device__ __forceinline__ void apply_line(const StepArgs& a, int i, int cx, const LineCtx& k,
+                                             const T* __restrict__ Xc, const CH& xi, CH& acc,
+                                             T hu_r, T hu_i, T du) const {
+    int jf[DIMS], jb[DIMS];
+    bool hf[DIMS], hb[DIMS];
+    const int L0 = a.line_len;
+    const bool per0 = a.geom.periodic[0] != 0;
+    hf[0] = (cx + 1 < L0) || per0;
+    jf[0] = (cx + 1 < L0) ? i + 1 : (per0 ? i - (L0 - 1) : i);
+    hb[0] = (cx > 0) || per0;
+    jb[0] = (cx > 0) ? i - 1 : (per0 ? i + (L0 - 1) : i);
+#pragma unroll
+    for (int d2 = 1; d2 < DIMS; ++d2) {
+      jf[d2] = i + k.df[d2];
+      jb[d2] = i + k.db[d2];
+      hf[d2] = k.hf[d2];
+      hb[d2] = k.hb[d2];
+    }
+    core(a, i, jf, jb, hf, hb, Xc, xi, acc, hu_r, hu_i, du);
+  }
+
+  // Row i in natural order: coordinates decoded from the index.
+  __device__ __forceinline__ void apply(const StepArgs& a, int64_t i64, const T* __restrict__ Xc,
+                                        const CH& xi, CH& acc, T hu_r, T hu_i, T du) const {
+    const int i = (int)i64;
     int jf[DIMS], jb[DIMS];
     bool hf[DIMS], hb[DIMS];
     int rem = i;
@@ -113,54 +346,34 @@ struct StencilOp {
       hb[d2] = (x > 0) || per;
       jb[d2] = (x > 0) ? i - s : (per ? i + (L - 1) * s : i);
     }
-    // hoppings
-    T fr[DIMS], fi[DIMS], br[DIMS], bi[DIMS];
-#pragma unroll
-    for (int d2 = 0; d2 < DIMS; ++d2) {
-      if constexpr (HAS_HOP) {
-        const T* hs = reinterpret_cast<const T*>(a.hs);
-        if constexpr (CPLX) {
-          fr[d2] = __ldg(hs + 2 * ((size_t)i * DIMS + d2));
-          fi[d2] = __ldg(hs + 2 * ((size_t)i * DIMS + d2) + 1);
-          br[d2] = __ldg(hs + 2 * ((size_t)jb[d2] * DIMS + d2));
-          bi[d2] = -__ldg(hs + 2 * ((size_t)jb[d2] * DIMS + d2) + 1);
-        } else {
-          fr[d2] = __ldg(hs + (size_t)i * DIMS + d2);
-          br[d2] = __ldg(hs + (size_t)jb[d2] * DIMS + d2);
-          fi[d2] = bi[d2] = T(0);
-        }
-      } else {
-        fr[d2] = hu_r; fi[d2] = hu_i; br[d2] = hu_r; bi[d2] = -hu_i;
-      }
-      if (!hf[d2]) { fr[d2] = T(0); fi[d2] = T(0); }
-      if (!hb[d2]) { br[d2] = T(0); bi[d2] = T(0); }
-    }
-    const int G = a.G;
-    T xf[DIMS][SC], xb[DIMS][SC];
-#pragma unroll
-    for (int d2 = 0; d2 < DIMS; ++d2) {
-      ld16_nc(X + ((size_t)jf[d2] * G + c) * SC, xf[d2]);
-      ld16_nc(X + ((size_t)jb[d2] * G + c) * SC, xb[d2]);
-    }
-#pragma unroll
-    for (int d2 = 0; d2 < DIMS; ++d2) {
-      mac<T, CPLX>(acc, fr[d2], fi[d2], xf[d2]);
-      mac<T, CPLX>(acc, br[d2], bi[d2], xb[d2]);
-    }
+    core(a, i, jf, jb, hf, hb, Xc, xi, acc, hu_r, hu_i, du);
   }
 };
 
 // CSR rows: y_i = du x_i + sum_k vals[k] x_{col[k]}
-template <typename T, bool CPLX>
+template <class CH>
 struct CsrOp {
-  static constexpr int SC = Traits<T>::SC;
-  __device__ __forceinline__ void apply(const StepArgs& a, int64_t i, int c, const T* __restrict__ X,
-                                        const T (&xi)[SC], T (&acc)[SC], T, T, T du) const {
-#pragma unroll
-    for (int k = 0; k < SC; ++k) acc[k] = fma(du, xi[k], acc[k]);
+  using T = typename CH::T;
+  static constexpr bool CPLX = CH::CPLX;
+  static constexpr bool kLines = false;
+  struct LineCtx {};
+  __device__ __forceinline__ void hop(const T* V, int64_t k, T& hr, T& hi) const {
+    if constexpr (CPLX) {
+      using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+      const T2 h = __ldg(reinterpret_cast<const T2*>(V) + k);
+      hr = h.x;
+      hi = h.y;
+    } else {
+      hr = __ldg(V + k);
+      hi = T(0);
+    }
+  }
+  __device__ __forceinline__ void apply(const StepArgs& a, int64_t i, const T* __restrict__ Xc,
+                                        const CH& xi, CH& acc, T, T, T du) const {
+    acc.axpy(du, xi);
     const int64_t k0 = __ldg(a.rowptr + i), k1 = __ldg(a.rowptr + i + 1);
     const T* V = reinterpret_cast<const T*>(a.vals);
-    const int G = a.G;
+    const size_t rowS = (size_t)a.G * CH::SC;
     int64_t k = k0;
     for (; k + 4 <= k1; k += 4) {
       int j[4];
@@ -168,43 +381,31 @@ struct CsrOp {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         j[u] = __ldg(a.col + k + u);
-        if constexpr (CPLX) {
-          hr[u] = __ldg(V + 2 * (k + u));
-          hi[u] = __ldg(V + 2 * (k + u) + 1);
-        } else {
-          hr[u] = __ldg(V + k + u);
-          hi[u] = T(0);
-        }
+        hop(V, k + u, hr[u], hi[u]);
       }
-      T xj[4][SC];
+      CH xj[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) ld16_nc(X + ((size_t)j[u] * G + c) * SC, xj[u]);
+      for (int u = 0; u < 4; ++u) xj[u].ld_nc(Xc + (size_t)j[u] * rowS);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) mac<T, CPLX>(acc, hr[u], hi[u], xj[u]);
+      for (int u = 0; u < 4; ++u) acc.cmac(hr[u], hi[u], xj[u]);
     }
     for (; k < k1; ++k) {
       const int j = __ldg(a.col + k);
       T hr, hi;
-      if constexpr (CPLX) {
-        hr = __ldg(V + 2 * k);
-        hi = __ldg(V + 2 * k + 1);
-      } else {
-        hr = __ldg(V + k);
-        hi = T(0);
-      }
-      T xj[SC];
-      ld16_nc(X + ((size_t)j * G + c) * SC, xj);
-      mac<T, CPLX>(acc, hr, hi, xj);
+      hop(V, k, hr, hi);
+      CH xj;
+      xj.ld_nc(Xc + (size_t)j * rowS);
+      acc.cmac(hr, hi, xj);
     }
   }
 };
 
-// ---------------------------------------------------------------- the fused step
-template <typename T, bool CPLX, int MODE, class OP>
-__global__ void __launch_bounds__(256) cheb_step_kernel(const StepArgs a) {
-  constexpr int SC = Traits<T>::SC;
-  constexpr int VEC = CPLX ? SC / 2 : SC;
-  constexpr bool F32 = sizeof(T) == 4;
+// ================================================================ the fused step
+template <class CH, int MODE, class OP>
+__global__ void __launch_bounds__(256, KPM_STEP_MIN_BLOCKS) cheb_step_kernel(const StepArgs a) {
+  using T = typename CH::T;
+  constexpr int SC = CH::SC;
+  constexpr int VEC = CH::VEC;
   const OP op;
   const int Gt = a.Gt;
   const int t = threadIdx.x;
@@ -212,77 +413,77 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(const StepArgs a) {
   const int c = blockIdx.y * Gt + cl;     // chunk within the row
   const int q = t / Gt;
   const int spi = blockDim.x / Gt;
-  const int G = a.G;
-  const int64_t s0 = (int64_t)blockIdx.x * a.sites_per_cta;
-  const int64_t s1 = min(s0 + (int64_t)a.sites_per_cta, a.n);
-  const T* __restrict__ X = reinterpret_cast<const T*>(a.x);
-  const T* W = reinterpret_cast<const T*>(a.w);
-  T* Y = reinterpret_cast<T*>(a.y);
+  const size_t rowS = (size_t)a.G * SC;
+  const T* __restrict__ Xc = reinterpret_cast<const T*>(a.x) + (size_t)c * SC;
+  const T* Wc = reinterpret_cast<const T*>(a.w) + (size_t)c * SC;
+  T* Yc = reinterpret_cast<T*>(a.y) + (size_t)c * SC;
   T hu_r, hu_i, du;
   scal_from_block<T>(a.sc, hu_r, hu_i, du);
 
-  double dA[VEC], dB[VEC];
-  T fA[VEC], fB[VEC];
-#pragma unroll
-  for (int k = 0; k < VEC; ++k) { dA[k] = 0.0; dB[k] = 0.0; fA[k] = T(0); fB[k] = T(0); }
-  int cnt = 0;
+  typename CH::Acc s;
+  CH::acc_zero(s);
 
-  for (int64_t i = s0 + q; i < s1; i += spi) {
-    const size_t base = ((size_t)i * G + c) * SC;
-    T xi[SC], acc[SC];
-    ld16_nc(X + base, xi);
-    if constexpr (MODE == MODE_STEP) {
-      T wv[SC];
-      ld16_cs(W + base, wv);
-#pragma unroll
-      for (int k = 0; k < SC; ++k) acc[k] = -wv[k];
-    } else {
-#pragma unroll
-      for (int k = 0; k < SC; ++k) acc[k] = T(0);
-    }
-    op.apply(a, i, c, X, xi, acc, hu_r, hu_i, du);
-    if constexpr (MODE == MODE_FIRST) {
-#pragma unroll
-      for (int k = 0; k < SC; ++k) acc[k] *= T(0.5);
-    }
-    st16(Y + base, acc);
-    if constexpr (MODE != MODE_SPMV) {
-#pragma unroll
-      for (int k = 0; k < VEC; ++k) {
-        T a2, b2;
-        if constexpr (CPLX) {
-          a2 = fma(xi[2 * k], xi[2 * k], xi[2 * k + 1] * xi[2 * k + 1]);
-          b2 = fma(acc[2 * k], xi[2 * k], acc[2 * k + 1] * xi[2 * k + 1]);
-        } else {
-          a2 = xi[k] * xi[k];
-          b2 = acc[k] * xi[k];
-        }
-        if constexpr (F32) {
-          fA[k] += a2;
-          fB[k] += b2;
-        } else {
-          dA[k] += a2;
-          dB[k] += b2;
-        }
+  const int Lx = a.line_len;
+  const int u = a.chunk;
+  const int64_t nchunks = (a.passes + u - 1) / u;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int64_t p_beg = ch * (int64_t)u;
+    const int np = (int)min((int64_t)u, a.passes - p_beg);
+    // line traversal: x and the line context advance incrementally
+    int cx = 0, blk = 0;
+    typename OP::LineCtx lctx{};
+    if constexpr (OP::kLines) {
+      if (Lx > 0) {
+        const int pb = (int)p_beg;  // passes < 2^31
+        blk = pb / Lx;
+        cx = pb - blk * Lx;
+        lctx = op.line_ctx(a, blk * spi + q);
       }
-      if constexpr (F32) {
-        if (++cnt == PROMOTE) {
-#pragma unroll
-          for (int k = 0; k < VEC; ++k) {
-            dA[k] += (double)fA[k]; dB[k] += (double)fB[k];
-            fA[k] = T(0); fB[k] = T(0);
+    }
+    for (int jp = 0; jp < np; ++jp) {
+      int64_t i;
+      bool line_mode = false;
+      if constexpr (OP::kLines) {
+        if (Lx > 0) {
+          line_mode = true;
+          if (jp > 0 && ++cx == Lx) {
+            cx = 0;
+            ++blk;
+            lctx = op.line_ctx(a, blk * spi + q);
           }
-          cnt = 0;
+          if (!lctx.valid) continue;
+          i = lctx.row0 + cx;
         }
       }
+      if (!line_mode) {
+        i = (p_beg + jp) * spi + q;
+        if (i >= a.n) continue;
+      }
+      const size_t base = (size_t)i * rowS;
+      CH xi, acc;
+      xi.ld_nc(Xc + base);
+      if constexpr (MODE == MODE_STEP) {
+        CH wv;
+        wv.ld_cs(Wc + base);
+        acc.set_neg(wv);
+      } else {
+        acc.zero();
+      }
+      if constexpr (OP::kLines) {
+        if (line_mode) op.apply_line(a, (int)i, cx, lctx, Xc, xi, acc, hu_r, hu_i, du);
+        else op.apply(a, i, Xc, xi, acc, hu_r, hu_i, du);
+      } else {
+        op.apply(a, i, Xc, xi, acc, hu_r, hu_i, du);
+      }
+      if constexpr (MODE == MODE_FIRST) acc.half();
+      acc.st(Yc + base);
+      if constexpr (MODE != MODE_SPMV) CH::acc_add(s, xi, acc);
     }
   }
   if constexpr (MODE == MODE_SPMV) return;
   else {
-    if constexpr (F32) {
-#pragma unroll
-      for (int k = 0; k < VEC; ++k) { dA[k] += (double)fA[k]; dB[k] += (double)fB[k]; }
-    }
+    double dA[VEC], dB[VEC];
+    CH::acc_out(s, dA, dB);
     extern __shared__ double red[];
     const int lane = t & 31, warp = t >> 5;
     bool rep;
@@ -314,36 +515,31 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(const StepArgs a) {
     const int Rp = a.Rp, Rt = Gt * VEC;
     for (int o = t; o < 2 * Rt; o += blockDim.x) {
       const int which = o / Rt, col = o % Rt, cc = col / VEC, k = col % VEC;
-      double s = 0.0;
-      for (int qq = 0; qq < nq; ++qq) s += red[((qq * Gt + cc) * 2 + which) * VEC + k];
-      a.partial[(size_t)blockIdx.x * 2 * Rp + which * Rp + blockIdx.y * Rt + col] = s;
+      double sum = 0.0;
+      for (int qq = 0; qq < nq; ++qq) sum += red[((qq * Gt + cc) * 2 + which) * VEC + k];
+      a.partial[(size_t)blockIdx.x * 2 * Rp + which * Rp + blockIdx.y * Rt + col] = sum;
     }
   }
 }
 
-inline size_t step_smem_bytes(int G, int block, int vec) {
-  const int nq = G < 32 ? block / 32 : block / G;
-  return (size_t)nq * G * 2 * vec * sizeof(double);
+inline size_t step_smem_bytes(int Gt, int block, int vec) {
+  const int nq = Gt < 32 ? block / 32 : block / Gt;
+  return (size_t)nq * Gt * 2 * vec * sizeof(double);
 }
 
-template <typename T, bool CPLX, int MODE, class OP>
+template <class CH, int MODE, class OP>
 cudaError_t launch_one(const StepArgs& a, const LaunchCfg& cfg, cudaStream_t st) {
-  constexpr int SC = Traits<T>::SC;
-  constexpr int VEC = CPLX ? SC / 2 : SC;
-  const size_t smem = MODE == MODE_SPMV ? 0 : step_smem_bytes(a.Gt, cfg.block, VEC);
-  cheb_step_kernel<T, CPLX, MODE, OP><<<dim3(cfg.grid, a.G / a.Gt), cfg.block, smem, st>>>(a);
+  const size_t smem = MODE == MODE_SPMV ? 0 : step_smem_bytes(a.Gt, cfg.block, CH::VEC);
+  cheb_step_kernel<CH, MODE, OP><<<dim3(cfg.grid, a.G / a.Gt), cfg.block, smem, st>>>(a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
-template <typename T, bool CPLX, int MODE, class OP>
-int occupancy_one(int block, int G) {
-  constexpr int SC = Traits<T>::SC;
-  constexpr int VEC = CPLX ? SC / 2 : SC;
+template <class CH, int MODE, class OP>
+int occupancy_one(int block, int Gt) {
   int nb = 0;
-  const size_t smem = MODE == MODE_SPMV ? 0 : step_smem_bytes(G, block, VEC);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cheb_step_kernel<T, CPLX, MODE, OP>, block,
-                                                smem);
+  const size_t smem = MODE == MODE_SPMV ? 0 : step_smem_bytes(Gt, block, CH::VEC);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cheb_step_kernel<CH, MODE, OP>, block, smem);
   return nb;
 }
 

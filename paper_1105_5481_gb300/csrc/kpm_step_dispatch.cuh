@@ -1,35 +1,31 @@
-// Selects the operator specialisation of the fused step for one scalar type.
+// Selects the operator specialisation of the fused step for one chunk policy.
 #pragma once
 
 #include "kpm_step.cuh"
 
 namespace kpm {
 
-template <typename T, bool CPLX, int MODE, class F>
+template <class CH, class F>
 auto visit_op(bool stencil, const StepArgs& a, F&& f) {
-  if (!stencil) return f.template operator()<CsrOp<T, CPLX>>();
+  if (!stencil) return f.template operator()<CsrOp<CH>>();
   const bool hh = a.hs != nullptr, hd = a.ds != nullptr;
 #define KPM_CASE(D, H, S) \
-  if (a.geom.dims == D && hh == H && hd == S) return f.template operator()<StencilOp<T, CPLX, D, H, S>>();
+  if (a.geom.dims == D && hh == H && hd == S) return f.template operator()<StencilOp<CH, D, H, S>>();
   KPM_CASE(3, true, false) KPM_CASE(3, true, true) KPM_CASE(3, false, false) KPM_CASE(3, false, true)
   KPM_CASE(2, true, false) KPM_CASE(2, true, true) KPM_CASE(2, false, false) KPM_CASE(2, false, true)
   KPM_CASE(1, true, false) KPM_CASE(1, true, true) KPM_CASE(1, false, false)
 #undef KPM_CASE
-  return f.template operator()<StencilOp<T, CPLX, 1, false, true>>();
+  return f.template operator()<StencilOp<CH, 1, false, true>>();
 }
 
-template <typename T, bool CPLX, int MODE>
+template <class CH, int MODE>
 cudaError_t run_mode(bool stencil, const StepArgs& a, const LaunchCfg& cfg, cudaStream_t st) {
-  return visit_op<T, CPLX, MODE>(stencil, a, [&]<class OP>() {
-    return launch_one<T, CPLX, MODE, OP>(a, cfg, st);
-  });
+  return visit_op<CH>(stencil, a, [&]<class OP>() { return launch_one<CH, MODE, OP>(a, cfg, st); });
 }
 
-template <typename T, bool CPLX, int MODE>
+template <class CH, int MODE>
 int occ_mode(bool stencil, const StepArgs& a, int block) {
-  return visit_op<T, CPLX, MODE>(stencil, a, [&]<class OP>() {
-    return occupancy_one<T, CPLX, MODE, OP>(block, a.Gt);
-  });
+  return visit_op<CH>(stencil, a, [&]<class OP>() { return occupancy_one<CH, MODE, OP>(block, a.Gt); });
 }
 
 }  // namespace kpm

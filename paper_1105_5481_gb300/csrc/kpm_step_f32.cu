@@ -1,4 +1,5 @@
-// FP32-vector instantiations of the fused Chebyshev step (stencil and CSR).
+// FP32-vector instantiations of the fused Chebyshev step (stencil and CSR):
+// 32-byte chunks, packed f32x2 arithmetic, FP64 moment sums.
 #include "kpm_step_dispatch.cuh"
 
 namespace kpm {
@@ -7,15 +8,15 @@ cudaError_t launch_step_f32(bool stencil, bool cplx, StepMode mode, const StepAr
                             const LaunchCfg& cfg, cudaStream_t st) {
   if (mode == MODE_SPMV) return cudaErrorInvalidValue;  // the Lanczos product is FP64 only
   if (cplx)
-    return mode == MODE_FIRST ? run_mode<float, true, MODE_FIRST>(stencil, a, cfg, st)
-                              : run_mode<float, true, MODE_STEP>(stencil, a, cfg, st);
-  return mode == MODE_FIRST ? run_mode<float, false, MODE_FIRST>(stencil, a, cfg, st)
-                            : run_mode<float, false, MODE_STEP>(stencil, a, cfg, st);
+    return mode == MODE_FIRST ? run_mode<ChunkF32<true>, MODE_FIRST>(stencil, a, cfg, st)
+                              : run_mode<ChunkF32<true>, MODE_STEP>(stencil, a, cfg, st);
+  return mode == MODE_FIRST ? run_mode<ChunkF32<false>, MODE_FIRST>(stencil, a, cfg, st)
+                            : run_mode<ChunkF32<false>, MODE_STEP>(stencil, a, cfg, st);
 }
 
 int occ_step_f32(bool stencil, bool cplx, const StepArgs& a, int block) {
-  return cplx ? occ_mode<float, true, MODE_STEP>(stencil, a, block)
-              : occ_mode<float, false, MODE_STEP>(stencil, a, block);
+  return cplx ? occ_mode<ChunkF32<true>, MODE_STEP>(stencil, a, block)
+              : occ_mode<ChunkF32<false>, MODE_STEP>(stencil, a, block);
 }
 
 }  // namespace kpm

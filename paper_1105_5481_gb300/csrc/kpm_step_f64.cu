@@ -8,21 +8,21 @@ cudaError_t launch_step_f64(bool stencil, bool cplx, StepMode mode, const StepAr
                             const LaunchCfg& cfg, cudaStream_t st) {
   if (cplx) {
     switch (mode) {
-      case MODE_FIRST: return run_mode<double, true, MODE_FIRST>(stencil, a, cfg, st);
-      case MODE_STEP: return run_mode<double, true, MODE_STEP>(stencil, a, cfg, st);
-      default: return run_mode<double, true, MODE_SPMV>(stencil, a, cfg, st);
+      case MODE_FIRST: return run_mode<ChunkF64<true>, MODE_FIRST>(stencil, a, cfg, st);
+      case MODE_STEP: return run_mode<ChunkF64<true>, MODE_STEP>(stencil, a, cfg, st);
+      default: return run_mode<ChunkF64<true>, MODE_SPMV>(stencil, a, cfg, st);
     }
   }
   switch (mode) {
-    case MODE_FIRST: return run_mode<double, false, MODE_FIRST>(stencil, a, cfg, st);
-    case MODE_STEP: return run_mode<double, false, MODE_STEP>(stencil, a, cfg, st);
-    default: return run_mode<double, false, MODE_SPMV>(stencil, a, cfg, st);
+    case MODE_FIRST: return run_mode<ChunkF64<false>, MODE_FIRST>(stencil, a, cfg, st);
+    case MODE_STEP: return run_mode<ChunkF64<false>, MODE_STEP>(stencil, a, cfg, st);
+    default: return run_mode<ChunkF64<false>, MODE_SPMV>(stencil, a, cfg, st);
   }
 }
 
 int occ_step_f64(bool stencil, bool cplx, const StepArgs& a, int block) {
-  return cplx ? occ_mode<double, true, MODE_STEP>(stencil, a, block)
-              : occ_mode<double, false, MODE_STEP>(stencil, a, block);
+  return cplx ? occ_mode<ChunkF64<true>, MODE_STEP>(stencil, a, block)
+              : occ_mode<ChunkF64<false>, MODE_STEP>(stencil, a, block);
 }
 
 }  // namespace kpm
