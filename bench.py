@@ -45,6 +45,31 @@ def peaks():
         return 6800.0, "fallback"
 
 
+STEP_SOURCES = ["paper_1105_5481_gb300/csrc/kpm_step.cuh",
+                "paper_1105_5481_gb300/csrc/kpm_step_dispatch.cuh",
+                "paper_1105_5481_gb300/csrc/kpm_step_f32.cu",
+                "paper_1105_5481_gb300/csrc/kpm_internal.h"]
+# DRAM bytes (read + write) per fused-step launch from one ncu capture, keyed by
+# workload, with the hash of the kernel sources it was taken on
+# (profiles/cheb_step_fp32_cubic_spin_L64.md); reported only while the hash matches.
+MEASURED_TRAFFIC = {"cubic_spin_L64": (380.48e6, "8da0b5092cc32a8d")}
+
+
+def step_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in STEP_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload):
+    t = MEASURED_TRAFFIC.get(workload)
+    return t[0] if t and t[1] == step_source_hash() else None
+
+
 # FP64 FMA issue rate of GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flop at the
 # sustained clock.  A dependent-chain probe measured 1.20 TFLOP/s (1.97 GHz).
 FP64_PEAK_TFLOPS = 1.20
@@ -166,7 +191,12 @@ def reference_arm(args):
     return 0
 
 
-def profile_run(prec):
+def csr_handle(K, w):
+    rp, col, val = K.kpm_stencil_to_csr(3, w["L"], hop=w["hop"], bond_mask=w["mask"], complex_=True)
+    return K.kpm_create_csr(rp.size - 1, rp, col, val, complex_=True)
+
+
+def profile_run(prec, workload):
     """Two solves of the workload with Gershgorin bounds (no Lanczos products, so
     the only fused-step launches are those of the two solves)."""
     import torch
@@ -176,13 +206,76 @@ def profile_run(prec):
     from paper_1105_5481_gb300 import kpm as K
 
     B.build()
-    w = I.workload("cubic_spin_L64")
-    with K.kpm_create_stencil(3, w["L"], hop=w["hop"], complex_=True) as h:
+    w = I.workload(workload)
+    if workload == "csr_spin_dilute_L160":
+        h = csr_handle(K, w)
+        M, R = 64, w["R"]   # a short solve: the fused steps are identical at any M
+    else:
+        h = K.kpm_create_stencil(3, w["L"], hop=w["hop"], complex_=True)
+        M, R = WORKLOAD["M"], WORKLOAD["R"]
+    with h:
         _, _, a, b = K.kpm_bounds(h, 0, WORKLOAD["pad_eps"])
         for i in range(2):
-            mu = K.kpm_moments(h, WORKLOAD["M"], WORKLOAD["R"], a, b, seed=1000 + i, precision=prec)
+            mu = K.kpm_moments(h, M, R, a, b, seed=1000 + i, precision=prec)
         torch.cuda.synchronize()
-    print(json.dumps({"profile": prec, "mu0": float(mu[0]), "mu2": float(mu[2])}))
+    print(json.dumps({"profile": prec, "workload": workload, "mu0": float(mu[0]), "mu2": float(mu[2])}))
+    return 0
+
+
+def csr_leg(args):
+    """The large diluted CSR lattice: one solve per step (a JSON line of its own)."""
+    import torch
+
+    from paper_1105_5481_gb300 import build as B
+    from paper_1105_5481_gb300 import inputs as I
+    from paper_1105_5481_gb300 import kpm as K
+
+    B.build()
+    w = I.workload("csr_spin_dilute_L160")
+    N, R, M = int(np.prod(w["L"])), w["R"], w["M"]
+    h = csr_handle(K, w)
+    nnz = K.kpm_info(h)["nnz"]
+    emin, emax, a, b = K.kpm_bounds(h, WORKLOAD["lanczos_steps"], WORKLOAD["pad_eps"], seed=6)
+    stream = torch.cuda.Stream()
+    mu_d = torch.empty(M, dtype=torch.float64, device="cuda")
+    E_d = torch.empty(w["K"], dtype=torch.float64, device="cuda")
+    rho_d = torch.empty(w["K"], dtype=torch.float64, device="cuda")
+    mu_chk = K.kpm_moments(h, M, R, a, b, seed=1, precision="fp32", stream=stream)
+    assert abs(mu_chk[0] - 1.0) < 1e-5 and np.all(np.abs(mu_chk) <= 1 + 1e-5)
+    steps = min(args.steps, 3)
+    for i in range(min(args.warmup, 3)):
+        K.kpm_moments(h, M, R, a, b, seed=10 + i, precision="fp32", out=mu_d, stream=stream)
+    stream.synchronize()
+    l0 = K.kpm_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record(stream)
+        for i in range(steps):
+            K.kpm_moments(h, M, R, a, b, seed=100 + i, precision="fp32", out=mu_d, stream=stream)
+            K.kpm_dos(mu_d, a, b, w["K"], "jackson", E=E_d, rho=rho_d, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    chain_ms, nsteps = K.kpm_step_timing(h)
+    bytes_step = 3 * N * R * 8 + nnz * (8 + 4) + 8 * (N + 1)
+    hbm, peak_kind = peaks()
+    ach = bytes_step / (chain_ms / nsteps / 1e3) / 1e9
+    print(json.dumps({
+        "metric": METRIC, "value": nnz * R * M / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": steps, "warmup": min(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 vectors, f64 moments",
+        "data": "synthetic",
+        "config": {"workload": "csr_spin_dilute_L160",
+                   "lattice": "3D cubic L=160 periodic, spin hoppings, 10% bond dilution, CSR",
+                   "N": N, "nnz": nnz, "R": R, "M": M, "K": w["K"],
+                   "bounds": {"emin": emin, "emax": emax, "a": a, "b": b},
+                   "l2": "inputs larger than L2"},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "traffic": None, "bytes_per_launch": bytes_step,
+                     "launch_ms": chain_ms / nsteps, "peak_kind": peak_kind},
+        "gpu_launches": K.kpm_kernel_launches() - l0, "clocks": clk.summary()}))
+    h.close()
     return 0
 
 
@@ -194,6 +287,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="cubic_spin_L64",
+                    choices=["cubic_spin_L64", "csr_spin_dilute_L160"],
+                    help="cubic_spin_L64 (default, the headline) or the large diluted CSR "
+                         "lattice (L=160, N=4.1M, R=32, M=4096, FP32 vectors)")
     ap.add_argument("--profile", default=None, choices=["fp32", "fp64"],
                     help="run two solves of the workload at the given precision and exit "
                          "(a short command for ncu captures of the fused step)")
@@ -201,7 +298,9 @@ def main():
     if args.impl == "reference":
         return reference_arm(args)
     if args.profile:
-        return profile_run(args.profile)
+        return profile_run(args.profile, args.workload)
+    if args.workload == "csr_spin_dilute_L160":
+        return csr_leg(args)
 
     import torch
 
@@ -329,7 +428,7 @@ def main():
                        "l2": "inputs larger than L2 (two 134 MB vector blocks)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s",
-                         "frac": ach32 / hbm, "traffic": None,
+                         "frac": ach32 / hbm, "traffic": measured_traffic(WORKLOAD["name"]),
                          "kernel": "cheb_step_kernel<float, complex, STEP, StencilOp<3,hop>>",
                          "bytes_per_launch": bytes32, "launch_ms": step_ms32,
                          "peak_kind": f"{peak_kind} (copy bandwidth)"},

@@ -111,6 +111,11 @@ StepArgs base_args(const kpm_handle_s* h, int slot, int Rp, int G) {
   if (h->stencil) {
     a.hs = h->has_hop ? h->d_hs[slot] : nullptr;
     a.ds = h->has_onsite ? h->d_ds[slot] : nullptr;
+  } else if (h->ell_w > 0) {
+    a.rowptr = nullptr;
+    a.col = h->d_ell_col;
+    a.vals = h->d_vals[slot];
+    a.ell_w = h->ell_w;
   } else {
     a.rowptr = h->d_rowptr;
     a.col = h->d_col;
@@ -177,7 +182,8 @@ kpm_status ensure_scaled(kpm_handle_s* h, int slot, bool fp32) {
     }
   } else if (!h->d_vals[slot] && h->nnz > 0) {
     void* p = nullptr;
-    KPM_CUDA(cudaMalloc(&p, (size_t)h->nnz * c * s));
+    const size_t entries = h->ell_w > 0 ? (size_t)h->n * h->ell_w : (size_t)h->nnz;
+    KPM_CUDA(cudaMalloc(&p, entries * c * s));
     h->d_vals[slot] = p;
   }
   return KPM_OK;
@@ -188,6 +194,9 @@ cudaError_t prescale(kpm_handle_s* h, int slot, bool fp32, bool lanczos, cudaStr
     return launch_prescale_stencil(fp32, h->cplx, h->n, h->geom.dims, h->d_onsite, h->d_hop,
                                    h->t_re, h->t_im, h->d_prm, lanczos, h->d_hs[slot],
                                    h->d_ds[slot], h->d_sc + slot, st);
+  if (h->ell_w > 0)
+    return launch_prescale_csr(fp32, h->cplx, h->n * h->ell_w, h->d_ell_val, h->d_prm, lanczos,
+                               h->d_vals[slot], h->d_sc + slot, st);
   return launch_prescale_csr(fp32, h->cplx, h->nnz, h->d_val, h->d_prm, lanczos,
                              h->d_vals[slot], h->d_sc + slot, st);
 }
@@ -215,6 +224,8 @@ void destroy_handle(kpm_handle_s* h) {
   dfree(h->d_rowptr);
   dfree(h->d_col);
   dfree(h->d_val);
+  dfree(h->d_ell_col);
+  dfree(h->d_ell_val);
   for (int i = 0; i < 3; ++i) {
     dfree(h->d_hs[i]);
     dfree(h->d_ds[i]);
@@ -386,6 +397,34 @@ kpm_status kpm_create_csr(int64_t n, const int64_t* rowptr, const int32_t* col, 
   if (e == cudaSuccess && nnz)
     e = cudaMemcpy(h->d_val, val, nnz * c * sizeof(double), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { destroy_handle(h); return cuda_fail(e, "copy CSR"); }
+  // Short rows: keep a padded ELL copy for the fused step (fixed trip count, no
+  // row-pointer indirection).  Width = longest row rounded up to even, used when
+  // it is at most 8 and the padding at most doubles the stored entries.
+  int64_t wmax = 0;
+  for (int64_t i = 0; i < n; ++i) wmax = std::max(wmax, rowptr[i + 1] - rowptr[i]);
+  const int64_t W = std::max<int64_t>(2, (wmax + 1) / 2 * 2);
+  if (wmax <= 8 && n * W <= 2 * std::max<int64_t>(nnz, 1)) {
+    std::vector<int32_t> ec((size_t)n * W);
+    std::vector<double> ev((size_t)n * W * c, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t k = 0;
+      for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q, ++k) {
+        ec[(size_t)i * W + k] = col[q];
+        for (int z = 0; z < c; ++z) ev[((size_t)i * W + k) * c + z] = val[q * c + z];
+      }
+      for (; k < W; ++k) ec[(size_t)i * W + k] = (int32_t)i;  // value stays 0
+    }
+    if ((st = dalloc(&h->d_ell_col, ec.size())) != KPM_OK ||
+        (st = dalloc(&h->d_ell_val, ev.size())) != KPM_OK) {
+      destroy_handle(h);
+      return st;
+    }
+    e = cudaMemcpy(h->d_ell_col, ec.data(), ec.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h->d_ell_val, ev.data(), ev.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { destroy_handle(h); return cuda_fail(e, "copy ELL"); }
+    h->ell_w = (int)W;
+  }
   *out = h;
   return KPM_OK;
 }

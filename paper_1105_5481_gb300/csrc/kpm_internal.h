@@ -76,8 +76,9 @@ struct StepArgs {
   const void* ds;    // stencil scaled diagonal [N] (T), NULL => uniform
   StencilGeom geom;
   const int64_t* rowptr;  // CSR
-  const int32_t* col;
-  const void* vals;       // CSR scaled values (T or complex<T>)
+  const int32_t* col;     // CSR column indices, or ELL [n][ell_w]
+  const void* vals;       // CSR / ELL scaled values (T or complex<T>)
+  int ell_w;              // > 0: padded ELL rows of this width (col/vals are ELL)
   // Traversal.  The rows are visited in passes of Q = (threads / Gt) rows,
   // one row per thread group.  line_len == 0: pass P covers rows P*Q .. P*Q+Q-1
   // (natural order).  Otherwise pass P covers x = P % line_len on the Q
@@ -174,6 +175,10 @@ struct kpm_handle_s {
   int64_t* d_rowptr = nullptr;
   int32_t* d_col = nullptr;
   double* d_val = nullptr;      // FP64 raw
+  // padded ELL copy used by the fused step when rows are short (ell_w > 0)
+  int ell_w = 0;
+  int32_t* d_ell_col = nullptr;
+  double* d_ell_val = nullptr;  // FP64 raw, [n][ell_w] (x2 complex)
   // scaled operator copies: [0] = KPM FP64, [1] = KPM FP32, [2] = Lanczos FP64
   void* d_hs[3] = {nullptr, nullptr, nullptr};
   void* d_ds[3] = {nullptr, nullptr, nullptr};

@@ -28,9 +28,13 @@
 
 #include "kpm_internal.h"
 
-// Minimum resident CTAs per SM requested from the register allocator.
+// Minimum resident CTAs per SM requested from the register allocator
+// (stencil steps; CSR/ELL steps).
 #ifndef KPM_STEP_MIN_BLOCKS
 #define KPM_STEP_MIN_BLOCKS 2
+#endif
+#ifndef KPM_SPARSE_MIN_BLOCKS
+#define KPM_SPARSE_MIN_BLOCKS 3
 #endif
 
 namespace kpm {
@@ -229,6 +233,7 @@ struct StencilOp {
   using T = typename CH::T;
   static constexpr bool CPLX = CH::CPLX;
   static constexpr bool kLines = DIMS >= 2;
+  static constexpr int kMinBlocks = KPM_STEP_MIN_BLOCKS;
 
   // Neighbour offsets along d >= 1 depend only on the lattice line (y, z):
   // computed once per chunk of passes.
@@ -356,6 +361,7 @@ struct CsrOp {
   using T = typename CH::T;
   static constexpr bool CPLX = CH::CPLX;
   static constexpr bool kLines = false;
+  static constexpr int kMinBlocks = KPM_SPARSE_MIN_BLOCKS;
   struct LineCtx {};
   __device__ __forceinline__ void hop(const T* V, int64_t k, T& hr, T& hi) const {
     if constexpr (CPLX) {
@@ -400,9 +406,67 @@ struct CsrOp {
   }
 };
 
+// Padded ELL rows (built by the library from a CSR with short rows): row i
+// holds exactly W (even) entries col[i*W + k], vals[i*W + k]; padding entries
+// point at row i with value 0.  No row pointer, fixed trip count, and every
+// neighbour load of the row is issued in one batch.
+template <class CH, int W>
+struct EllOp {
+  using T = typename CH::T;
+  static constexpr bool CPLX = CH::CPLX;
+  static constexpr bool kLines = false;
+  static constexpr int kMinBlocks = KPM_SPARSE_MIN_BLOCKS;
+  struct LineCtx {};
+  __device__ __forceinline__ void apply(const StepArgs& a, int64_t i, const T* __restrict__ Xc,
+                                        const CH& xi, CH& acc, T, T, T du) const {
+    acc.axpy(du, xi);
+    const int2* cp = reinterpret_cast<const int2*>(a.col + (size_t)i * W);
+    int j[W];
+    T hr[W], hi[W];
+#pragma unroll
+    for (int k = 0; k < W / 2; ++k) {
+      const int2 c2 = __ldg(cp + k);
+      j[2 * k] = c2.x;
+      j[2 * k + 1] = c2.y;
+    }
+    if constexpr (CPLX) {
+      using T4 = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
+      if constexpr (sizeof(T) == 4) {
+        const float4* vp = reinterpret_cast<const float4*>(a.vals) + (size_t)i * (W / 2);
+#pragma unroll
+        for (int k = 0; k < W / 2; ++k) {
+          const float4 v = __ldg(vp + k);
+          hr[2 * k] = v.x; hi[2 * k] = v.y; hr[2 * k + 1] = v.z; hi[2 * k + 1] = v.w;
+        }
+      } else {
+        const double2* vp = reinterpret_cast<const double2*>(a.vals) + (size_t)i * W;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          const double2 v = __ldg(vp + k);
+          hr[k] = v.x; hi[k] = v.y;
+        }
+      }
+      (void)sizeof(T4);
+    } else {
+      const T* vp = reinterpret_cast<const T*>(a.vals) + (size_t)i * W;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        hr[k] = __ldg(vp + k);
+        hi[k] = T(0);
+      }
+    }
+    const size_t rowS = (size_t)a.G * CH::SC;
+    CH xj[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) xj[k].ld_nc(Xc + (size_t)j[k] * rowS);
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc.cmac(hr[k], hi[k], xj[k]);
+  }
+};
+
 // ================================================================ the fused step
 template <class CH, int MODE, class OP>
-__global__ void __launch_bounds__(256, KPM_STEP_MIN_BLOCKS) cheb_step_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(256, OP::kMinBlocks) cheb_step_kernel(const StepArgs a) {
   using T = typename CH::T;
   constexpr int SC = CH::SC;
   constexpr int VEC = CH::VEC;

@@ -7,7 +7,15 @@ namespace kpm {
 
 template <class CH, class F>
 auto visit_op(bool stencil, const StepArgs& a, F&& f) {
-  if (!stencil) return f.template operator()<CsrOp<CH>>();
+  if (!stencil) {
+    switch (a.ell_w) {
+      case 2: return f.template operator()<EllOp<CH, 2>>();
+      case 4: return f.template operator()<EllOp<CH, 4>>();
+      case 6: return f.template operator()<EllOp<CH, 6>>();
+      case 8: return f.template operator()<EllOp<CH, 8>>();
+      default: return f.template operator()<CsrOp<CH>>();
+    }
+  }
   const bool hh = a.hs != nullptr, hd = a.ds != nullptr;
 #define KPM_CASE(D, H, S) \
   if (a.geom.dims == D && hh == H && hd == S) return f.template operator()<StencilOp<CH, D, H, S>>();

@@ -89,6 +89,18 @@ def random_block(seed: int, N: int, R: int, complex_: bool, s: int = 0) -> np.nd
     return phase_block(seed, N, R, s) if complex_ else rademacher_block(seed, N, R, s)
 
 
+def random_columns(seed: int, N: int, R: int, cols, complex_: bool, s: int = 0) -> np.ndarray:
+    """Columns `cols` of the N x R block of realisation s (same counters as random_block)."""
+    cols = np.asarray(cols, dtype=np.uint64)
+    i = np.arange(N, dtype=np.uint64)[:, None]
+    ctr = (np.uint64(s) * np.uint64(R) + cols[None, :]) * np.uint64(N) + i
+    z = u64(seed, STREAM_VECTORS, ctr)
+    if complex_:
+        phi = 2.0 * np.pi * ((z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53))
+        return np.cos(phi) + 1j * np.sin(phi)
+    return np.where((z >> np.uint64(63)) == 1, -1.0, 1.0)
+
+
 def lanczos_start(seed: int, N: int) -> np.ndarray:
     """Real Rademacher start vector for the Lanczos bound estimate (stream 6)."""
     bits = u64(seed, STREAM_LANCZOS, np.arange(N, dtype=np.uint64)) >> np.uint64(63)
@@ -205,6 +217,17 @@ def workload(name: str, seed: int | None = None) -> dict:
         N = lattice_sites(L)
         return dict(dims=2, L=L, periodic=(True, True), onsite=onsite_disorder(seed, N, 1.0),
                     hop=None, t=1.0, complex=False, mask=None, R=8, M=256, seed=seed, K=1024)
+    if name.startswith("csr_spin_dilute_L"):
+        # 3D cubic lattice, spin hoppings, 10% bond dilution, handled as CSR:
+        # R=32 complex vectors, M=4096
+        Lc = int(name[len("csr_spin_dilute_L"):])
+        seed = 4 if seed is None else seed
+        L = (Lc, Lc, Lc)
+        N = lattice_sites(L)
+        th, ph = spins(seed, N)
+        return dict(dims=3, L=L, periodic=(True, True, True), onsite=None,
+                    hop=spin_hoppings(L, th, ph), t=1.0, complex=True,
+                    mask=dilution_mask(seed, N, 3, 0.1), R=32, M=4096, seed=seed, K=4096)
     if name.startswith("cubic_spin_L"):
         # 3D cubic lattice with spin-derived complex hoppings, random-phase vectors
         Lc = int(name[len("cubic_spin_L"):].split("_")[0])

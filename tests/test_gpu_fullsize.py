@@ -1,0 +1,53 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times: the oracle recomputes sampled vector columns (each column's recursion
+is independent of the others), and every column must satisfy the invariants
+mu_0 = 1 and |mu_n| <= 1 that hold at any size."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1105_5481_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def K(gpu_lib):
+    from paper_1105_5481_gb300 import kpm
+
+    return kpm
+
+
+def test_cubic_L64_full_size_sampled_columns(K):
+    # 3D L=64 spin lattice (N=262144), R=64 random phases, M=1024: the bench workload
+    w = I.workload("cubic_spin_L64")
+    H = O.lattice_hamiltonian(w["L"], hop=w["hop"])
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    cols = [0, 41]
+    seed = 1000
+    v0 = I.random_columns(seed, H.n, w["R"], cols, True)
+    _, per_o = O.moments_doubling(H, a, b, v0, w["M"])
+    with K.kpm_create_stencil(3, w["L"], hop=w["hop"], complex_=True) as h:
+        for prec, tol, tol0 in (("fp32", 1e-5, 1e-6), ("fp64", 1e-10, 1e-14)):
+            mu, per = K.kpm_moments(h, w["M"], w["R"], a, b, seed=seed, precision=prec, per_vec=True)
+            assert np.abs(per[cols] - per_o).max() <= tol, prec
+            assert np.abs(per[:, 0] - 1.0).max() <= tol0
+            assert np.abs(per).max() <= 1.0 + tol
+            np.testing.assert_allclose(mu, per.mean(axis=0), rtol=0, atol=1e-14)
+
+
+def test_csr_L160_full_size_prefix(K):
+    # 3D L=160 spin lattice with 10% bond dilution as CSR (N=4.1M, nnz=22.1M),
+    # R=32, M=4096, FP32 vectors: oracle on one sampled column, first 32 moments
+    w = I.workload("csr_spin_dilute_L160")
+    rp, col, val = K.kpm_stencil_to_csr(3, w["L"], hop=w["hop"], bond_mask=w["mask"], complex_=True)
+    H = O.lattice_hamiltonian(w["L"], hop=w["hop"], mask=w["mask"])
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    seed, c = 77, [19]
+    with K.kpm_create_csr(rp.size - 1, rp, col, val, complex_=True) as h:
+        mu, per = K.kpm_moments(h, w["M"], w["R"], a, b, seed=seed, precision="fp32", per_vec=True)
+    assert np.abs(per[:, 0] - 1.0).max() <= 1e-6
+    assert np.abs(per).max() <= 1.0 + 1e-5
+    v0 = I.random_columns(seed, H.n, w["R"], c, True)
+    _, per_o = O.moments_doubling(H, a, b, v0, 32)
+    assert np.abs(per[c, :32] - per_o).max() <= 1e-5

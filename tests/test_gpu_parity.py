@@ -193,3 +193,31 @@ def test_dos_device_buffers(K):
     torch.cuda.synchronize()
     E_o, rho_o = O.dos(mu.cpu().numpy(), 2.0, 0.0, 128)
     assert np.abs(rho.cpu().numpy() - rho_o).max() <= 1e-12 * np.abs(rho_o).max()
+
+
+def random_hermitian_csr(n, seed, max_row=20):
+    """Sparse Hermitian matrix with rows of very different lengths (generic CSR path)."""
+    rng = np.random.default_rng(seed)
+    A = np.zeros((n, n), dtype=np.complex128)
+    for i in range(n):
+        k = int(rng.integers(0, max_row // 2))
+        js = rng.choice(n, size=k, replace=False)
+        A[i, js] += rng.normal(size=k) + 1j * rng.normal(size=k)
+    A = A + A.conj().T + np.diag(rng.normal(size=n))
+    rows, cols = np.nonzero(A)
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    return np.cumsum(rowptr), cols.astype(np.int32), A[rows, cols]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_generic_csr_long_rows_match_oracle(K, prec):
+    n, R, M = 300, 6, 96
+    rp, col, val = random_hermitian_csr(n, 3)
+    assert np.diff(rp).max() > 8            # too long for the padded-ELL layout
+    H = O.CSR(n, rp, col, val)
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    mu_o, per_o = O.moments_doubling(H, a, b, I.random_block(5, n, R, True), M)
+    with K.kpm_create_csr(n, rp, col, val, complex_=True) as h:
+        mu, per = K.kpm_moments(h, M, R, a, b, seed=5, precision=prec, per_vec=True)
+    assert np.abs(per - per_o).max() <= TOL[prec]
