@@ -175,6 +175,56 @@ kpm_status kpm_dos(const double* mu, int M, double a, double b, int K, int kerne
  * the kpm_moments stream has completed; KPM_ENOTREADY if no call was made. */
 kpm_status kpm_step_timing(kpm_handle h, double* ms, int* step_launches);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent solves of uneven size (different lattices, N and M) run
+ * by ONE persistent kernel launch, captured once into a CUDA graph and
+ * replayed.  The launch is made of thread-block clusters of C CTAs; each
+ * cluster takes the next instance from a device queue (longest first), splits
+ * its rows among its C CTAs and runs all of its M/2 products back to back,
+ * the CTAs meeting at the hardware cluster barrier between products and
+ * adding their moment partials through distributed shared memory in rank
+ * order.  An instance's moments therefore depend only on C and the instance,
+ * not on the rest of the batch.  This is the batched form of kpm_moments for
+ * the paper's many-realisation workload (Sec. II-A-4: S realisations, each a
+ * different Hamiltonian for disorder averages). */
+typedef struct kpm_batch_s* kpm_batch;
+
+/* Builds a batch of `count` instances: handles[i] with params[i] (M even,
+ * a, b, seed; S must be 1 and user_v0 NULL).  All handles must be on the same
+ * device and of the same kind (field; stencil dims, presence of per-bond
+ * hoppings and on-site terms; or CSR with the same padded-ELL width), and all
+ * params must share precision and R.  The batch owns its vector blocks and
+ * its own scaled copies of the operators (later calls on the handles do not
+ * affect it); the handles must outlive the batch.  If an autotuned
+ * configuration for this device and batch shape is in the tuning cache
+ * (file $KPM_TUNE_CACHE, default ~/.cache/kpm_gb300_autotune.txt) it is used. */
+kpm_status kpm_batch_create(int count, const kpm_handle* handles, const kpm_params* params,
+                            kpm_batch* out);
+
+/* Runs the whole batch (every instance from its first to its last product)
+ * on `stream` by replaying the captured graph, and writes the moments of
+ * instance i to mu[off_i .. off_i + M_i) with off_i = M_0 + ... + M_{i-1}
+ * (host or device; NULL skips the copy).  Host outputs synchronise and
+ * report KPM_EDIVERGE like kpm_moments. */
+kpm_status kpm_batch_run(kpm_batch b, double* mu, void* stream);
+
+/* Autotuner: times `reps` replays of every launchable configuration (cluster
+ * size C in {1, 2, 4, 8, 16}, traversal chunk in {2, 4, 16} passes, 100 % or
+ * 50 % of the co-resident clusters), keeps the fastest for this batch and
+ * appends it to the tuning cache. */
+kpm_status kpm_batch_tune(kpm_batch b, int reps, void* stream);
+
+/* Fixes the configuration (cluster size a power of two <= 16, chunk >= 1,
+ * percent of co-resident clusters in 1..100) without tuning. */
+kpm_status kpm_batch_set_config(kpm_batch b, int cluster, int chunk, int percent);
+
+/* Current configuration, clusters launched, and the device time (ms) of the
+ * most recent replay (CUDA events recorded inside the graph). */
+kpm_status kpm_batch_info(kpm_batch b, int* cluster, int* chunk, int* clusters_launched,
+                          double* last_ms);
+
+void kpm_batch_destroy(kpm_batch b);
+
 /* Size of the fixed device scratch array behind kpm_moments_csr_noalloc. */
 #define KPM_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include "kpm_internal.h"
+#include "kpm_rng.cuh"
 
 namespace kpm {
 
@@ -20,19 +21,6 @@ inline unsigned blocks_for(int64_t n, int block) {
 inline cudaError_t counted(cudaError_t e) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return e;
-}
-
-// SplitMix64 (Steele, Lea, Flood 2014): counter-based draw for (seed, stream, counter).
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
-  z += 0x9E3779B97F4A7C15ULL;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-  return z ^ (z >> 31);
-}
-__device__ __forceinline__ unsigned long long draw(unsigned long long seed, int stream,
-                                                   unsigned long long counter) {
-  const unsigned long long key = seed ^ (0x9E3779B97F4A7C15ULL * (unsigned long long)(1 + stream));
-  return splitmix64(key + counter);
 }
 
 // ------------------------------------------------------------------ prescale
@@ -97,22 +85,6 @@ __global__ void prescale_csr_kernel(int64_t nnz, const double* __restrict__ val,
 }
 
 // ------------------------------------------------------------------ random vectors
-// Scalar offsets of the real and imaginary parts of entry (i, r) of an N x Rp
-// complex block.  FP64 blocks interleave (re, im); FP32 blocks store 32-byte
-// chunks of 4 columns split as (re0..re3, im0..im3).
-template <typename T>
-__device__ __forceinline__ void cplx_offsets(int64_t i, int r, int Rp, int64_t& re, int64_t& im) {
-  if (sizeof(T) == 8) {
-    re = 2 * (i * Rp + r);
-    im = re + 1;
-  } else {
-    re = i * 2 * Rp + (r / 4) * 8 + (r % 4);
-    im = re + 4;
-  }
-}
-
-// Entry (s, r, i): counter (s R + r) N + i of stream 0; Rademacher (top bit) or
-// exp(2 pi i u), u = (u64 >> 11) 2^-53.  Padded columns r >= R are zero.
 template <typename T, bool CPLX>
 __global__ void rng_init_kernel(int64_t n, int Rp, const RunParams* __restrict__ prm, T* v0) {
   const int R = prm->R;
@@ -120,36 +92,8 @@ __global__ void rng_init_kernel(int64_t n, int Rp, const RunParams* __restrict__
   const unsigned long long s = (unsigned long long)prm->s;
   const int64_t total = n * Rp;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / Rp;
-    const int r = (int)(e % Rp);
-    int64_t ore = e, oim = e;
-    if (CPLX) cplx_offsets<T>(i, r, Rp, ore, oim);
-    if (r >= R) {
-      if (CPLX) { v0[ore] = T(0); v0[oim] = T(0); }
-      else v0[e] = T(0);
-      continue;
-    }
-    const unsigned long long ctr = (s * (unsigned long long)R + (unsigned long long)r) *
-                                       (unsigned long long)n + (unsigned long long)i;
-    const unsigned long long z = draw(seed, 0, ctr);
-    if (CPLX) {
-      const double u = (double)(z >> 11) * 0x1.0p-53;
-      if (sizeof(T) == 8) {
-        double sv, cv;
-        sincospi(2.0 * u, &sv, &cv);
-        v0[ore] = (T)cv;
-        v0[oim] = (T)sv;
-      } else {
-        float sv, cv;
-        sincospif(2.0f * (float)u, &sv, &cv);
-        v0[ore] = (T)cv;
-        v0[oim] = (T)sv;
-      }
-    } else {
-      v0[e] = (z >> 63) ? T(-1) : T(1);
-    }
-  }
+       e += (int64_t)gridDim.x * blockDim.x)
+    random_entry<T, CPLX>(v0, n, Rp, R, seed, s, e);
 }
 
 template <typename T, bool CPLX>

@@ -1,0 +1,190 @@
+// Batched persistent launch: many independent KPM instances (different
+// lattices, sizes and moment counts) advanced by one kernel launch.
+//
+// The grid is made of thread-block clusters of C CTAs.  Each cluster takes the
+// next instance from an atomic queue (instances are ordered by decreasing
+// work, so the longest start first), splits the instance's rows among its C
+// CTAs with the same traversal as the single-instance fused step, and runs the
+// instance's steps [step_begin, step_end) back to back, separated by the
+// hardware cluster barrier (release/acquire at cluster scope, which orders the
+// vector rows written by one CTA before the next step's reads by the others).
+// Each CTA's moment partial goes to CTA rank 0 through distributed shared
+// memory; rank 0 adds the C partials in rank order.  Every access to another
+// CTA's shared memory is followed by a cluster barrier before any CTA can
+// leave the kernel.  An instance's result thus
+// depends only on C and the instance, never on the other instances in the
+// batch or on which cluster ran it.
+//
+// Vectors of v_n are written by the same launch in the previous step, so
+// they are read with coherent loads (chunk policy NC = false).
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "kpm_rng.cuh"
+#include "kpm_step.cuh"
+
+namespace kpm {
+
+namespace cg = cooperative_groups;
+
+struct BatchTask {
+  StepArgs a;         // operator, geometry, traversal (x, y, w, partial set per step)
+  void* v[2];         // the two vector blocks; step s reads v[s & 1], writes v[(s + 1) & 1]
+  double* sums;       // [M/2][2 Rp] per-step moment sums (A, B per column)
+  double* per_vec;    // [R][M]
+  double* mu;         // [M]
+  int step_begin;     // steps advanced by this launch: [step_begin, step_end);
+  int step_end;       //   step 0 = random start block + first product
+  int M, R;
+  unsigned long long seed;
+  int realisation;
+  int flags;          // set by the kernel: bit0 = a moment left [-1, 1]
+};
+
+template <class CH, class OP>
+__global__ void __launch_bounds__(256, 2) batch_kernel(BatchTask* tasks, int ntasks,
+                                                       int* queue) {
+  using T = typename CH::T;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int C = (int)cluster.num_blocks();
+  const int t = threadIdx.x;
+  extern __shared__ double smem[];
+  __shared__ int s_task;
+  const OP op;
+  for (;;) {
+    if (rank == 0 && t == 0) s_task = atomicAdd(queue, 1);
+    cluster.sync();
+    const int task = *cluster.map_shared_rank(&s_task, 0);
+    // Every CTA has read rank 0's s_task before any CTA goes on: rank 0 may
+    // then overwrite it, or exit (a CTA's shared memory must not be accessed
+    // by the rest of its cluster after it has exited).
+    cluster.sync();
+    if (task >= ntasks) break;
+    BatchTask& bt = tasks[task];
+    StepArgs a = bt.a;
+    const int Rp = a.Rp;
+    const int nsteps = bt.M / 2;
+    // shared memory: CTA reduction scratch, then partials [2 parities][C][2 Rp] (rank 0)
+    double* red = smem;
+    double* part = smem + step_smem_bytes(a.Gt, blockDim.x, CH::VEC) / sizeof(double);
+    double* part0 = cluster.map_shared_rank(part, 0);
+    for (int step = bt.step_begin; step < bt.step_end; ++step) {
+      if (step == 0) {
+        T* v0 = reinterpret_cast<T*>(bt.v[0]);
+        const int64_t total = a.n * Rp;
+        for (int64_t e = (int64_t)rank * blockDim.x + t; e < total; e += (int64_t)C * blockDim.x)
+          random_entry<T, CH::CPLX>(v0, a.n, Rp, bt.R, bt.seed,
+                                    (unsigned long long)bt.realisation, e);
+        cluster.sync();
+      }
+      a.x = bt.v[step & 1];
+      a.y = bt.v[(step + 1) & 1];
+      a.w = a.y;
+      typename CH::Acc s;
+      CH::acc_zero(s);
+      if (step == 0) step_rows<CH, MODE_FIRST, OP>(a, op, rank, C, 0, s);
+      else step_rows<CH, MODE_STEP, OP>(a, op, rank, C, 0, s);
+      cta_reduce<CH>(a, s, 0, red, part0 + ((size_t)(step & 1) * C + rank) * 2 * Rp);
+      cluster.sync();
+      if (rank == 0) {
+        const double* pp = part + (size_t)(step & 1) * C * 2 * Rp;
+        for (int o = t; o < 2 * Rp; o += blockDim.x) {
+          double sum = 0.0;
+          for (int r = 0; r < C; ++r) sum += pp[(size_t)r * 2 * Rp + o];
+          bt.sums[(size_t)step * 2 * Rp + o] = sum;
+        }
+      }
+    }
+    if (bt.step_end == nsteps && bt.step_begin < bt.step_end && rank == 0) {
+      __syncthreads();  // rank 0's own sums writes above
+      const int R = bt.R, M = bt.M;
+      const double inv_n = 1.0 / (double)a.n;
+      for (int e = t; e < R * nsteps; e += blockDim.x) {
+        const int r = e / nsteps, step = e % nsteps;
+        const double mu0 = bt.sums[r] * inv_n, mu1 = bt.sums[Rp + r] * inv_n;
+        double me = mu0, mo = mu1;
+        if (step > 0) {
+          me = 2.0 * bt.sums[(size_t)step * 2 * Rp + r] * inv_n - mu0;
+          mo = 2.0 * bt.sums[(size_t)step * 2 * Rp + Rp + r] * inv_n - mu1;
+        }
+        bt.per_vec[(size_t)r * M + 2 * step] = me;
+        bt.per_vec[(size_t)r * M + 2 * step + 1] = mo;
+        if (!(fabs(me) <= 1.0 + 1e-6) || !(fabs(mo) <= 1.0 + 1e-6)) atomicOr(&bt.flags, 1);
+      }
+      __syncthreads();
+      for (int m = t; m < M; m += blockDim.x) {
+        double acc = 0.0;
+        for (int r = 0; r < R; ++r) acc += bt.per_vec[(size_t)r * M + m];
+        bt.mu[m] = acc / (double)R;
+      }
+    }
+    cluster.sync();  // the instance is complete on every CTA of the cluster
+  }
+}
+
+inline size_t batch_smem_bytes(int Gt, int block, int vec, int C, int Rp) {
+  return step_smem_bytes(Gt, block, vec) + (size_t)2 * C * 2 * Rp * sizeof(double);
+}
+
+template <class CH, class OP>
+cudaError_t launch_batch_one(BatchTask* tasks, int ntasks, int* queue, int grid, int C, int Gt,
+                             int Rp, cudaStream_t st) {
+  const int block = 256;
+  const size_t smem = batch_smem_bytes(Gt, block, CH::VEC, C, Rp);
+  auto kern = batch_kernel<CH, OP>;
+  cudaError_t e = cudaSuccess;
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (C > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, tasks, ntasks, queue);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return e;
+}
+
+template <class CH, class OP>
+int batch_max_clusters(int C, int Gt, int Rp) {
+  const int block = 256;
+  const size_t smem = batch_smem_bytes(Gt, block, CH::VEC, C, Rp);
+  auto kern = batch_kernel<CH, OP>;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (C > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+}  // namespace kpm

@@ -1,0 +1,17 @@
+// FP64 instantiations of the batched persistent kernel.
+#include "kpm_batch_dispatch.cuh"
+
+namespace kpm {
+
+cudaError_t launch_batch_f64(bool cplx, const StepArgs& proto, BatchTask* tasks, int ntasks,
+                             int* queue, int grid, int C, cudaStream_t st) {
+  return cplx ? run_batch<ChunkF64<true, false>>(proto, tasks, ntasks, queue, grid, C, st)
+              : run_batch<ChunkF64<false, false>>(proto, tasks, ntasks, queue, grid, C, st);
+}
+
+int max_clusters_batch_f64(bool cplx, const StepArgs& proto, int C) {
+  return cplx ? clusters_batch<ChunkF64<true, false>>(proto, C)
+              : clusters_batch<ChunkF64<false, false>>(proto, C);
+}
+
+}  // namespace kpm

@@ -40,11 +40,17 @@
 namespace kpm {
 
 // ================================================================ chunk policies
+// Vector rows of v_n are read with ld_x: through the read-only path (NC) when
+// no thread writes them during the kernel (one fused step per launch), or with
+// plain coherent loads when the same launch writes them in an earlier step
+// (the batched persistent kernel).
+//
 // FP64: 16 bytes = 2 doubles.
-template <bool CPLX_>
+template <bool CPLX_, bool NC_ = true>
 struct ChunkF64 {
   using T = double;
   static constexpr bool CPLX = CPLX_;
+  static constexpr bool NC = NC_;
   static constexpr int SC = 2;                // scalars per chunk
   static constexpr int VEC = CPLX ? 1 : 2;    // vector columns per chunk
   double v[2];
@@ -56,6 +62,14 @@ struct ChunkF64 {
   __device__ __forceinline__ void ld_cs(const double* p) {
     const double2 q = __ldcs(reinterpret_cast<const double2*>(p));
     v[0] = q.x; v[1] = q.y;
+  }
+  __device__ __forceinline__ void ld_x(const double* p) {
+    if constexpr (NC) {
+      ld_nc(p);
+    } else {
+      const double2 q = *reinterpret_cast<const double2*>(p);
+      v[0] = q.x; v[1] = q.y;
+    }
   }
   __device__ __forceinline__ void st(double* p) const {
     *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
@@ -120,10 +134,11 @@ __device__ __forceinline__ void kahan2(float2& s, float2& c, float2 v) {
   s = t;
 }
 
-template <bool CPLX_>
+template <bool CPLX_, bool NC_ = true>
 struct ChunkF32 {
   using T = float;
   static constexpr bool CPLX = CPLX_;
+  static constexpr bool NC = NC_;
   static constexpr int SC = 8;
   static constexpr int VEC = CPLX ? 4 : 8;
   float2 p[4];
@@ -139,6 +154,17 @@ struct ChunkF32 {
                  : "=f"(p[0].x), "=f"(p[0].y), "=f"(p[1].x), "=f"(p[1].y), "=f"(p[2].x),
                    "=f"(p[2].y), "=f"(p[3].x), "=f"(p[3].y)
                  : "l"(a));
+  }
+  __device__ __forceinline__ void ld_x(const float* a) {
+    if constexpr (NC) {
+      ld_nc(a);
+    } else {
+      asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=f"(p[0].x), "=f"(p[0].y), "=f"(p[1].x), "=f"(p[1].y), "=f"(p[2].x),
+                     "=f"(p[2].y), "=f"(p[3].x), "=f"(p[3].y)
+                   : "l"(a)
+                   : "memory");
+    }
   }
   __device__ __forceinline__ void st(float* a) const {
     asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(a), "f"(p[0].x),
@@ -301,8 +327,8 @@ struct StencilOp {
     CH xf[DIMS], xb[DIMS];
 #pragma unroll
     for (int d2 = 0; d2 < DIMS; ++d2) {
-      xf[d2].ld_nc(Xc + (size_t)jf[d2] * rowS);
-      xb[d2].ld_nc(Xc + (size_t)jb[d2] * rowS);
+      xf[d2].ld_x(Xc + (size_t)jf[d2] * rowS);
+      xb[d2].ld_x(Xc + (size_t)jb[d2] * rowS);
     }
 #pragma unroll
     for (int d2 = 0; d2 < DIMS; ++d2) {
@@ -391,7 +417,7 @@ struct CsrOp {
       }
       CH xj[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) xj[u].ld_nc(Xc + (size_t)j[u] * rowS);
+      for (int u = 0; u < 4; ++u) xj[u].ld_x(Xc + (size_t)j[u] * rowS);
 #pragma unroll
       for (int u = 0; u < 4; ++u) acc.cmac(hr[u], hi[u], xj[u]);
     }
@@ -400,7 +426,7 @@ struct CsrOp {
       T hr, hi;
       hop(V, k, hr, hi);
       CH xj;
-      xj.ld_nc(Xc + (size_t)j * rowS);
+      xj.ld_x(Xc + (size_t)j * rowS);
       acc.cmac(hr, hi, xj);
     }
   }
@@ -458,23 +484,24 @@ struct EllOp {
     const size_t rowS = (size_t)a.G * CH::SC;
     CH xj[W];
 #pragma unroll
-    for (int k = 0; k < W; ++k) xj[k].ld_nc(Xc + (size_t)j[k] * rowS);
+    for (int k = 0; k < W; ++k) xj[k].ld_x(Xc + (size_t)j[k] * rowS);
 #pragma unroll
     for (int k = 0; k < W; ++k) acc.cmac(hr[k], hi[k], xj[k]);
   }
 };
 
 // ================================================================ the fused step
+// Rows of one step handled by CTA `cta` of `ncta` CTAs working on the same
+// vectors: chunks of a.chunk passes taken in a stride-ncta loop (see
+// StepArgs).  Accumulates this thread's moment dots into s.
 template <class CH, int MODE, class OP>
-__global__ void __launch_bounds__(256, OP::kMinBlocks) cheb_step_kernel(const StepArgs a) {
+__device__ __forceinline__ void step_rows(const StepArgs& a, const OP& op, int cta, int ncta,
+                                          int ycol, typename CH::Acc& s) {
   using T = typename CH::T;
   constexpr int SC = CH::SC;
-  constexpr int VEC = CH::VEC;
-  const OP op;
   const int Gt = a.Gt;
   const int t = threadIdx.x;
-  const int cl = t % Gt;                  // chunk within this CTA's column slice
-  const int c = blockIdx.y * Gt + cl;     // chunk within the row
+  const int c = ycol * Gt + t % Gt;       // chunk within the row
   const int q = t / Gt;
   const int spi = blockDim.x / Gt;
   const size_t rowS = (size_t)a.G * SC;
@@ -484,13 +511,10 @@ __global__ void __launch_bounds__(256, OP::kMinBlocks) cheb_step_kernel(const St
   T hu_r, hu_i, du;
   scal_from_block<T>(a.sc, hu_r, hu_i, du);
 
-  typename CH::Acc s;
-  CH::acc_zero(s);
-
   const int Lx = a.line_len;
   const int u = a.chunk;
   const int64_t nchunks = (a.passes + u - 1) / u;
-  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+  for (int64_t ch = cta; ch < nchunks; ch += ncta) {
     const int64_t p_beg = ch * (int64_t)u;
     const int np = (int)min((int64_t)u, a.passes - p_beg);
     // line traversal: x and the line context advance incrementally
@@ -525,7 +549,7 @@ __global__ void __launch_bounds__(256, OP::kMinBlocks) cheb_step_kernel(const St
       }
       const size_t base = (size_t)i * rowS;
       CH xi, acc;
-      xi.ld_nc(Xc + base);
+      xi.ld_x(Xc + base);
       if constexpr (MODE == MODE_STEP) {
         CH wv;
         wv.ld_cs(Wc + base);
@@ -544,49 +568,70 @@ __global__ void __launch_bounds__(256, OP::kMinBlocks) cheb_step_kernel(const St
       if constexpr (MODE != MODE_SPMV) CH::acc_add(s, xi, acc);
     }
   }
-  if constexpr (MODE == MODE_SPMV) return;
-  else {
-    double dA[VEC], dB[VEC];
-    CH::acc_out(s, dA, dB);
-    extern __shared__ double red[];
-    const int lane = t & 31, warp = t >> 5;
-    bool rep;
-    int qrep, nq;
-    if (Gt < 32) {
-      for (int off = Gt; off < 32; off <<= 1) {
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) {
-          dA[k] += __shfl_xor_sync(0xffffffffu, dA[k], off);
-          dB[k] += __shfl_xor_sync(0xffffffffu, dB[k], off);
-        }
-      }
-      rep = lane < Gt;
-      qrep = warp;
-      nq = blockDim.x >> 5;
-    } else {
-      rep = true;
-      qrep = q;
-      nq = spi;
-    }
-    if (rep) {
+}
+
+// CTA-wide sum of the threads' moment dots: lanes sharing a column are
+// combined with warp shuffles, warps in shared memory `red` in warp order.
+// Writes dst[which * Rp + ycol * Rt + col] for which in {A, B} and the Rt
+// columns of this column slice.  All threads of the CTA must call it.
+template <class CH>
+__device__ __forceinline__ void cta_reduce(const StepArgs& a, const typename CH::Acc& s, int ycol,
+                                           double* red, double* dst) {
+  constexpr int VEC = CH::VEC;
+  const int Gt = a.Gt;
+  const int t = threadIdx.x;
+  const int cl = t % Gt, q = t / Gt, spi = blockDim.x / Gt;
+  double dA[VEC], dB[VEC];
+  CH::acc_out(s, dA, dB);
+  const int lane = t & 31, warp = t >> 5;
+  bool rep;
+  int qrep, nq;
+  if (Gt < 32) {
+    for (int off = Gt; off < 32; off <<= 1) {
 #pragma unroll
       for (int k = 0; k < VEC; ++k) {
-        red[((qrep * Gt + cl) * 2 + 0) * VEC + k] = dA[k];
-        red[((qrep * Gt + cl) * 2 + 1) * VEC + k] = dB[k];
+        dA[k] += __shfl_xor_sync(0xffffffffu, dA[k], off);
+        dB[k] += __shfl_xor_sync(0xffffffffu, dB[k], off);
       }
     }
-    __syncthreads();
-    const int Rp = a.Rp, Rt = Gt * VEC;
-    for (int o = t; o < 2 * Rt; o += blockDim.x) {
-      const int which = o / Rt, col = o % Rt, cc = col / VEC, k = col % VEC;
-      double sum = 0.0;
-      for (int qq = 0; qq < nq; ++qq) sum += red[((qq * Gt + cc) * 2 + which) * VEC + k];
-      a.partial[(size_t)blockIdx.x * 2 * Rp + which * Rp + blockIdx.y * Rt + col] = sum;
+    rep = lane < Gt;
+    qrep = warp;
+    nq = blockDim.x >> 5;
+  } else {
+    rep = true;
+    qrep = q;
+    nq = spi;
+  }
+  if (rep) {
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      red[((qrep * Gt + cl) * 2 + 0) * VEC + k] = dA[k];
+      red[((qrep * Gt + cl) * 2 + 1) * VEC + k] = dB[k];
     }
+  }
+  __syncthreads();
+  const int Rp = a.Rp, Rt = Gt * VEC;
+  for (int o = t; o < 2 * Rt; o += blockDim.x) {
+    const int which = o / Rt, col = o % Rt, cc = col / VEC, k = col % VEC;
+    double sum = 0.0;
+    for (int qq = 0; qq < nq; ++qq) sum += red[((qq * Gt + cc) * 2 + which) * VEC + k];
+    dst[which * Rp + ycol * Rt + col] = sum;
   }
 }
 
-inline size_t step_smem_bytes(int Gt, int block, int vec) {
+template <class CH, int MODE, class OP>
+__global__ void __launch_bounds__(256, OP::kMinBlocks) cheb_step_kernel(const StepArgs a) {
+  const OP op;
+  typename CH::Acc s;
+  CH::acc_zero(s);
+  step_rows<CH, MODE, OP>(a, op, blockIdx.x, gridDim.x, blockIdx.y, s);
+  if constexpr (MODE != MODE_SPMV) {
+    extern __shared__ double red[];
+    cta_reduce<CH>(a, s, blockIdx.y, red, a.partial + (size_t)blockIdx.x * 2 * a.Rp);
+  }
+}
+
+__host__ __device__ inline size_t step_smem_bytes(int Gt, int block, int vec) {
   const int nq = Gt < 32 ? block / 32 : block / Gt;
   return (size_t)nq * Gt * 2 * vec * sizeof(double);
 }

@@ -204,6 +204,21 @@ def batch_shapes(seed: int, count: int, L_lo=16, L_hi=128, W_hi=4.0, M_lo=128, M
     return L, W, M
 
 
+def batch_workload(seed: int = 3, count: int = 256, L_lo=16, L_hi=128, M_lo=128, M_hi=2048):
+    """Independent 2D disorder realisations of uneven size: L ~ U{L_lo..L_hi},
+    W ~ U[0, 4), M even ~ U{M_lo..M_hi} (stream 5), t = 1, periodic, on-site
+    energies from stream 1 with seed (seed * 1000003 + k), R = 16 Rademacher
+    vectors with seed (seed * 7919 + k)."""
+    Ls, Ws, Ms = batch_shapes(seed, count, L_lo, L_hi, 4.0, M_lo, M_hi)
+    out = []
+    for k in range(count):
+        L = (int(Ls[k]), int(Ls[k]))
+        out.append(dict(dims=2, L=L, periodic=(True, True), W=float(Ws[k]), M=int(Ms[k]),
+                        onsite=onsite_disorder(seed * 1000003 + k, L[0] * L[1], float(Ws[k])),
+                        R=16, seed=seed * 7919 + k))
+    return out
+
+
 def workload(name: str, seed: int | None = None) -> dict:
     """Hamiltonian inputs for the named synthetic workload.
 

@@ -72,13 +72,22 @@ def lib() -> C.CDLL:
         L.kpm_moments_csr_noalloc.argtypes = [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_double,
                                               C.c_double, C.c_void_p, C.c_void_p]
+        L.kpm_batch_create.argtypes = [C.c_int, C.POINTER(C.c_void_p), C.POINTER(kpm_params), C.POINTER(h)]
+        L.kpm_batch_run.argtypes = [h, C.c_void_p, C.c_void_p]
+        L.kpm_batch_tune.argtypes = [h, C.c_int, C.c_void_p]
+        L.kpm_batch_set_config.argtypes = [h, C.c_int, C.c_int, C.c_int]
+        L.kpm_batch_info.argtypes = [h, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_double)]
+        L.kpm_batch_destroy.argtypes = [h]
+        L.kpm_batch_destroy.restype = None
         L.kpm_destroy.argtypes = [h]
         L.kpm_destroy.restype = None
         L.kpm_last_error.restype = C.c_char_p
         L.kpm_kernel_launches.restype = C.c_uint64
         for name in ("kpm_create_stencil", "kpm_create_csr", "kpm_stencil_to_csr", "kpm_bounds",
                      "kpm_moments", "kpm_dos", "kpm_info", "kpm_step_timing",
-                     "kpm_moments_csr_noalloc"):
+                     "kpm_moments_csr_noalloc", "kpm_batch_create", "kpm_batch_run", "kpm_batch_tune",
+                     "kpm_batch_set_config", "kpm_batch_info"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -286,6 +295,80 @@ def kpm_moments_csr_noalloc(n, nnz, d_rowptr, d_col, d_val, M, R, a, b, seed=0, 
                                          int(seed) & 0xFFFFFFFFFFFFFFFF, float(a), float(b), _ptr(mu),
                                          _stream(stream)))
     return mu
+
+
+class Batch:
+    """Owning wrapper of a kpm_batch (keeps its handles alive)."""
+
+    def __init__(self, raw, handles, Ms):
+        self.raw = raw
+        self.handles = list(handles)
+        self.Ms = list(Ms)
+        self.offsets = np.concatenate([[0], np.cumsum(self.Ms)]).astype(np.int64)
+
+    def close(self):
+        if self.raw:
+            lib().kpm_batch_destroy(self.raw)
+            self.raw = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def split(self, mu):
+        return [mu[self.offsets[i]:self.offsets[i + 1]] for i in range(len(self.Ms))]
+
+
+def kpm_batch_create(handles, Ms, R, a, b, seeds, precision="fp32") -> Batch:
+    """Batch of len(handles) instances; Ms, a, b, seeds are per-instance sequences."""
+    n = len(handles)
+    ps = (kpm_params * n)()
+    for i in range(n):
+        ps[i].M, ps[i].R, ps[i].S = int(Ms[i]), int(R), 1
+        ps[i].seed = int(seeds[i]) & 0xFFFFFFFFFFFFFFFF
+        ps[i].precision = PRECISIONS[precision]
+        ps[i].a, ps[i].b = float(a[i]), float(b[i])
+        ps[i].user_v0 = None
+    hs = (C.c_void_p * n)(*[h.raw for h in handles])
+    raw = C.c_void_p()
+    _check(lib().kpm_batch_create(n, hs, ps, C.byref(raw)))
+    return Batch(raw, handles, Ms)
+
+
+def kpm_batch_run(bt: Batch, out=None, stream=None):
+    """Runs the batch; returns the concatenated moments (numpy) unless ``out``
+    (a CUDA tensor of sum(M) doubles) is given."""
+    mu = np.zeros(int(bt.offsets[-1])) if out is None else out
+    _check(lib().kpm_batch_run(bt.raw, _ptr(mu), _stream(stream)))
+    return mu
+
+
+def kpm_batch_tune(bt: Batch, reps=1, stream=None):
+    _check(lib().kpm_batch_tune(bt.raw, int(reps), _stream(stream)))
+    return kpm_batch_info(bt)
+
+
+def kpm_batch_set_config(bt: Batch, cluster, chunk=4, percent=100):
+    _check(lib().kpm_batch_set_config(bt.raw, int(cluster), int(chunk), int(percent)))
+
+
+def kpm_batch_info(bt: Batch):
+    cl, ch, nc = C.c_int(), C.c_int(), C.c_int()
+    ms = C.c_double()
+    _check(lib().kpm_batch_info(bt.raw, C.byref(cl), C.byref(ch), C.byref(nc), C.byref(ms)))
+    return dict(cluster=cl.value, chunk=ch.value, clusters=nc.value, last_ms=ms.value)
+
+
+def kpm_batch_destroy(bt: Batch):
+    bt.close()
 
 
 def kpm_destroy(h: Handle):
