@@ -225,6 +225,63 @@ kpm_status kpm_batch_info(kpm_batch b, int* cluster, int* chunk, int* clusters_l
 
 void kpm_batch_destroy(kpm_batch b);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop with continuous batching.  Requests (a handle, its
+ * parameters and a DOS node count) may be submitted from any thread while
+ * others run.  A scheduler thread owns a device arena of `hbm_budget_bytes`
+ * and runs ticks: pending requests are admitted first come first served as
+ * soon as their device memory fits in the budget (two N x R vector blocks,
+ * a scaled copy of the operator, moment sums and outputs, DOS buffers);
+ * every resident request then advances up to `steps_per_tick` products -
+ * small and medium ones (< 2^17 sites) together in one batched persistent
+ * cluster launch per operator kind and vector width, large ones as full-GPU
+ * fused steps on a second stream - so requests that arrive while others are
+ * on the GPU join the next tick and their work overlaps; finished requests
+ * get the Jackson DOS on the device, their results are copied to the host and
+ * their memory is released.  A request's moments are the same alone and in
+ * any mix.  Handles must outlive their requests. */
+typedef struct kpm_server_s* kpm_server;
+
+typedef struct {
+  uint64_t submitted, completed, failed, cancelled, ticks;
+  double p50_s, p99_s, mean_s, max_s;  /* submit -> results-on-host latency of completed requests */
+  double solves_per_s;                 /* completed / (last completion - first submission) */
+  int peak_resident;
+  size_t peak_bytes, budget_bytes;
+} kpm_server_stats_t;
+
+/* cluster: CTAs per cluster of the batched launches (power of two <= 16);
+ * steps_per_tick in 1..64. */
+kpm_status kpm_server_create(size_t hbm_budget_bytes, int steps_per_tick, int cluster,
+                             kpm_server* out);
+
+/* Queues a request: params as for kpm_moments (S = 1, no user_v0; a and b
+ * given), K Jackson-DOS nodes (0: moments only).  KPM_ENOMEM if the request
+ * alone exceeds the budget. */
+kpm_status kpm_server_submit(kpm_server s, kpm_handle h, const kpm_params* p, int K,
+                             uint64_t* req_id);
+
+/* Blocks until the request has finished, failed or been cancelled
+ * (timeout_s < 0: no limit; KPM_ETIMEOUT otherwise). */
+kpm_status kpm_server_wait(kpm_server s, uint64_t req_id, double timeout_s);
+
+/* Copies a finished request's results (mu[M], E[K], rho[K] host buffers, any
+ * may be NULL) and its latency, then forgets the request.  KPM_ENOTREADY while
+ * it is pending or running; the request's own status (e.g. KPM_EDIVERGE)
+ * otherwise. */
+kpm_status kpm_server_poll(kpm_server s, uint64_t req_id, double* mu, double* E, double* rho,
+                           double* latency_s);
+
+/* Cancels a pending or running request at the next tick boundary; the other
+ * requests are unaffected.  Its poll then reports KPM_EINVAL. */
+kpm_status kpm_server_cancel(kpm_server s, uint64_t req_id);
+
+kpm_status kpm_server_stats(kpm_server s, kpm_server_stats_t* out);
+
+/* Stops the scheduler (requests still queued or running are dropped) and
+ * releases the arena. */
+void kpm_server_destroy(kpm_server s);
+
 /* Size of the fixed device scratch array behind kpm_moments_csr_noalloc. */
 #define KPM_NOALLOC_SCRATCH_BYTES (32u << 20)
 

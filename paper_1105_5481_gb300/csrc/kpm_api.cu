@@ -16,6 +16,20 @@
 
 namespace kpm {
 
+// vector columns per chunk (FP32: 32-byte chunks; FP64: 16-byte chunks)
+int vec_per_chunk(bool fp32, bool cplx) { return fp32 ? (cplx ? 4 : 8) : (cplx ? 1 : 2); }
+
+void padded_width(int R, bool fp32, bool cplx, int* Rp, int* G) {
+  const int vec = vec_per_chunk(fp32, cplx);
+  int g = (R + vec - 1) / vec;
+  int p2 = 1;
+  while (p2 < g) p2 <<= 1;
+  *G = p2;
+  *Rp = p2 * vec;
+}
+
+size_t elem_bytes(bool fp32, bool cplx) { return (fp32 ? 4 : 8) * (cplx ? 2 : 1); }
+
 static thread_local std::string t_err;
 std::atomic<uint64_t> g_launches{0};
 
@@ -60,19 +74,6 @@ void dfree(void* p) {
   if (p) cudaFree(p);
 }
 
-// vector columns per chunk (FP32: 32-byte chunks; FP64: 16-byte chunks)
-int vec_per_chunk(bool fp32, bool cplx) { return fp32 ? (cplx ? 4 : 8) : (cplx ? 1 : 2); }
-
-void padded_width(int R, bool fp32, bool cplx, int* Rp, int* G) {
-  const int vec = vec_per_chunk(fp32, cplx);
-  int g = (R + vec - 1) / vec;
-  int p2 = 1;
-  while (p2 < g) p2 <<= 1;
-  *G = p2;
-  *Rp = p2 * vec;
-}
-
-size_t elem_bytes(bool fp32, bool cplx) { return (fp32 ? 4 : 8) * (cplx ? 2 : 1); }
 
 kpm_status check_device(int* dev) {
   int n = 0;
@@ -300,6 +301,60 @@ int64_t stencil_nnz(const kpm_stencil_desc* d, int c, int64_t n) {
 }
 
 }  // namespace
+
+void plan_step_grid(const kpm_handle_s* h, bool fp32, StepArgs& a, int* block, int* grid) {
+  plan_grid(h, fp32, a, block, grid);
+}
+
+void operator_args(StepArgs& a, const kpm_handle_s* h, void* hs, void* ds, const ScalarBlock* sc,
+                   int Rp, int G) {
+  a.n = h->n;
+  a.Rp = Rp;
+  a.G = G;
+  a.Gt = std::min(G, BLOCK);
+  a.sc = sc;
+  a.geom = h->geom;
+  a.hs = a.ds = nullptr;
+  a.rowptr = nullptr;
+  a.col = nullptr;
+  a.vals = nullptr;
+  a.ell_w = 0;
+  if (h->stencil) {
+    a.hs = h->has_hop ? hs : nullptr;
+    a.ds = h->has_onsite ? ds : nullptr;
+  } else if (h->ell_w > 0) {
+    a.col = h->d_ell_col;
+    a.vals = hs;
+    a.ell_w = h->ell_w;
+  } else {
+    a.rowptr = h->d_rowptr;
+    a.col = h->d_col;
+    a.vals = hs;
+  }
+}
+
+void scaled_operator_bytes(const kpm_handle_s* h, bool fp32, size_t* hs_bytes, size_t* ds_bytes) {
+  const size_t ssz = fp32 ? 4 : 8, c = h->cplx ? 2 : 1;
+  *hs_bytes = *ds_bytes = 0;
+  if (h->stencil) {
+    if (h->has_hop) *hs_bytes = (size_t)h->n * h->geom.dims * c * ssz;
+    if (h->has_onsite) *ds_bytes = (size_t)h->n * ssz;
+  } else {
+    *hs_bytes = (h->ell_w > 0 ? (size_t)h->n * h->ell_w : (size_t)h->nnz) * c * ssz;
+  }
+}
+
+cudaError_t prescale_into(const kpm_handle_s* h, bool fp32, const RunParams* prm, void* hs,
+                          void* ds, ScalarBlock* sc, cudaStream_t st) {
+  if (h->stencil)
+    return launch_prescale_stencil(fp32, h->cplx, h->n, h->geom.dims, h->d_onsite, h->d_hop,
+                                   h->t_re, h->t_im, prm, false, h->has_hop ? hs : nullptr,
+                                   h->has_onsite ? ds : nullptr, sc, st);
+  if (h->ell_w > 0)
+    return launch_prescale_csr(fp32, h->cplx, h->n * h->ell_w, h->d_ell_val, prm, false, hs, sc, st);
+  return launch_prescale_csr(fp32, h->cplx, h->nnz, h->d_val, prm, false, hs, sc, st);
+}
+
 }  // namespace kpm
 
 using namespace kpm;

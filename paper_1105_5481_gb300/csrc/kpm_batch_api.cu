@@ -16,15 +16,6 @@
 
 #include "kpm_batch.cuh"
 
-namespace kpm {
-cudaError_t launch_batch_f32(bool cplx, const StepArgs& proto, BatchTask* tasks, int ntasks,
-                             int* queue, int grid, int C, cudaStream_t st);
-cudaError_t launch_batch_f64(bool cplx, const StepArgs& proto, BatchTask* tasks, int ntasks,
-                             int* queue, int grid, int C, cudaStream_t st);
-int max_clusters_batch_f32(bool cplx, const StepArgs& proto, int C);
-int max_clusters_batch_f64(bool cplx, const StepArgs& proto, int C);
-}  // namespace kpm
-
 using namespace kpm;
 
 struct BatchConfig {

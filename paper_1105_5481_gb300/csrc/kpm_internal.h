@@ -156,6 +156,34 @@ cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, int m
 cudaError_t launch_dos(const double* mu, int M, double a, double b, int K, int kernel,
                        double* E, double* rho, double* work, cudaStream_t st);
 
+// Vector columns per chunk and chunk rounding of R (shared by all entry points).
+int vec_per_chunk(bool fp32, bool cplx);
+void padded_width(int R, bool fp32, bool cplx, int* Rp, int* G);
+size_t elem_bytes(bool fp32, bool cplx);
+
+}  // namespace kpm
+
+struct kpm_handle_s;
+namespace kpm {
+// Fills the operator part of a step's arguments from a handle and scaled
+// operator arrays (stencil: hs, ds; CSR/ELL: vals in hs).
+void operator_args(StepArgs& a, const kpm_handle_s* h, void* hs, void* ds, const ScalarBlock* sc,
+                   int Rp, int G);
+// Traversal and grid of the single-instance fused step (fills a.line_len,
+// a.lines, a.line_L1, a.passes, a.chunk).
+void plan_step_grid(const kpm_handle_s* h, bool fp32, StepArgs& a, int* block, int* grid);
+// Bytes of the scaled operator arrays of a handle at one precision.
+void scaled_operator_bytes(const kpm_handle_s* h, bool fp32, size_t* hs_bytes, size_t* ds_bytes);
+cudaError_t prescale_into(const kpm_handle_s* h, bool fp32, const RunParams* prm, void* hs,
+                          void* ds, ScalarBlock* sc, cudaStream_t st);
+// Batched persistent kernel (kpm_batch_f32.cu / kpm_batch_f64.cu)
+struct BatchTask;
+cudaError_t launch_batch_f32(bool cplx, const StepArgs& proto, BatchTask* tasks, int ntasks,
+                             int* queue, int grid, int C, cudaStream_t st);
+cudaError_t launch_batch_f64(bool cplx, const StepArgs& proto, BatchTask* tasks, int ntasks,
+                             int* queue, int grid, int C, cudaStream_t st);
+int max_clusters_batch_f32(bool cplx, const StepArgs& proto, int C);
+int max_clusters_batch_f64(bool cplx, const StepArgs& proto, int C);
 }  // namespace kpm
 
 // The handle (opaque to callers).

@@ -219,6 +219,31 @@ def batch_workload(seed: int = 3, count: int = 256, L_lo=16, L_hi=128, M_lo=128,
     return out
 
 
+def serving_stream(seed: int = 5, count: int = 64, rate_hz: float = 50.0, N_lo=1e3, N_hi=4e6,
+                   M_lo=256, M_hi=8192, Rs=(8, 16, 32, 64)):
+    """Poisson stream of DOS requests (stream 5, counters 1000000 + 8k + j):
+    arrival gaps exponential with the given rate; 2D or 3D cubic lattice with
+    N log-uniform in [N_lo, N_hi] (side rounded, at least 4); M even and
+    log-uniform in [M_lo, M_hi]; R uniform in Rs; real or complex spin
+    hoppings (real: all azimuths 0); spins from seed 1000 + k."""
+    out = []
+    t = 0.0
+    for k in range(count):
+        c = 1000000 + 8 * np.arange(7, dtype=np.uint64) + np.uint64(8 * k)
+        u = uniform(seed, STREAM_SHAPES, c)
+        t += -np.log(1.0 - u[0]) / rate_hz
+        dims = 2 if u[1] < 0.5 else 3
+        N = float(np.exp(np.log(N_lo) + u[2] * (np.log(N_hi) - np.log(N_lo))))
+        side = max(4, int(round(N ** (1.0 / dims))))
+        M = int(np.exp(np.log(M_lo) + u[3] * (np.log(M_hi) - np.log(M_lo))))
+        M += M % 2
+        R = int(Rs[min(int(u[4] * len(Rs)), len(Rs) - 1)])
+        cplx = bool(u[5] < 0.5)
+        out.append(dict(t=t, dims=dims, L=(side,) * dims, M=M, R=R, complex=cplx, spin_seed=1000 + k,
+                        seed=7000 + k))
+    return out
+
+
 def workload(name: str, seed: int | None = None) -> dict:
     """Hamiltonian inputs for the named synthetic workload.
 

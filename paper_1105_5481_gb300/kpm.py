@@ -47,6 +47,14 @@ class kpm_params(C.Structure):
                 ("user_v0", C.c_void_p)]
 
 
+class kpm_server_stats_t(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("cancelled", C.c_uint64), ("ticks", C.c_uint64), ("p50_s", C.c_double),
+                ("p99_s", C.c_double), ("mean_s", C.c_double), ("max_s", C.c_double),
+                ("solves_per_s", C.c_double), ("peak_resident", C.c_int),
+                ("peak_bytes", C.c_size_t), ("budget_bytes", C.c_size_t)]
+
+
 _lib = None
 
 
@@ -80,6 +88,15 @@ def lib() -> C.CDLL:
                                      C.POINTER(C.c_double)]
         L.kpm_batch_destroy.argtypes = [h]
         L.kpm_batch_destroy.restype = None
+        L.kpm_server_create.argtypes = [C.c_size_t, C.c_int, C.c_int, C.POINTER(h)]
+        L.kpm_server_submit.argtypes = [h, h, C.POINTER(kpm_params), C.c_int, C.POINTER(C.c_uint64)]
+        L.kpm_server_wait.argtypes = [h, C.c_uint64, C.c_double]
+        L.kpm_server_poll.argtypes = [h, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.POINTER(C.c_double)]
+        L.kpm_server_cancel.argtypes = [h, C.c_uint64]
+        L.kpm_server_stats.argtypes = [h, C.POINTER(kpm_server_stats_t)]
+        L.kpm_server_destroy.argtypes = [h]
+        L.kpm_server_destroy.restype = None
         L.kpm_destroy.argtypes = [h]
         L.kpm_destroy.restype = None
         L.kpm_last_error.restype = C.c_char_p
@@ -87,7 +104,9 @@ def lib() -> C.CDLL:
         for name in ("kpm_create_stencil", "kpm_create_csr", "kpm_stencil_to_csr", "kpm_bounds",
                      "kpm_moments", "kpm_dos", "kpm_info", "kpm_step_timing",
                      "kpm_moments_csr_noalloc", "kpm_batch_create", "kpm_batch_run", "kpm_batch_tune",
-                     "kpm_batch_set_config", "kpm_batch_info"):
+                     "kpm_batch_set_config", "kpm_batch_info", "kpm_server_create",
+                     "kpm_server_submit", "kpm_server_wait", "kpm_server_poll", "kpm_server_cancel",
+                     "kpm_server_stats"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -369,6 +388,85 @@ def kpm_batch_info(bt: Batch):
 
 def kpm_batch_destroy(bt: Batch):
     bt.close()
+
+
+class Server:
+    """Owning wrapper of a kpm_server; remembers (M, K) of each request."""
+
+    def __init__(self, raw):
+        self.raw = raw
+        self.shapes = {}
+        self.handles = {}
+
+    def close(self):
+        if self.raw:
+            lib().kpm_server_destroy(self.raw)
+            self.raw = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def kpm_server_create(hbm_budget_bytes, steps_per_tick=32, cluster=4) -> Server:
+    raw = C.c_void_p()
+    _check(lib().kpm_server_create(int(hbm_budget_bytes), int(steps_per_tick), int(cluster), C.byref(raw)))
+    return Server(raw)
+
+
+def kpm_server_submit(srv: Server, h: Handle, M, R, a, b, seed=0, precision="fp32", K=0) -> int:
+    p = kpm_params()
+    p.M, p.R, p.S = int(M), int(R), 1
+    p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    p.precision = PRECISIONS[precision]
+    p.a, p.b = float(a), float(b)
+    p.user_v0 = None
+    rid = C.c_uint64()
+    _check(lib().kpm_server_submit(srv.raw, h.raw, C.byref(p), int(K), C.byref(rid)))
+    srv.shapes[rid.value] = (int(M), int(K))
+    srv.handles[rid.value] = h
+    return rid.value
+
+
+def kpm_server_wait(srv: Server, rid: int, timeout_s=-1.0):
+    _check(lib().kpm_server_wait(srv.raw, int(rid), float(timeout_s)))
+
+
+def kpm_server_poll(srv: Server, rid: int, check=True):
+    """(mu, E, rho, latency_s) of a finished request, or None while it runs."""
+    M, K = srv.shapes[rid]
+    mu, E, rho = np.zeros(M), np.zeros(max(K, 1)), np.zeros(max(K, 1))
+    lat = C.c_double()
+    st = lib().kpm_server_poll(srv.raw, int(rid), _ptr(mu), _ptr(E), _ptr(rho), C.byref(lat))
+    if st == KPM_ENOTREADY:
+        return None
+    srv.shapes.pop(rid, None)
+    srv.handles.pop(rid, None)
+    if check:
+        _check(st)
+    return mu, E[:K], rho[:K], lat.value
+
+
+def kpm_server_cancel(srv: Server, rid: int):
+    _check(lib().kpm_server_cancel(srv.raw, int(rid)))
+
+
+def kpm_server_stats(srv: Server) -> dict:
+    st = kpm_server_stats_t()
+    _check(lib().kpm_server_stats(srv.raw, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def kpm_server_destroy(srv: Server):
+    srv.close()
 
 
 def kpm_destroy(h: Handle):
