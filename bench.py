@@ -52,7 +52,7 @@ STEP_SOURCES = ["paper_1105_5481_gb300/csrc/kpm_step.cuh",
 # DRAM bytes (read + write) per fused-step launch from one ncu capture, keyed by
 # workload, with the hash of the kernel sources it was taken on
 # (profiles/cheb_step_fp32_cubic_spin_L64.md); reported only while the hash matches.
-MEASURED_TRAFFIC = {"cubic_spin_L64": (380.48e6, "8da0b5092cc32a8d")}
+MEASURED_TRAFFIC = {"cubic_spin_L64": (380.64e6, "99dbc3236aa3f62e")}
 
 
 def step_source_hash():
@@ -555,6 +555,14 @@ def main():
     ms32, launches32, step_ms32, clk32 = timed("fp32", args.steps, args.warmup)
     ms64, launches64, step_ms64, clk64 = timed("fp64", args.fp64_steps, min(args.warmup, 3))
 
+    combined = None
+    if dist is not None:
+        # replicas ran disjoint random vectors (seed per rank): the job's moments
+        # are the vector-weighted mean over ranks (one all-reduce of M+1 doubles)
+        from paper_1105_5481_gb300.replicas import combine_moments
+
+        mu_last = K.kpm_moments(h, M, R, a, b, seed=seed0, precision="fp32", stream=stream)
+        combined = combine_moments(mu_last, R)
     units = nnz * R * M  # per solve
     value = world * units / (ms32 / 1e3)
     bytes32, flops = algorithmic(nnz, N, R, M, True)
@@ -607,7 +615,8 @@ def main():
                                   "method": "Gershgorin + 30-step Lanczos, pad 0.01"},
                        "step": "random block + M/2 fused steps + moment reduction + Jackson DOS",
                        "l2": "inputs larger than L2 (two 134 MB vector blocks)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "replicas_combined": combined is not None},
             "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s",
                          "frac": ach32 / hbm, "traffic": measured_traffic(WORKLOAD["name"]),
                          "kernel": "cheb_step_kernel<float, complex, STEP, StencilOp<3,hop>>",
