@@ -386,7 +386,7 @@ def serve_leg(args, count=48, rate_hz=40.0, K_nodes=1024):
         ab.append(K.kpm_bounds(h, 0, WORKLOAD["pad_eps"])[2:])
 
     def run_served(prec):
-        srv = K.kpm_server_create(48 << 30, steps_per_tick=16, cluster=4)
+        srv = K.kpm_server_create(48 << 30, steps_per_tick=32, cluster=4)
         ids = [None] * len(reqs)
         t0 = time.perf_counter()
 
@@ -440,8 +440,8 @@ def serve_leg(args, count=48, rate_hz=40.0, K_nodes=1024):
         "config": {"workload": "serve_poisson", "requests": count, "arrival_rate_hz": rate_hz,
                    "mix": "2D/3D cubic, N log-uniform [1e3, 4e6], M even log-uniform [256, 8192], "
                           "R in {8,16,32,64}, real or complex spin hoppings, K=1024 Jackson DOS",
-                   "server": "48 GiB arena, 16 products per tick, clusters of 4, large requests "
-                             "(>= 2^17 sites) as full-GPU steps on a second stream",
+                   "server": "48 GiB arena, 32 products per tick, clusters of 4, large requests "
+                             "(>= 8 MB per product) as full-GPU steps on 4 streams",
                    "bounds": "Gershgorin per request, pad 0.01"},
         "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"], "mean": st["mean_s"], "max": st["max_s"]},
         "throughput": {"solves_per_s": st["completed"] / wall, "nnz_R_moments_per_s": units / wall},

@@ -233,9 +233,9 @@ void kpm_batch_destroy(kpm_batch b);
  * soon as their device memory fits in the budget (two N x R vector blocks,
  * a scaled copy of the operator, moment sums and outputs, DOS buffers);
  * every resident request then advances up to `steps_per_tick` products -
- * small and medium ones (< 2^17 sites) together in one batched persistent
+ * small ones (a product moving < 8 MB) together in one batched persistent
  * cluster launch per operator kind and vector width, large ones as full-GPU
- * fused steps on a second stream - so requests that arrive while others are
+ * fused steps on a pool of streams - so requests that arrive while others are
  * on the GPU join the next tick and their work overlaps; finished requests
  * get the Jackson DOS on the device, their results are copied to the host and
  * their memory is released.  A request's moments are the same alone and in

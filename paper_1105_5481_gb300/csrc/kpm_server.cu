@@ -10,8 +10,9 @@
 //      Small and medium requests, grouped by operator kind and vector width,
 //      advance together in one batched persistent cluster launch per group
 //      (the instance task table is rewritten every tick, so requests that
-//      arrived during the previous tick join this one); large requests
-//      (>= 2^17 sites) advance as full-GPU fused steps between them;
+//      arrived during the previous tick join this one); large requests (a
+//      product moving >= 8 MB) advance as full-GPU fused steps on a pool of
+//      streams that overlap with the batched launches and with each other;
 //   3. retirement: finished requests get their Jackson DOS on the device,
 //      their results are copied to the host, their arena memory is released
 //      and their waiters are woken.
@@ -38,8 +39,11 @@ using namespace kpm;
 
 namespace {
 
-constexpr int64_t SOLO_SITES = int64_t(1) << 17;
+// Requests whose product moves at least this many bytes (3 N Rp s_v) run as
+// full-GPU fused steps; smaller ones share the batched cluster launches.
+constexpr size_t SOLO_STEP_BYTES = size_t(8) << 20;
 constexpr int MAX_GROUPS = 1024;
+constexpr int SOLO_STREAMS = 4;
 constexpr size_t ALIGN = 256;
 
 size_t al(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
@@ -130,6 +134,7 @@ struct Req {
   RunParams host_prm{};
   StepArgs args{};
   int block = 0, grid = 0, ring_slots = 0;
+  cudaStream_t st = nullptr;  // the stream this request runs on
   double a = 1.0, b = 0.0;
   std::vector<double> out_mu, out_E, out_rho;
   double t_submit = 0, t_admit = 0, t_done = 0;
@@ -151,8 +156,8 @@ struct kpm_server_s {
   int steps_per_tick = 32;
   int C = 4;
   Arena arena;
-  cudaStream_t stream = nullptr;   // batched groups
-  cudaStream_t stream2 = nullptr;  // large requests, overlapping the batched launches
+  cudaStream_t stream = nullptr;                // batched groups
+  cudaStream_t solo_streams[SOLO_STREAMS] = {};  // large requests (round robin)
   BatchTask* d_tasks = nullptr;
   BatchTask* h_tasks = nullptr;  // pinned staging
   int* d_queue = nullptr;
@@ -247,7 +252,8 @@ void prepare(kpm_server_s* s, Req* r) {
 }
 
 cudaError_t solo_advance(kpm_server_s* s, Req* r, int b, int e) {
-  cudaStream_t st = s->stream2;
+  cudaStream_t st = r->st;
+  (void)s;
   cudaError_t err = cudaSuccess;
   StepArgs a = r->args;
   const LaunchCfg cfg{r->block, r->grid};
@@ -325,10 +331,11 @@ void worker_loop(kpm_server_s* s) {
       if (e == cudaSuccess) prepare(s, r);
       if (e != cudaSuccess) fail_req(r, KPM_ECUDA, cudaGetErrorString(e));
     }
-    // the large requests' stream must see the set-up done on the main stream
+    // the large requests' streams must see the set-up done on the main stream
     bool any_solo = false;
     for (Req* r : admitted) any_solo |= r->solo;
     if (any_solo) cudaStreamSynchronize(st);
+    for (Req* r : admitted) r->st = r->solo ? s->solo_streams[r->id % SOLO_STREAMS] : st;
     // advance: batched groups, then the large requests
     std::vector<Req*> live;
     for (Req* r : s->resident)
@@ -392,7 +399,7 @@ void worker_loop(kpm_server_s* s) {
     for (auto& pe : advanced) {
       Req* r = pe.first;
       if (err != cudaSuccess || pe.second != r->steps) continue;
-      cudaStream_t rs = r->solo ? s->stream2 : st;
+      cudaStream_t rs = r->st;
       if (r->K > 0)
         err = launch_dos(r->mu, r->p.M, r->a, r->b, r->K, KPM_KERNEL_JACKSON, r->E, r->rho,
                          r->dos_work, rs);
@@ -410,7 +417,8 @@ void worker_loop(kpm_server_s* s) {
       }
     }
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(s->stream2);
+    for (int k = 0; k < SOLO_STREAMS && err == cudaSuccess; ++k)
+      err = cudaStreamSynchronize(s->solo_streams[k]);
     const double t = now_s();
     {
       std::lock_guard<std::mutex> lock(s->mu);
@@ -484,7 +492,8 @@ kpm_status kpm_server_create(size_t hbm_budget_bytes, int steps_per_tick, int cl
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_tasks, s->max_tasks * sizeof(BatchTask));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s->h_tasks, s->max_tasks * sizeof(BatchTask));
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_queue, MAX_GROUPS * sizeof(int));
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream2, cudaStreamNonBlocking);
+  for (int k = 0; k < SOLO_STREAMS && e == cudaSuccess; ++k)
+    e = cudaStreamCreateWithFlags(&s->solo_streams[k], cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     kpm_status st = cuda_fail(e, "server set-up");
     s->arena.destroy();
@@ -521,7 +530,8 @@ kpm_status kpm_server_submit(kpm_server s, kpm_handle h, const kpm_params* p, in
   r->cplx = h->cplx;
   padded_width(p->R, r->fp32, r->cplx, &r->Rp, &r->G);
   r->steps = p->M / 2;
-  r->solo = h->n >= SOLO_SITES || r->G > 256;
+  r->solo = 3 * (size_t)h->n * r->Rp * elem_bytes(r->fp32, r->cplx) >= SOLO_STEP_BYTES ||
+            r->G > 256;
   if (r->solo) {
     // grid of the full-GPU fused step for this shape (sets the ring size)
     StepArgs probe{};
@@ -639,11 +649,11 @@ void kpm_server_destroy(kpm_server s) {
   if (s->worker.joinable()) s->worker.join();
   cudaSetDevice(s->device);
   cudaStreamSynchronize(s->stream);
-  cudaStreamSynchronize(s->stream2);
+  for (int k = 0; k < SOLO_STREAMS; ++k) cudaStreamSynchronize(s->solo_streams[k]);
   for (auto& kv : s->reqs) delete kv.second;
   s->arena.destroy();
   cudaStreamDestroy(s->stream);
-  cudaStreamDestroy(s->stream2);
+  for (int k = 0; k < SOLO_STREAMS; ++k) cudaStreamDestroy(s->solo_streams[k]);
   cudaFree(s->d_tasks);
   cudaFreeHost(s->h_tasks);
   cudaFree(s->d_queue);

@@ -28,6 +28,11 @@
 
 #include "kpm_internal.h"
 
+// Sliding register window along x in the line traversal (1: on).
+#ifndef KPM_STEP_XWINDOW
+#define KPM_STEP_XWINDOW 1
+#endif
+
 // Minimum resident CTAs per SM requested from the register allocator
 // (stencil steps; CSR/ELL steps).
 #ifndef KPM_STEP_MIN_BLOCKS
@@ -292,11 +297,15 @@ struct StencilOp {
     return k;
   }
 
-  // The shared core: diagonal, hoppings and the 2*DIMS neighbour rows.
+  // The shared core: diagonal, hoppings and the 2*DIMS neighbour rows.  With
+  // WIN the x-neighbour rows (d = 0) are supplied by the caller (xm: x-1,
+  // xp: x+1) from its sliding register window instead of being loaded.
+  template <bool WIN = false>
   __device__ __forceinline__ void core(const StepArgs& a, int i, const int (&jf)[DIMS],
                                        const int (&jb)[DIMS], const bool (&hf)[DIMS],
                                        const bool (&hb)[DIMS], const T* __restrict__ Xc,
-                                       const CH& xi, CH& acc, T hu_r, T hu_i, T du) const {
+                                       const CH& xi, CH& acc, T hu_r, T hu_i, T du,
+                                       const CH* xm = nullptr, const CH* xp = nullptr) const {
     const T d = HAS_DS ? __ldg(reinterpret_cast<const T*>(a.ds) + i) : du;
     acc.axpy(d, xi);
     T fr[DIMS], fi[DIMS], br[DIMS], bi[DIMS];
@@ -326,15 +335,51 @@ struct StencilOp {
     const size_t rowS = (size_t)a.G * CH::SC;
     CH xf[DIMS], xb[DIMS];
 #pragma unroll
-    for (int d2 = 0; d2 < DIMS; ++d2) {
+    for (int d2 = WIN ? 1 : 0; d2 < DIMS; ++d2) {
       xf[d2].ld_x(Xc + (size_t)jf[d2] * rowS);
       xb[d2].ld_x(Xc + (size_t)jb[d2] * rowS);
     }
+    if constexpr (WIN) {
+      acc.cmac(fr[0], fi[0], *xp);
+      acc.cmac(br[0], bi[0], *xm);
+    }
 #pragma unroll
-    for (int d2 = 0; d2 < DIMS; ++d2) {
+    for (int d2 = WIN ? 1 : 0; d2 < DIMS; ++d2) {
       acc.cmac(fr[d2], fi[d2], xf[d2]);
       acc.cmac(br[d2], bi[d2], xb[d2]);
     }
+  }
+
+  // Row indices of the x-neighbours of position cx (periodic wrap, or the
+  // row itself with a zero hopping at an open edge).
+  __device__ __forceinline__ void x_neighbours(const StepArgs& a, int i, int cx, int& jf0,
+                                               int& jb0) const {
+    const int L0 = a.line_len;
+    const bool per0 = a.geom.periodic[0] != 0;
+    jf0 = (cx + 1 < L0) ? i + 1 : (per0 ? i - (L0 - 1) : i);
+    jb0 = (cx > 0) ? i - 1 : (per0 ? i + (L0 - 1) : i);
+  }
+
+  // Line traversal with the x-neighbours taken from the caller's window.
+  __device__ __forceinline__ void apply_line_win(const StepArgs& a, int i, int cx,
+                                                 const LineCtx& k, const T* __restrict__ Xc,
+                                                 const CH& xi, const CH& xm, const CH& xp,
+                                                 CH& acc, T hu_r, T hu_i, T du) const {
+    int jf[DIMS], jb[DIMS];
+    bool hf[DIMS], hb[DIMS];
+    const int L0 = a.line_len;
+    const bool per0 = a.geom.periodic[0] != 0;
+    hf[0] = (cx + 1 < L0) || per0;
+    hb[0] = (cx > 0) || per0;
+    x_neighbours(a, i, cx, jf[0], jb[0]);
+#pragma unroll
+    for (int d2 = 1; d2 < DIMS; ++d2) {
+      jf[d2] = i + k.df[d2];
+      jb[d2] = i + k.db[d2];
+      hf[d2] = k.hf[d2];
+      hb[d2] = k.hb[d2];
+    }
+    core<true>(a, i, jf, jb, hf, hb, Xc, xi, acc, hu_r, hu_i, du, &xm, &xp);
   }
 
   // Row i at position cx on a line described by k (line traversal).
@@ -528,6 +573,52 @@ __device__ __forceinline__ void step_rows(const StepArgs& a, const OP& op, int c
         lctx = op.line_ctx(a, blk * spi + q);
       }
     }
+#if KPM_STEP_XWINDOW
+    if constexpr (OP::kLines) {
+      if (Lx > 0) {
+        // line traversal with a sliding window (x-1, x, x+1) of v_n rows in
+        // registers: one new x-neighbour row per pass instead of three rows
+        bool have = false;
+        CH xm, x0, xp;
+        const size_t rowS2 = rowS;
+        for (int jp = 0; jp < np; ++jp) {
+          if (jp > 0 && ++cx == Lx) {
+            cx = 0;
+            ++blk;
+            lctx = op.line_ctx(a, blk * spi + q);
+            have = false;
+          }
+          if (!lctx.valid) continue;
+          const int i = lctx.row0 + cx;
+          int jf0, jb0;
+          op.x_neighbours(a, i, cx, jf0, jb0);
+          if (!have) {
+            xm.ld_x(Xc + (size_t)jb0 * rowS2);
+            x0.ld_x(Xc + (size_t)i * rowS2);
+            have = true;
+          } else {
+            xm = x0;
+            x0 = xp;
+          }
+          xp.ld_x(Xc + (size_t)jf0 * rowS2);
+          const size_t base = (size_t)i * rowS2;
+          CH acc;
+          if constexpr (MODE == MODE_STEP) {
+            CH wv;
+            wv.ld_cs(Wc + base);
+            acc.set_neg(wv);
+          } else {
+            acc.zero();
+          }
+          op.apply_line_win(a, i, cx, lctx, Xc, x0, xm, xp, acc, hu_r, hu_i, du);
+          if constexpr (MODE == MODE_FIRST) acc.half();
+          acc.st(Yc + base);
+          if constexpr (MODE != MODE_SPMV) CH::acc_add(s, x0, acc);
+        }
+        continue;
+      }
+    }
+#endif
     for (int jp = 0; jp < np; ++jp) {
       int64_t i;
       bool line_mode = false;
