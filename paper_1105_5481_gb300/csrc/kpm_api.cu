@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -58,22 +59,62 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Device memory comes from a library-owned, stream-ordered pool per device
+// that keeps freed memory (release threshold = unlimited): creating, solving
+// and destroying handles repeatedly reuses it without cudaMalloc/cudaFree.
+constexpr int MAX_DEVICES = 64;
+cudaMemPool_t g_pools[MAX_DEVICES] = {};
+std::mutex g_pool_mu;
+
+cudaMemPool_t device_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = p;
+  }
+  return g_pools[dev];
+}
+
+// Allocation ordered on `st` (memory usable by work enqueued on `st` after it).
+cudaError_t palloc(void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  cudaMemPool_t pool = device_pool();
+  if (!pool) return cudaMalloc(p, bytes);
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+void pfree(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+// Synchronous-use allocation: ordered on the legacy stream and completed
+// before return, so any stream may use the memory afterwards.
 template <typename T>
 kpm_status dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) return KPM_OK;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  cudaError_t e = palloc((void**)p, count * sizeof(T), 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e != cudaSuccess) {
     *p = nullptr;
-    return cuda_fail(e, "cudaMalloc");
+    return cuda_fail(e, "device allocation");
   }
   return KPM_OK;
 }
 
-void dfree(void* p) {
-  if (p) cudaFree(p);
-}
-
+void dfree(void* p) { pfree(p, 0); }
 
 kpm_status check_device(int* dev) {
   int n = 0;
@@ -172,19 +213,22 @@ kpm_status ensure_scaled(kpm_handle_s* h, int slot, bool fp32) {
   const size_t c = h->cplx ? 2 : 1;
   if (h->stencil) {
     if (h->has_hop && !h->d_hs[slot]) {
-      void* p = nullptr;
-      KPM_CUDA(cudaMalloc(&p, (size_t)h->n * h->geom.dims * c * s));
+      char* p = nullptr;
+      kpm_status st = dalloc(&p, (size_t)h->n * h->geom.dims * c * s);
+      if (st != KPM_OK) return st;
       h->d_hs[slot] = p;
     }
     if (h->has_onsite && !h->d_ds[slot]) {
-      void* p = nullptr;
-      KPM_CUDA(cudaMalloc(&p, (size_t)h->n * s));
+      char* p = nullptr;
+      kpm_status st = dalloc(&p, (size_t)h->n * s);
+      if (st != KPM_OK) return st;
       h->d_ds[slot] = p;
     }
   } else if (!h->d_vals[slot] && h->nnz > 0) {
-    void* p = nullptr;
+    char* p = nullptr;
     const size_t entries = h->ell_w > 0 ? (size_t)h->n * h->ell_w : (size_t)h->nnz;
-    KPM_CUDA(cudaMalloc(&p, entries * c * s));
+    kpm_status st = dalloc(&p, entries * c * s);
+    if (st != KPM_OK) return st;
     h->d_vals[slot] = p;
   }
   return KPM_OK;
@@ -208,8 +252,9 @@ kpm_status common_init(kpm_handle_s* h) {
   if (st != KPM_OK) return st;
   h->device = dev;
   KPM_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
-  KPM_CUDA(cudaMalloc((void**)&h->d_sc, 3 * sizeof(ScalarBlock)));
-  KPM_CUDA(cudaMalloc((void**)&h->d_prm, sizeof(RunParams)));
+  kpm_status st0 = dalloc(&h->d_sc, 3);
+  if (st0 == KPM_OK) st0 = dalloc(&h->d_prm, 1);
+  if (st0 != KPM_OK) return st0;
   KPM_CUDA(cudaMemset(h->d_prm, 0, sizeof(RunParams)));
   KPM_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   return KPM_OK;
@@ -235,6 +280,7 @@ void destroy_handle(kpm_handle_s* h) {
   dfree(h->d_sc);
   dfree(h->d_prm);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  cudaStreamSynchronize(0);
   delete h;
 }
 
@@ -385,7 +431,23 @@ kpm_status kpm_create_stencil(const kpm_stencil_desc* d, kpm_field field, kpm_ha
   }
   h->t_re = d->t_re;
   h->t_im = h->cplx ? d->t_im : 0.0;
-  h->nnz = stencil_nnz(d, field == KPM_COMPLEX ? 2 : 1, n);
+  // stored entries: closed form for unmasked lattices, one host pass otherwise
+  if (d->bond_mask) {
+    h->nnz = stencil_nnz(d, field == KPM_COMPLEX ? 2 : 1, n);
+  } else {
+    int64_t nnz = 0;
+    bool diag = d->onsite != nullptr;
+    for (int k = 0; k < d->dims; ++k) {
+      const int64_t Lk = d->L[k], lines_k = n / Lk;
+      if (d->periodic[k]) {
+        if (Lk == 1) diag = true;                 // self bond: on the diagonal
+        else nnz += lines_k * (Lk == 2 ? 2 : 2 * Lk);
+      } else {
+        nnz += lines_k * 2 * (Lk - 1);
+      }
+    }
+    h->nnz = nnz + (diag ? n : 0);
+  }
   if ((st = common_init(h)) != KPM_OK) {
     destroy_handle(h);
     return st;
@@ -397,7 +459,13 @@ kpm_status kpm_create_stencil(const kpm_stencil_desc* d, kpm_field field, kpm_ha
     cudaError_t e = cudaMemcpy(h->d_onsite, d->onsite, n * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { destroy_handle(h); return cuda_fail(e, "copy onsite"); }
   }
-  if (d->hop || d->bond_mask) {
+  if (d->hop && !d->bond_mask) {
+    h->has_hop = true;
+    const size_t cnt = (size_t)n * d->dims * c;
+    if ((st = dalloc(&h->d_hop, cnt)) != KPM_OK) { destroy_handle(h); return st; }
+    cudaError_t e = cudaMemcpy(h->d_hop, d->hop, cnt * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { destroy_handle(h); return cuda_fail(e, "copy hop"); }
+  } else if (d->bond_mask) {
     h->has_hop = true;
     std::vector<double> hop((size_t)n * d->dims * c);
     for (int64_t i = 0; i < n; ++i)
@@ -542,7 +610,7 @@ kpm_status kpm_bounds(kpm_handle h, int lanczos_steps, double pad_eps, uint64_t 
   if (!(pad_eps >= 0.0 && pad_eps < 1.0)) return fail(KPM_EINVAL, "pad_eps must be in [0, 1)");
   KPM_CUDA(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
-  const int nblk = (int)std::min<int64_t>((h->n + 255) / 256, 4 * (int64_t)h->num_sms);
+  const int nblk = (int)std::min<int64_t>((h->n + 255) / 256, 2 * (int64_t)h->num_sms);
   const int k = (int)std::min<int64_t>(lanczos_steps, h->n);
   const int64_t len = 2 * h->n;  // flat FP64 scalars of one Lanczos vector
   double *pmin = nullptr, *pmax = nullptr, *gersh = nullptr, *out = nullptr;
@@ -602,13 +670,11 @@ kpm_status kpm_bounds(kpm_handle h, int lanczos_steps, double pad_eps, uint64_t 
       KPM_TRY(launch_step(h->stencil, false, h->cplx, MODE_SPMV, sa, LaunchCfg{block, grid}, st));
       for (int pass = 0; pass < 2; ++pass) {
         KPM_TRY(launch_dots(h->cplx, h->n, Q, len, j, y, part, nblk, st));
-        KPM_TRY(launch_dots_final(part, nblk, j, coef, st));
-        if (pass == 0) KPM_TRY(launch_store_alpha(coef, j, alpha, st));
+        KPM_TRY(launch_dots_final(part, nblk, j, coef, pass == 0 ? alpha : nullptr, st));
         KPM_TRY(launch_gs_update(h->cplx, h->n, Q, len, j, coef, y, st));
       }
       KPM_TRY(launch_norm2(h->n, y, part, nblk, st));
-      KPM_TRY(launch_norm_final(part, nblk, beta, j, st));
-      KPM_TRY(launch_lanczos_next(h->n, y, beta, j, Q + (size_t)(j + 1) * len, st));
+      KPM_TRY(launch_lanczos_next(h->n, y, part, nblk, beta, j, Q + (size_t)(j + 1) * len, st));
     }
   }
   KPM_TRY(launch_tridiag_bounds(alpha, beta, k, gersh, pad_eps, out, st));
@@ -667,15 +733,23 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
       dfree(w.v[1]);
       w.v[0] = w.v[1] = nullptr;
       w.vbytes = 0;
-      KPM_CUDA(cudaMalloc(&w.v[0], vbytes));
-      KPM_CUDA(cudaMalloc(&w.v[1], vbytes));
+      char *v0 = nullptr, *v1 = nullptr;
+      kpm_status sa = dalloc(&v0, vbytes);
+      if (sa == KPM_OK) sa = dalloc(&v1, vbytes);
+      if (sa != KPM_OK) {
+        dfree(v0);
+        return sa;
+      }
+      w.v[0] = v0;
+      w.v[1] = v1;
       w.vbytes = vbytes;
     }
     if (w.sums_bytes < sums_bytes) {
       dfree(w.sums);
       w.sums = nullptr;
       w.sums_bytes = 0;
-      KPM_CUDA(cudaMalloc((void**)&w.sums, sums_bytes));
+      kpm_status sa = dalloc((char**)&w.sums, sums_bytes);
+      if (sa != KPM_OK) return sa;
       w.sums_bytes = sums_bytes;
     }
     StepArgs proto = base_args(h, slot, Rp, G);
@@ -684,7 +758,10 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
     w.proto = proto;
     dfree(w.ring);
     w.ring = nullptr;
-    KPM_CUDA(cudaMalloc((void**)&w.ring, (size_t)RING * grid * 2 * Rp * sizeof(double)));
+    {
+      kpm_status sa = dalloc(&w.ring, (size_t)RING * grid * 2 * Rp);
+      if (sa != KPM_OK) return sa;
+    }
     w.Rp = Rp;
     w.prec = p->precision;
     w.M = M;
@@ -746,7 +823,10 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
     w.per_vec = nullptr;
     w.mu = nullptr;
     w.out_bytes = 0;
-    KPM_CUDA(cudaMalloc((void**)&w.per_vec, out_bytes));
+    {
+      kpm_status sa = dalloc((char**)&w.per_vec, out_bytes);
+      if (sa != KPM_OK) return sa;
+    }
     w.mu = w.per_vec + (size_t)S * R * M;
     w.out_bytes = out_bytes;
   }
@@ -773,7 +853,10 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
         dfree(w.v0stage);
         w.v0stage = nullptr;
         w.v0stage_bytes = 0;
-        KPM_CUDA(cudaMalloc((void**)&w.v0stage, vb));
+        {
+          kpm_status sa = dalloc((char**)&w.v0stage, vb);
+          if (sa != KPM_OK) return sa;
+        }
         w.v0stage_bytes = vb;
       }
       KPM_CUDA(cudaMemcpyAsync(w.v0stage, p->user_v0, vb, cudaMemcpyHostToDevice, st));

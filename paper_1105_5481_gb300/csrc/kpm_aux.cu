@@ -282,12 +282,16 @@ __global__ void gershgorin_csr_kernel(bool cplx, int64_t n, const int64_t* __res
 }
 
 __global__ void minmax_final_kernel(const double* pmin, const double* pmax, int nblk, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double lo = INFINITY, hi = -INFINITY;
-    for (int b = 0; b < nblk; ++b) {
-      lo = fmin(lo, pmin[b]);
-      hi = fmax(hi, pmax[b]);
-    }
+  double lo = INFINITY, hi = -INFINITY;
+  for (int b = threadIdx.x; b < nblk; b += 32) {
+    lo = fmin(lo, pmin[b]);
+    hi = fmax(hi, pmax[b]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if (threadIdx.x == 0) {
     out[0] = lo;
     out[1] = hi;
   }
@@ -309,50 +313,68 @@ __global__ void lanczos_start_kernel(bool cplx, int64_t n, int stride_scal,
   }
 }
 
-// part[blk][l][2] = partial <q_l | y> for l = 0..j  (complex: re, im; real: re, 0)
+// part[l][blk][2] = partial <q_l | y> (complex: re, im; real: re, 0): one
+// block row per l (blockIdx.y), so all j+1 products run at once; each block
+// reduces with warp shuffles and one shared-memory stage.
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __global__ void dots_kernel(bool cplx, int64_t len, const double* __restrict__ Q, int64_t ldq,
-                            int j, const double* __restrict__ y, double* part) {
-  extern __shared__ double sh[];
-  const int nl = j + 1;
-  for (int l = 0; l < nl; ++l) {
-    double re = 0.0, im = 0.0;
-    const double* q = Q + (size_t)l * ldq;
-    if (cplx) {
-      for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len / 2;
-           e += (int64_t)gridDim.x * blockDim.x) {
-        const double qr = q[2 * e], qi = q[2 * e + 1], yr = y[2 * e], yi = y[2 * e + 1];
-        re += qr * yr + qi * yi;
-        im += qr * yi - qi * yr;
-      }
-    } else {
-      for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
-           e += (int64_t)gridDim.x * blockDim.x)
-        re += q[e] * y[e];
+                            const double* __restrict__ y, double* part) {
+  __shared__ double sh[2][32];
+  const int l = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double re = 0.0, im = 0.0;
+  const double* q = Q + (size_t)l * ldq;
+  if (cplx) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len / 2;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const double2 qv = reinterpret_cast<const double2*>(q)[e];
+      const double2 yv = reinterpret_cast<const double2*>(y)[e];
+      re += qv.x * yv.x + qv.y * yv.y;
+      im += qv.x * yv.y - qv.y * yv.x;
     }
-    sh[threadIdx.x] = re;
-    sh[blockDim.x + threadIdx.x] = im;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if ((int)threadIdx.x < o) {
-        sh[threadIdx.x] += sh[threadIdx.x + o];
-        sh[blockDim.x + threadIdx.x] += sh[blockDim.x + threadIdx.x + o];
-      }
-      __syncthreads();
+  } else {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * blockDim.x)
+      re += q[e] * y[e];
+  }
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if (lane == 0) {
+    sh[0][warp] = re;
+    sh[1][warp] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      a += sh[0][w];
+      b += sh[1][w];
     }
-    if (threadIdx.x == 0) {
-      part[((size_t)blockIdx.x * nl + l) * 2] = sh[0];
-      part[((size_t)blockIdx.x * nl + l) * 2 + 1] = sh[blockDim.x];
-    }
-    __syncthreads();
+    part[((size_t)l * gridDim.x + blockIdx.x) * 2] = a;
+    part[((size_t)l * gridDim.x + blockIdx.x) * 2 + 1] = b;
   }
 }
 
-__global__ void dots_final_kernel(const double* part, int nblk, int j, double* out) {
+// out[2l + c] = sum over blocks of part[l][blk][c]: one warp per output, lanes
+// striding over the blocks, then a shuffle sum (fixed order).  alpha != NULL:
+// also alpha[j] = Re out[j] (the Lanczos diagonal).
+__global__ void dots_final_kernel(const double* part, int nblk, int j, double* out,
+                                  double* alpha) {
   const int nl = j + 1;
-  for (int o = threadIdx.x; o < 2 * nl; o += blockDim.x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = warp; o < 2 * nl; o += nw) {
+    const int l = o / 2, c = o % 2;
     double acc = 0.0;
-    for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * 2 * nl + o];
-    out[o] = acc;
+    for (int b = lane; b < nblk; b += 32) acc += part[((size_t)l * nblk + b) * 2 + c];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      out[o] = acc;
+      if (alpha && o == 2 * j) alpha[j] = acc;
+    }
   }
 }
 
@@ -383,10 +405,6 @@ __global__ void gs_update_kernel(bool cplx, int64_t len, const double* __restric
   }
 }
 
-__global__ void store_alpha_kernel(const double* coef, int j, double* alpha) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) alpha[j] = coef[2 * j];
-}
-
 __global__ void norm_partial_kernel(int64_t len, const double* __restrict__ y, double* part) {
   __shared__ double sh[256];
   double acc = 0.0;
@@ -402,18 +420,24 @@ __global__ void norm_partial_kernel(int64_t len, const double* __restrict__ y, d
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-__global__ void norm_final_kernel(const double* part, int nblk, double* beta, int j) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double acc = 0.0;
-    for (int b = 0; b < nblk; ++b) acc += part[b];
-    beta[j] = sqrt(acc);
-  }
-}
-
+// beta_j = ||y|| from the norm partials (each block sums them in the same
+// order; block 0 stores beta_j), then q_{j+1} = y / beta_j.
 __global__ void lanczos_next_kernel(int64_t len, const double* __restrict__ y,
-                                    const double* __restrict__ beta, int j, double* qnext) {
-  const double b = beta[j];
-  const double inv = b > 0.0 ? 1.0 / b : 0.0;
+                                    const double* __restrict__ part, int nblk, double* beta, int j,
+                                    double* qnext) {
+  __shared__ double s_inv;
+  if (threadIdx.x < 32) {
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += 32) acc += part[k];
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) {
+      const double b = sqrt(acc);
+      if (blockIdx.x == 0) beta[j] = b;
+      s_inv = b > 0.0 ? 1.0 / b : 0.0;
+    }
+  }
+  __syncthreads();
+  const double inv = s_inv;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
        e += (int64_t)gridDim.x * blockDim.x)
     qnext[e] = y[e] * inv;
@@ -434,14 +458,25 @@ __device__ int sturm_count(const double* al, const double* be, int m, double x) 
   return cnt;
 }
 
-// k-th smallest eigenvalue (0-based) by bisection to full precision.
-__device__ double bisect_eig(const double* al, const double* be, int m, int k, double lo,
-                             double hi) {
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_count(al, be, m, mid) > k) hi = mid;
-    else lo = mid;
+// k-th smallest eigenvalue (0-based), by multisection with one warp: every
+// lane evaluates the Sturm count at one of 32 interior points of the current
+// bracket, which shrinks 33-fold per round, down to adjacent doubles.  All 32
+// lanes of the calling warp must call it with the same arguments.
+__device__ double multisect_eig(const double* al, const double* be, int m, int k, double lo,
+                                double hi) {
+  const int lane = threadIdx.x & 31;
+  for (int it = 0; it < 64; ++it) {
+    const double w = (hi - lo) / 33.0;
+    const double x = lo + w * (double)(lane + 1);
+    const bool above = sturm_count(al, be, m, x) > k;  // eigenvalue k lies below x
+    const unsigned ball = __ballot_sync(0xffffffffu, above);
+    const int first = ball ? __ffs(ball) - 1 : 32;      // first point above eigenvalue k
+    const double nlo = first == 0 ? lo : lo + w * (double)first;
+    const double nhi = first == 32 ? hi : lo + w * (double)(first + 1);
+    if (!(nlo > lo || nhi < hi) || nhi - nlo <= 0.0) break;
+    lo = nlo;
+    hi = nhi;
+    if (hi - lo <= 4.0 * fmax(fabs(lo), fabs(hi)) * 1.1102230246251565e-16) break;
   }
   return 0.5 * (lo + hi);
 }
@@ -511,22 +546,26 @@ __device__ double last_component(const double* al, const double* be, int m, doub
   return fabs(x[m - 1]) / sqrt(n2);
 }
 
-// out = [emin, emax, a, b, theta_min, theta_max, beta_k, m]
+// out = [emin, emax, a, b, theta_min, theta_max, beta_k, m].  Two warps:
+// warp 0 finds theta_min, warp 1 theta_max (multisection), lane 0 of each
+// its eigenvector's last component; thread 0 then combines.
 __global__ void tridiag_bounds_kernel(const double* alpha, const double* beta, int kmax,
                                       const double* gersh, double pad_eps, double* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ double s_theta[2], s_last[2];
+  __shared__ int s_m;
+  __shared__ double s_bk, s_lo, s_hi;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double gmin = gersh[0], gmax = gersh[1];
-  double emin = gmin, emax = gmax, tmin = gmin, tmax = gmax, bk = 0.0;
-  int m = 0;
-  if (kmax > 0) {
-    m = kmax;
+  if (threadIdx.x == 0) {
+    int m = kmax;
     for (int j = 0; j < kmax; ++j) {
       if (beta[j] <= 1e-12 * fmax(1.0, fabs(alpha[j]))) {
         m = j + 1;
         break;
       }
     }
-    bk = beta[m - 1];
+    s_m = m;
+    s_bk = m > 0 ? beta[m - 1] : 0.0;
     double lo = INFINITY, hi = -INFINITY;
     for (int j = 0; j < m; ++j) {
       const double r = (j > 0 ? fabs(beta[j - 1]) : 0.0) + (j + 1 < m ? fabs(beta[j]) : 0.0);
@@ -534,14 +573,27 @@ __global__ void tridiag_bounds_kernel(const double* alpha, const double* beta, i
       hi = fmax(hi, alpha[j] + r);
     }
     const double span = fmax(hi - lo, 1e-300);
-    lo -= 1e-3 * span;
-    hi += 1e-3 * span;
-    tmin = bisect_eig(alpha, beta, m, 0, lo, hi);
-    tmax = bisect_eig(alpha, beta, m, m - 1, lo, hi);
-    const double smin = m > 1 ? last_component(alpha, beta, m, tmin, span) : 1.0;
-    const double smax = m > 1 ? last_component(alpha, beta, m, tmax, span) : 1.0;
-    emin = fmax(gmin, tmin - bk * smin);
-    emax = fmin(gmax, tmax + bk * smax);
+    s_lo = lo - 1e-3 * span;
+    s_hi = hi + 1e-3 * span;
+  }
+  __syncthreads();
+  const int m = s_m;
+  if (m > 0 && warp < 2) {
+    const double th = multisect_eig(alpha, beta, m, warp == 0 ? 0 : m - 1, s_lo, s_hi);
+    if (lane == 0) {
+      s_theta[warp] = th;
+      s_last[warp] = m > 1 ? last_component(alpha, beta, m, th, s_hi - s_lo) : 1.0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double emin = gmin, emax = gmax, tmin = gmin, tmax = gmax;
+  const double bk = s_bk;
+  if (m > 0) {
+    tmin = s_theta[0];
+    tmax = s_theta[1];
+    emin = fmax(gmin, tmin - bk * s_last[0]);
+    emax = fmin(gmax, tmax + bk * s_last[1]);
   }
   out[0] = emin;
   out[1] = emax;
@@ -709,12 +761,13 @@ cudaError_t launch_lanczos_start(bool cplx, int64_t n, unsigned long long seed, 
 
 cudaError_t launch_dots(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
                         const double* y, double* part, int nblk, cudaStream_t st) {
-  dots_kernel<<<nblk, 256, 2 * 256 * sizeof(double), st>>>(cplx, 2 * n, Q, ldq, j, y, part);
+  dots_kernel<<<dim3(nblk, j + 1), 256, 0, st>>>(cplx, 2 * n, Q, ldq, y, part);
   return counted(cudaGetLastError());
 }
 
-cudaError_t launch_dots_final(const double* part, int nblk, int j, double* out, cudaStream_t st) {
-  dots_final_kernel<<<1, 128, 0, st>>>(part, nblk, j, out);
+cudaError_t launch_dots_final(const double* part, int nblk, int j, double* out, double* alpha,
+                              cudaStream_t st) {
+  dots_final_kernel<<<1, 1024, 0, st>>>(part, nblk, j, out, alpha);
   return counted(cudaGetLastError());
 }
 
@@ -724,32 +777,21 @@ cudaError_t launch_gs_update(bool cplx, int64_t n, const double* Q, int64_t ldq,
   return counted(cudaGetLastError());
 }
 
-cudaError_t launch_store_alpha(const double* coef, int j, double* alpha, cudaStream_t st) {
-  store_alpha_kernel<<<1, 32, 0, st>>>(coef, j, alpha);
-  return counted(cudaGetLastError());
-}
-
 cudaError_t launch_norm2(int64_t n, const double* y, double* part, int nblk, cudaStream_t st) {
   norm_partial_kernel<<<nblk, 256, 0, st>>>(2 * n, y, part);
   return counted(cudaGetLastError());
 }
 
-cudaError_t launch_norm_final(const double* part, int nblk, double* beta, int j,
-                              cudaStream_t st) {
-  norm_final_kernel<<<1, 32, 0, st>>>(part, nblk, beta, j);
-  return counted(cudaGetLastError());
-}
-
-cudaError_t launch_lanczos_next(int64_t n, const double* y, const double* beta, int j,
-                                double* qnext, cudaStream_t st) {
-  lanczos_next_kernel<<<blocks_for(2 * n, 256), 256, 0, st>>>(2 * n, y, beta, j, qnext);
+cudaError_t launch_lanczos_next(int64_t n, const double* y, const double* part, int nblk,
+                                double* beta, int j, double* qnext, cudaStream_t st) {
+  lanczos_next_kernel<<<blocks_for(2 * n, 256), 256, 0, st>>>(2 * n, y, part, nblk, beta, j, qnext);
   return counted(cudaGetLastError());
 }
 
 cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, int m,
                                   const double* gersh, double pad_eps, double* out,
                                   cudaStream_t st) {
-  tridiag_bounds_kernel<<<1, 32, 0, st>>>(alpha, beta, m, gersh, pad_eps, out);
+  tridiag_bounds_kernel<<<1, 64, 0, st>>>(alpha, beta, m, gersh, pad_eps, out);
   return counted(cudaGetLastError());
 }
 

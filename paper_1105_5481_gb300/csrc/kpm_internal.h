@@ -141,15 +141,13 @@ cudaError_t launch_lanczos_start(bool cplx, int64_t n, unsigned long long seed, 
                                  cudaStream_t st);
 cudaError_t launch_dots(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
                         const double* y, double* part, int nblk, cudaStream_t st);
-cudaError_t launch_dots_final(const double* part, int nblk, int j, double* out, cudaStream_t st);
+cudaError_t launch_dots_final(const double* part, int nblk, int j, double* out, double* alpha,
+                              cudaStream_t st);
 cudaError_t launch_gs_update(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
                              const double* coef, double* y, cudaStream_t st);
-cudaError_t launch_store_alpha(const double* coef, int j, double* alpha, cudaStream_t st);
 cudaError_t launch_norm2(int64_t n, const double* y, double* part, int nblk, cudaStream_t st);
-cudaError_t launch_norm_final(const double* part, int nblk, double* beta, int j,
-                              cudaStream_t st);
-cudaError_t launch_lanczos_next(int64_t n, const double* y, const double* beta, int j,
-                                double* qnext, cudaStream_t st);
+cudaError_t launch_lanczos_next(int64_t n, const double* y, const double* part, int nblk,
+                                double* beta, int j, double* qnext, cudaStream_t st);
 cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, int m,
                                   const double* gersh, double pad_eps, double* out,
                                   cudaStream_t st);

@@ -75,6 +75,7 @@ def test_moments_match_oracle(K, name, csr, prec):
     v0 = I.random_block(seed, H.n, R, cplx)
     mu_o, per_o = O.moments_doubling(H, a, b, v0, M)
     with handle(K, kw, cplx, csr) as h:
+        assert K.kpm_info(h)["nnz"] == H.nnz      # stored entries of H (closed form or count)
         mu, per = K.kpm_moments(h, M, R, a, b, seed=seed, precision=prec, per_vec=True)
     tol = TOL[prec]
     assert np.abs(per - per_o).max() <= tol
