@@ -206,6 +206,17 @@ def profile_run(prec, workload):
     from paper_1105_5481_gb300 import kpm as K
 
     B.build()
+    if workload == "batch_2d_256":
+        insts = I.batch_workload(3, 256)
+        hs = [K.kpm_create_stencil(2, x["L"], onsite=x["onsite"]) for x in insts]
+        ab = [K.kpm_bounds(h, 0, WORKLOAD["pad_eps"])[2:] for h in hs]
+        with K.kpm_batch_create(hs, [x["M"] for x in insts], 16, [p[0] for p in ab],
+                                [p[1] for p in ab], [x["seed"] for x in insts], prec) as bt:
+            K.kpm_batch_set_config(bt, 4, 2, 100)
+            for _ in range(2):
+                mu = K.kpm_batch_run(bt)
+        print(json.dumps({"profile": prec, "workload": workload, "mu0": float(mu[0])}))
+        return 0
     w = I.workload(workload)
     if workload == "csr_spin_dilute_L160":
         h = csr_handle(K, w)

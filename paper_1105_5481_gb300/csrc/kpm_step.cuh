@@ -122,6 +122,16 @@ struct ChunkF64 {
 #pragma unroll
     for (int k = 0; k < VEC; ++k) { A[k] = s.a[k]; B[k] = s.b[k]; }
   }
+  // sum over the lanes of a warp that hold the same columns (xor offsets Gt .. 16)
+  static __device__ __forceinline__ void warp_reduce(Acc& s, int Gt) {
+    for (int off = Gt; off < 32; off <<= 1) {
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) {
+        s.a[k] += __shfl_xor_sync(0xffffffffu, s.a[k], off);
+        s.b[k] += __shfl_xor_sync(0xffffffffu, s.b[k], off);
+      }
+    }
+  }
 };
 
 // FP32: 32 bytes = 8 floats held as 4 packed pairs.  Complex: p[0] = (re0,
@@ -131,6 +141,21 @@ __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {  // a - b
   return __ffma2_rn(b, f2(-1.0f), a);
 }
+// (s1, c1) += (s2, c2) for compensated pairs whose value is s - c: the sum of
+// the leading parts with its exact rounding error (TwoSum, Knuth), the error
+// folded into the compensation.
+__device__ __forceinline__ void pair_add2(float2& s1, float2& c1, float2 s2, float2 c2) {
+  const float2 t = __fadd2_rn(s1, s2);
+  const float2 bb = sub2(t, s1);
+  const float2 err = __fadd2_rn(sub2(s1, sub2(t, bb)), sub2(s2, bb));  // s1 + s2 = t + err
+  c1 = sub2(__fadd2_rn(c1, c2), err);
+  s1 = t;
+}
+
+__device__ __forceinline__ float2 shfl2(float2 v, int off) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off));
+}
+
 // Kahan step: s += v with compensation c
 __device__ __forceinline__ void kahan2(float2& s, float2& c, float2 v) {
   const float2 y = sub2(v, c);
@@ -229,6 +254,18 @@ struct ChunkF32 {
       for (int j = 0; j < 4; ++j) {
         kahan2(s.a[j], s.ca[j], __fmul2_rn(x.p[j], x.p[j]));
         kahan2(s.b[j], s.cb[j], __fmul2_rn(y.p[j], x.p[j]));
+      }
+    }
+  }
+  // sum over the lanes of a warp that hold the same columns, in compensated
+  // FP32 pairs (FP32 pipes; accuracy of about 2^-44 relative)
+  static __device__ __forceinline__ void warp_reduce(Acc& s, int Gt) {
+#pragma unroll
+    for (int j = 0; j < VEC / 2; ++j) {
+#pragma unroll 1
+      for (int off = Gt; off < 32; off <<= 1) {
+        pair_add2(s.a[j], s.ca[j], shfl2(s.a[j], off), shfl2(s.ca[j], off));
+        pair_add2(s.b[j], s.cb[j], shfl2(s.b[j], off), shfl2(s.cb[j], off));
       }
     }
   }
@@ -662,29 +699,25 @@ __device__ __forceinline__ void step_rows(const StepArgs& a, const OP& op, int c
 }
 
 // CTA-wide sum of the threads' moment dots: lanes sharing a column are
-// combined with warp shuffles, warps in shared memory `red` in warp order.
+// combined with warp shuffles in the chunk's own precision (compensated FP32
+// pairs on the FP32 path), then converted to FP64 and summed over the warps in
+// shared memory `red` in warp order.
 // Writes dst[which * Rp + ycol * Rt + col] for which in {A, B} and the Rt
 // columns of this column slice.  All threads of the CTA must call it.
 template <class CH>
-__device__ __forceinline__ void cta_reduce(const StepArgs& a, const typename CH::Acc& s, int ycol,
+__device__ __forceinline__ void cta_reduce(const StepArgs& a, typename CH::Acc s, int ycol,
                                            double* red, double* dst) {
   constexpr int VEC = CH::VEC;
   const int Gt = a.Gt;
   const int t = threadIdx.x;
   const int cl = t % Gt, q = t / Gt, spi = blockDim.x / Gt;
+  if (Gt < 32) CH::warp_reduce(s, Gt);
   double dA[VEC], dB[VEC];
   CH::acc_out(s, dA, dB);
   const int lane = t & 31, warp = t >> 5;
   bool rep;
   int qrep, nq;
   if (Gt < 32) {
-    for (int off = Gt; off < 32; off <<= 1) {
-#pragma unroll
-      for (int k = 0; k < VEC; ++k) {
-        dA[k] += __shfl_xor_sync(0xffffffffu, dA[k], off);
-        dB[k] += __shfl_xor_sync(0xffffffffu, dB[k], off);
-      }
-    }
     rep = lane < Gt;
     qrep = warp;
     nq = blockDim.x >> 5;

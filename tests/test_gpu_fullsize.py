@@ -51,3 +51,30 @@ def test_csr_L160_full_size_prefix(K):
     v0 = I.random_columns(seed, H.n, w["R"], c, True)
     _, per_o = O.moments_doubling(H, a, b, v0, 32)
     assert np.abs(per[c, :32] - per_o).max() <= 1e-5
+
+
+def test_batch_256_full_size_sampled_instances(K):
+    # the full batch workload (256 2D disorder realisations, L 16..128, M 128..2048,
+    # R = 16 FP32) in one persistent launch; the oracle recomputes one vector column
+    # of four sampled instances at full M, and every instance obeys the invariants
+    insts = I.batch_workload(3, 256)
+    R = 16
+    hs = [K.kpm_create_stencil(2, x["L"], onsite=x["onsite"]) for x in insts]
+    ab = [K.kpm_bounds(h, 0, 0.01)[2:] for h in hs]
+    Ms = [x["M"] for x in insts]
+    with K.kpm_batch_create(hs, Ms, R, [p[0] for p in ab], [p[1] for p in ab],
+                            [x["seed"] for x in insts], "fp32") as bt:
+        parts = bt.split(K.kpm_batch_run(bt))
+    sizes = [x["L"][0] for x in insts]
+    picks = {int(np.argmin(sizes)), int(np.argmax(sizes)), 17, 200}
+    for k, mu in enumerate(parts):
+        assert abs(mu[0] - 1.0) <= 1e-6 and np.abs(mu).max() <= 1.0 + 1e-5
+    for k in sorted(picks):
+        x = insts[k]
+        H = O.lattice_hamiltonian(x["L"], onsite=x["onsite"])
+        a, b = ab[k]
+        v0 = I.random_block(x["seed"], H.n, R, False)
+        mu_o, _ = O.moments_doubling(H, a, b, v0, x["M"])
+        assert np.abs(parts[k] - mu_o).max() <= 1e-5, k
+    for h in hs:
+        h.close()
