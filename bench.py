@@ -49,25 +49,30 @@ STEP_SOURCES = ["paper_1105_5481_gb300/csrc/kpm_step.cuh",
                 "paper_1105_5481_gb300/csrc/kpm_step_dispatch.cuh",
                 "paper_1105_5481_gb300/csrc/kpm_step_f32.cu",
                 "paper_1105_5481_gb300/csrc/kpm_internal.h"]
-# DRAM bytes (read + write) per fused-step launch from one ncu capture, keyed by
-# workload, with the hash of the kernel sources it was taken on
-# (profiles/cheb_step_fp32_cubic_spin_L64.md); reported only while the hash matches.
-MEASURED_TRAFFIC = {"cubic_spin_L64": (380.64e6, "99dbc3236aa3f62e")}
+BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
+                                "paper_1105_5481_gb300/csrc/kpm_batch_dispatch.cuh",
+                                "paper_1105_5481_gb300/csrc/kpm_batch_f32.cu"]
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture,
+# keyed by workload (and launch configuration), with the hash of the kernel sources
+# it was taken on (profiles/cheb_step_fp32_cubic_spin_L64.md,
+# profiles/batch_kernel_fp32_batch_2d_256.md); reported only while the hash matches.
+MEASURED_TRAFFIC = {"cubic_spin_L64": (381.42e6, "step", "10b8caaedfe48719"),
+                    "batch_2d_256/C4/chunk2/clusters74": (77.55e9, "batch", "1c43c20496f7dd17")}
 
 
-def step_source_hash():
+def step_source_hash(kind="step"):
     import hashlib
 
     h = hashlib.sha256()
-    for f in STEP_SOURCES:
+    for f in (STEP_SOURCES if kind == "step" else BATCH_SOURCES):
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload):
-    t = MEASURED_TRAFFIC.get(workload)
-    return t[0] if t and t[1] == step_source_hash() else None
+def measured_traffic(key):
+    t = MEASURED_TRAFFIC.get(key)
+    return t[0] if t and t[2] == step_source_hash(t[1]) else None
 
 
 # FP64 FMA issue rate of GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flop at the
@@ -358,7 +363,9 @@ def batch_leg(args):
                    "launch": "one persistent cluster kernel per batch, CUDA graph replay",
                    "autotuned": info, "tune_s": tune_s, "l2": "instances' vectors mostly L2-resident"},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "traffic": None, "bytes_per_launch": byts, "peak_kind": peak_kind,
+                     "traffic": measured_traffic("batch_2d_256/C%d/chunk%d/clusters%d" % (
+                         info["cluster"], info["chunk"], info["clusters"])),
+                     "bytes_per_launch": byts, "peak_kind": peak_kind,
                      "note": "algorithmic bytes of all instances per batch launch; the working "
                              "set of the active instances is L2-resident, so frac can exceed 1"},
         "per_instance_calls": {"ms": ms_single, "speedup_of_batch": ms_single / ms},
