@@ -614,12 +614,12 @@ kpm_status kpm_bounds(kpm_handle h, int lanczos_steps, double pad_eps, uint64_t 
   const int k = (int)std::min<int64_t>(lanczos_steps, h->n);
   const int64_t len = 2 * h->n;  // flat FP64 scalars of one Lanczos vector
   double *pmin = nullptr, *pmax = nullptr, *gersh = nullptr, *out = nullptr;
-  double *Q = nullptr, *y = nullptr, *part = nullptr, *coef = nullptr, *alpha = nullptr,
-         *beta = nullptr;
+  double *Q = nullptr, *y = nullptr, *part = nullptr, *part_loc = nullptr, *coef = nullptr,
+         *alpha = nullptr, *beta = nullptr;
   kpm_status st_ = KPM_OK;
   auto cleanup = [&]() {
     dfree(pmin); dfree(pmax); dfree(gersh); dfree(out); dfree(Q); dfree(y); dfree(part);
-    dfree(coef); dfree(alpha); dfree(beta);
+    dfree(part_loc); dfree(coef); dfree(alpha); dfree(beta);
   };
 #define KPM_TRY(call)                                \
   do {                                               \
@@ -645,7 +645,8 @@ kpm_status kpm_bounds(kpm_handle h, int lanczos_steps, double pad_eps, uint64_t 
   KPM_TRY(launch_minmax_final(pmin, pmax, nblk, gersh, st));
   if (k > 0) {
     if ((st_ = dalloc(&Q, (size_t)(k + 1) * len)) || (st_ = dalloc(&y, len)) ||
-        (st_ = dalloc(&part, (size_t)nblk * 2 * (k + 1))) || (st_ = dalloc(&coef, 2 * (k + 1)))) {
+        (st_ = dalloc(&part, (size_t)nblk * 2 * (k + 1))) || (st_ = dalloc(&part_loc, (size_t)nblk * 4)) ||
+        (st_ = dalloc(&coef, 2 * (k + 1)))) {
       cudaStreamSynchronize(st);
       cleanup();
       return st_;
@@ -668,12 +669,11 @@ kpm_status kpm_bounds(kpm_handle h, int lanczos_steps, double pad_eps, uint64_t 
       sa.w = nullptr;
       sa.partial = nullptr;
       KPM_TRY(launch_step(h->stencil, false, h->cplx, MODE_SPMV, sa, LaunchCfg{block, grid}, st));
-      for (int pass = 0; pass < 2; ++pass) {
-        KPM_TRY(launch_dots(h->cplx, h->n, Q, len, j, y, part, nblk, st));
-        KPM_TRY(launch_dots_final(part, nblk, j, coef, pass == 0 ? alpha : nullptr, st));
-        KPM_TRY(launch_gs_update(h->cplx, h->n, Q, len, j, coef, y, st));
-      }
-      KPM_TRY(launch_norm2(h->n, y, part, nblk, st));
+      // three-term step against q_j, q_{j-1}, then one full Gram-Schmidt pass
+      KPM_TRY(launch_lz_local_dots(h->cplx, h->n, Q, len, j, y, part_loc, nblk, st));
+      KPM_TRY(launch_lz_reorth_dots(h->cplx, h->n, Q, len, j, part_loc, y, part, alpha, nblk, st));
+      KPM_TRY(launch_dots_final(part, nblk, j, coef, st));
+      KPM_TRY(launch_lz_update_norm(h->cplx, h->n, Q, len, j, coef, y, part, nblk, st));
       KPM_TRY(launch_lanczos_next(h->n, y, part, nblk, beta, j, Q + (size_t)(j + 1) * len, st));
     }
   }

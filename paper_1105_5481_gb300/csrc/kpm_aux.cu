@@ -313,57 +313,195 @@ __global__ void lanczos_start_kernel(bool cplx, int64_t n, int stride_scal,
   }
 }
 
-// part[l][blk][2] = partial <q_l | y> (complex: re, im; real: re, 0): one
-// block row per l (blockIdx.y), so all j+1 products run at once; each block
-// reduces with warp shuffles and one shared-memory stage.
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-__global__ void dots_kernel(bool cplx, int64_t len, const double* __restrict__ Q, int64_t ldq,
-                            const double* __restrict__ y, double* part) {
-  __shared__ double sh[2][32];
-  const int l = blockIdx.y;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double re = 0.0, im = 0.0;
-  const double* q = Q + (size_t)l * ldq;
-  if (cplx) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len / 2;
-         e += (int64_t)gridDim.x * blockDim.x) {
-      const double2 qv = reinterpret_cast<const double2*>(q)[e];
-      const double2 yv = reinterpret_cast<const double2*>(y)[e];
-      re += qv.x * yv.x + qv.y * yv.y;
-      im += qv.x * yv.y - qv.y * yv.x;
+// Reorthogonalisation.  The vectors are n pairs (double2): complex entries,
+// or a real value beside a zero pad.  One Lanczos step j, after y = H q_j:
+//   lz_local_dots:   c = (<q_j|y>, <q_{j-1}|y>) per block
+//   lz_reorth_dots:  y' = y - c_j q_j - c_{j-1} q_{j-1} (the three-term step),
+//                    then <q_l|y'> for l = 0..j per block (one full classical
+//                    Gram-Schmidt pass), alpha_j = Re <q_j|y>
+//   dots_final:      the coefficients d_l summed over the blocks
+//   lz_update_norm:  y'' = y' - sum_l d_l q_l, per-block |y''|^2
+//   lanczos_next:    beta_j = |y''|, q_{j+1} = y'' / beta_j
+// GB300 runs FP64 at 1/64 of its FP32 rate, so these kernels are bound by
+// FP64 instruction issue; the per-block sums of many values use a
+// recursive-halving warp reduction (about one add per value per lane instead
+// of five) so that the reductions stay small beside the dot products.
+
+// Sums each of V values over the 32 lanes of a warp.  At each of the log2 V
+// exchange steps a lane keeps one half of its values and adds the partner
+// lane's copy of that half; the single value left is then summed over the
+// remaining lane bits.  The result is the total of value index
+// lane >> (5 - log2 V), the same in every lane that holds that index.
+template <int V>
+__device__ __forceinline__ double warp_multi_sum(double (&v)[V]) {
+  static_assert(V >= 1 && V <= 32 && (V & (V - 1)) == 0, "V: a power of two up to 32");
+  const int lane = threadIdx.x & 31;
+  int o = 16;
+#pragma unroll
+  for (int h = V / 2; h >= 1; h /= 2, o /= 2) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const double send = up ? v[i] : v[i + h];
+      const double keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
-  } else {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
-         e += (int64_t)gridDim.x * blockDim.x)
-      re += q[e] * y[e];
   }
-  re = warp_sum(re);
-  im = warp_sum(im);
-  if (lane == 0) {
-    sh[0][warp] = re;
-    sh[1][warp] = im;
-  }
+  double s = v[0];
+#pragma unroll
+  for (; o >= 1; o /= 2) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+constexpr int LZ_BLOCK = 256;
+constexpr int LZ_WARPS = LZ_BLOCK / 32;
+constexpr int LZ_TILE = 8;  // Gram-Schmidt columns per reduction tile
+
+// CTA sum of V values per thread (warp_multi_sum, then the warps in order);
+// threads t < V return the total of value t.  `red` holds LZ_WARPS * V doubles.
+template <int V>
+__device__ __forceinline__ double block_multi_sum(double (&v)[V], double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int SH = (V == 1) ? 5 : (V == 2) ? 4 : (V == 4) ? 3 : (V == 8) ? 2 : (V == 16) ? 1 : 0;
+  const double s = warp_multi_sum<V>(v);
+  if ((lane & ((1 << SH) - 1)) == 0) red[warp * V + (lane >> SH)] = s;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int w = 0; w < nw; ++w) {
-      a += sh[0][w];
-      b += sh[1][w];
-    }
-    part[((size_t)l * gridDim.x + blockIdx.x) * 2] = a;
-    part[((size_t)l * gridDim.x + blockIdx.x) * 2 + 1] = b;
+  double tot = 0.0;
+  if ((int)threadIdx.x < V)
+    for (int w = 0; w < LZ_WARPS; ++w) tot += red[w * V + threadIdx.x];
+  return tot;
+}
+
+// acc += conj(q) * y  (real: the value only)
+template <bool CPLX>
+__device__ __forceinline__ void cdot_acc(double& re, double& im, double2 q, double2 y) {
+  if constexpr (CPLX) {
+    re = fma(q.x, y.x, fma(q.y, y.y, re));
+    im = fma(q.x, y.y, fma(-q.y, y.x, im));
+  } else {
+    re = fma(q.x, y.x, re);
   }
 }
 
+// y -= c * q
+template <bool CPLX>
+__device__ __forceinline__ void caxpy_sub(double2& y, double cr, double ci, double2 q) {
+  if constexpr (CPLX) {
+    y.x = fma(-cr, q.x, fma(ci, q.y, y.x));
+    y.y = fma(-cr, q.y, fma(-ci, q.x, y.y));
+  } else {
+    y.x = fma(-cr, q.x, y.x);
+  }
+}
+
+// part[blk][4] = (<q_j|y>, <q_{j-1}|y>) as (re, im, re, im); qm = NULL at j = 0
+template <bool CPLX>
+__global__ void __launch_bounds__(LZ_BLOCK) lz_local_dots_kernel(int64_t n,
+                                                                 const double2* __restrict__ qj,
+                                                                 const double2* __restrict__ qm,
+                                                                 const double2* __restrict__ y,
+                                                                 double* part) {
+  __shared__ double red[LZ_WARPS * 4];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t e = (int64_t)blockIdx.x * LZ_BLOCK + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * LZ_BLOCK) {
+    const double2 yv = y[e];
+    cdot_acc<CPLX>(acc[0], acc[1], qj[e], yv);
+    if (qm) cdot_acc<CPLX>(acc[2], acc[3], qm[e], yv);
+  }
+  const double tot = block_multi_sum<4>(acc, red);
+  if (threadIdx.x < 4) part[(size_t)blockIdx.x * 4 + threadIdx.x] = tot;
+}
+
+// The three-term step and the dot products of one classical Gram-Schmidt
+// pass (see above).  part[l][blk][2] for l = 0..j; alpha[j] = Re <q_j|y>.
+// Every block sums the local partials in the same order.
+template <bool CPLX>
+__global__ void __launch_bounds__(LZ_BLOCK) lz_reorth_dots_kernel(
+    int64_t n, const double2* __restrict__ Q, int64_t ldq, int j,
+    const double* __restrict__ part_loc, int nblk_loc, double2* y, double* part, double* alpha) {
+  __shared__ double s_c[4];
+  __shared__ double red[LZ_WARPS * 2 * LZ_TILE];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < 4) {
+    double s = 0.0;
+    for (int b = lane; b < nblk_loc; b += 32) s += part_loc[(size_t)b * 4 + warp];
+    s = warp_sum(s);
+    if (lane == 0) s_c[warp] = s;
+  }
+  __syncthreads();
+  const double c0r = s_c[0], c0i = CPLX ? s_c[1] : 0.0, c1r = s_c[2], c1i = CPLX ? s_c[3] : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) alpha[j] = c0r;
+  const double2* qj = Q + (size_t)j * ldq;
+  const double2* qm = j > 0 ? Q + (size_t)(j - 1) * ldq : nullptr;
+  const int64_t e0 = (int64_t)blockIdx.x * LZ_BLOCK + threadIdx.x, es = (int64_t)gridDim.x * LZ_BLOCK;
+  for (int64_t e = e0; e < n; e += es) {
+    double2 yv = y[e];
+    caxpy_sub<CPLX>(yv, c0r, c0i, qj[e]);
+    if (qm) caxpy_sub<CPLX>(yv, c1r, c1i, qm[e]);
+    y[e] = yv;  // read back below by this same thread
+  }
+  constexpr int V = CPLX ? 2 * LZ_TILE : LZ_TILE;
+  for (int l0 = 0; l0 <= j; l0 += LZ_TILE) {
+    double acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.0;
+    const int nt = min(LZ_TILE, j + 1 - l0);
+    for (int64_t e = e0; e < n; e += es) {
+      const double2 yv = y[e];
+#pragma unroll
+      for (int l = 0; l < LZ_TILE; ++l) {
+        if (l < nt) {
+          const double2 q = Q[(size_t)(l0 + l) * ldq + e];
+          if constexpr (CPLX) cdot_acc<true>(acc[2 * l], acc[2 * l + 1], q, yv);
+          else cdot_acc<false>(acc[l], acc[l], q, yv);
+        }
+      }
+    }
+    const double tot = block_multi_sum<V>(acc, red);
+    if ((int)threadIdx.x < V) {
+      const int l = CPLX ? (int)threadIdx.x / 2 : (int)threadIdx.x;
+      const int c = CPLX ? (int)threadIdx.x % 2 : 0;
+      if (l < nt) {
+        part[((size_t)(l0 + l) * gridDim.x + blockIdx.x) * 2 + c] = tot;
+        if (!CPLX) part[((size_t)(l0 + l) * gridDim.x + blockIdx.x) * 2 + 1] = 0.0;
+      }
+    }
+    __syncthreads();  // red is reused by the next tile
+  }
+}
+
+// y -= sum_{l <= j} coef_l q_l; part[blk] = partial |y|^2
+template <bool CPLX>
+__global__ void __launch_bounds__(LZ_BLOCK) lz_update_norm_kernel(int64_t n,
+                                                                  const double2* __restrict__ Q,
+                                                                  int64_t ldq, int j,
+                                                                  const double* __restrict__ coef,
+                                                                  double2* y, double* part) {
+  __shared__ double red[LZ_WARPS];
+  double acc[1] = {0.0};
+  for (int64_t e = (int64_t)blockIdx.x * LZ_BLOCK + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * LZ_BLOCK) {
+    double2 yv = y[e];
+    for (int l = 0; l <= j; ++l)
+      caxpy_sub<CPLX>(yv, __ldg(coef + 2 * l), CPLX ? __ldg(coef + 2 * l + 1) : 0.0,
+                      Q[(size_t)l * ldq + e]);
+    y[e] = yv;
+    acc[0] = fma(yv.x, yv.x, acc[0]);
+    if constexpr (CPLX) acc[0] = fma(yv.y, yv.y, acc[0]);
+  }
+  const double tot = block_multi_sum<1>(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
 // out[2l + c] = sum over blocks of part[l][blk][c]: one warp per output, lanes
-// striding over the blocks, then a shuffle sum (fixed order).  alpha != NULL:
-// also alpha[j] = Re out[j] (the Lanczos diagonal).
-__global__ void dots_final_kernel(const double* part, int nblk, int j, double* out,
-                                  double* alpha) {
+// striding over the blocks, then a shuffle sum (fixed order).
+__global__ void dots_final_kernel(const double* part, int nblk, int j, double* out) {
   const int nl = j + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int o = warp; o < 2 * nl; o += nw) {
@@ -371,53 +509,8 @@ __global__ void dots_final_kernel(const double* part, int nblk, int j, double* o
     double acc = 0.0;
     for (int b = lane; b < nblk; b += 32) acc += part[((size_t)l * nblk + b) * 2 + c];
     acc = warp_sum(acc);
-    if (lane == 0) {
-      out[o] = acc;
-      if (alpha && o == 2 * j) alpha[j] = acc;
-    }
+    if (lane == 0) out[o] = acc;
   }
-}
-
-// y -= sum_l coef_l q_l  (complex coefficients)
-__global__ void gs_update_kernel(bool cplx, int64_t len, const double* __restrict__ Q, int64_t ldq,
-                                 int j, const double* __restrict__ coef, double* y) {
-  const int nl = j + 1;
-  if (cplx) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len / 2;
-         e += (int64_t)gridDim.x * blockDim.x) {
-      double yr = y[2 * e], yi = y[2 * e + 1];
-      for (int l = 0; l < nl; ++l) {
-        const double cr = coef[2 * l], ci = coef[2 * l + 1];
-        const double qr = Q[(size_t)l * ldq + 2 * e], qi = Q[(size_t)l * ldq + 2 * e + 1];
-        yr -= cr * qr - ci * qi;
-        yi -= cr * qi + ci * qr;
-      }
-      y[2 * e] = yr;
-      y[2 * e + 1] = yi;
-    }
-  } else {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
-         e += (int64_t)gridDim.x * blockDim.x) {
-      double yv = y[e];
-      for (int l = 0; l < nl; ++l) yv -= coef[2 * l] * Q[(size_t)l * ldq + e];
-      y[e] = yv;
-    }
-  }
-}
-
-__global__ void norm_partial_kernel(int64_t len, const double* __restrict__ y, double* part) {
-  __shared__ double sh[256];
-  double acc = 0.0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
-       e += (int64_t)gridDim.x * blockDim.x)
-    acc += y[e] * y[e];
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
 // beta_j = ||y|| from the norm partials (each block sums them in the same
@@ -759,26 +852,45 @@ cudaError_t launch_lanczos_start(bool cplx, int64_t n, unsigned long long seed, 
   return counted(cudaGetLastError());
 }
 
-cudaError_t launch_dots(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
-                        const double* y, double* part, int nblk, cudaStream_t st) {
-  dots_kernel<<<dim3(nblk, j + 1), 256, 0, st>>>(cplx, 2 * n, Q, ldq, y, part);
+cudaError_t launch_lz_local_dots(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
+                                const double* y, double* part_loc, int nblk, cudaStream_t st) {
+  const double2* q = reinterpret_cast<const double2*>(Q);
+  const double2* qj = q + (size_t)j * (ldq / 2);
+  const double2* qm = j > 0 ? q + (size_t)(j - 1) * (ldq / 2) : nullptr;
+  const double2* y2 = reinterpret_cast<const double2*>(y);
+  if (cplx) lz_local_dots_kernel<true><<<nblk, LZ_BLOCK, 0, st>>>(n, qj, qm, y2, part_loc);
+  else lz_local_dots_kernel<false><<<nblk, LZ_BLOCK, 0, st>>>(n, qj, qm, y2, part_loc);
   return counted(cudaGetLastError());
 }
 
-cudaError_t launch_dots_final(const double* part, int nblk, int j, double* out, double* alpha,
-                              cudaStream_t st) {
-  dots_final_kernel<<<1, 1024, 0, st>>>(part, nblk, j, out, alpha);
+cudaError_t launch_lz_reorth_dots(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
+                                  const double* part_loc, double* y, double* part, double* alpha,
+                                  int nblk, cudaStream_t st) {
+  const double2* q = reinterpret_cast<const double2*>(Q);
+  double2* y2 = reinterpret_cast<double2*>(y);
+  if (cplx)
+    lz_reorth_dots_kernel<true><<<nblk, LZ_BLOCK, 0, st>>>(n, q, ldq / 2, j, part_loc, nblk, y2,
+                                                            part, alpha);
+  else
+    lz_reorth_dots_kernel<false><<<nblk, LZ_BLOCK, 0, st>>>(n, q, ldq / 2, j, part_loc, nblk, y2,
+                                                             part, alpha);
   return counted(cudaGetLastError());
 }
 
-cudaError_t launch_gs_update(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
-                             const double* coef, double* y, cudaStream_t st) {
-  gs_update_kernel<<<blocks_for(n, 256), 256, 0, st>>>(cplx, 2 * n, Q, ldq, j, coef, y);
+cudaError_t launch_dots_final(const double* part, int nblk, int j, double* out, cudaStream_t st) {
+  dots_final_kernel<<<1, 1024, 0, st>>>(part, nblk, j, out);
   return counted(cudaGetLastError());
 }
 
-cudaError_t launch_norm2(int64_t n, const double* y, double* part, int nblk, cudaStream_t st) {
-  norm_partial_kernel<<<nblk, 256, 0, st>>>(2 * n, y, part);
+cudaError_t launch_lz_update_norm(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
+                                  const double* coef, double* y, double* part, int nblk,
+                                  cudaStream_t st) {
+  const double2* q = reinterpret_cast<const double2*>(Q);
+  double2* y2 = reinterpret_cast<double2*>(y);
+  if (cplx)
+    lz_update_norm_kernel<true><<<nblk, LZ_BLOCK, 0, st>>>(n, q, ldq / 2, j, coef, y2, part);
+  else
+    lz_update_norm_kernel<false><<<nblk, LZ_BLOCK, 0, st>>>(n, q, ldq / 2, j, coef, y2, part);
   return counted(cudaGetLastError());
 }
 

@@ -139,13 +139,15 @@ cudaError_t launch_minmax_final(const double* part_min, const double* part_max, 
 // with a zero pad column, or interleaved complex pairs)
 cudaError_t launch_lanczos_start(bool cplx, int64_t n, unsigned long long seed, double* q,
                                  cudaStream_t st);
-cudaError_t launch_dots(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
-                        const double* y, double* part, int nblk, cudaStream_t st);
-cudaError_t launch_dots_final(const double* part, int nblk, int j, double* out, double* alpha,
-                              cudaStream_t st);
-cudaError_t launch_gs_update(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
-                             const double* coef, double* y, cudaStream_t st);
-cudaError_t launch_norm2(int64_t n, const double* y, double* part, int nblk, cudaStream_t st);
+cudaError_t launch_lz_local_dots(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
+                                const double* y, double* part_loc, int nblk, cudaStream_t st);
+cudaError_t launch_lz_reorth_dots(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
+                                  const double* part_loc, double* y, double* part, double* alpha,
+                                  int nblk, cudaStream_t st);
+cudaError_t launch_dots_final(const double* part, int nblk, int j, double* out, cudaStream_t st);
+cudaError_t launch_lz_update_norm(bool cplx, int64_t n, const double* Q, int64_t ldq, int j,
+                                  const double* coef, double* y, double* part, int nblk,
+                                  cudaStream_t st);
 cudaError_t launch_lanczos_next(int64_t n, const double* y, const double* part, int nblk,
                                 double* beta, int j, double* qnext, cudaStream_t st);
 cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, int m,
