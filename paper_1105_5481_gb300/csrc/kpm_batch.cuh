@@ -24,6 +24,11 @@
 #include "kpm_rng.cuh"
 #include "kpm_step.cuh"
 
+// Minimum resident CTAs per SM requested from the register allocator.
+#ifndef KPM_BATCH_MIN_BLOCKS
+#define KPM_BATCH_MIN_BLOCKS 2
+#endif
+
 namespace kpm {
 
 namespace cg = cooperative_groups;
@@ -43,7 +48,7 @@ struct BatchTask {
 };
 
 template <class CH, class OP>
-__global__ void __launch_bounds__(256, 2) batch_kernel(BatchTask* tasks, int ntasks,
+__global__ void __launch_bounds__(256, KPM_BATCH_MIN_BLOCKS) batch_kernel(BatchTask* tasks, int ntasks,
                                                        int* queue) {
   using T = typename CH::T;
   cg::cluster_group cluster = cg::this_cluster();
@@ -52,6 +57,10 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(BatchTask* tasks, int nta
   const int t = threadIdx.x;
   extern __shared__ double smem[];
   __shared__ int s_task;
+  // The task's step arguments for even and odd steps (x and y swapped), kept
+  // in shared memory: read where used instead of held in registers across
+  // the step loop.
+  __shared__ StepArgs s_args[2];
   const OP op;
   for (;;) {
     if (rank == 0 && t == 0) s_task = atomicAdd(queue, 1);
@@ -63,14 +72,23 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(BatchTask* tasks, int nta
     cluster.sync();
     if (task >= ntasks) break;
     BatchTask& bt = tasks[task];
-    StepArgs a = bt.a;
-    const int Rp = a.Rp;
+    if (t < 2) {
+      StepArgs a = bt.a;
+      a.x = bt.v[t];
+      a.y = bt.v[t ^ 1];
+      a.w = a.y;
+      s_args[t] = a;
+    }
+    __syncthreads();
+    const int Rp = s_args[0].Rp;
     const int nsteps = bt.M / 2;
     // shared memory: CTA reduction scratch, then partials [2 parities][C][2 Rp] (rank 0)
     double* red = smem;
-    double* part = smem + step_smem_bytes(a.Gt, blockDim.x, CH::VEC) / sizeof(double);
+    double* part = smem + step_smem_bytes(s_args[0].Gt, blockDim.x, CH::VEC) / sizeof(double);
     double* part0 = cluster.map_shared_rank(part, 0);
+
     for (int step = bt.step_begin; step < bt.step_end; ++step) {
+      const StepArgs& a = s_args[step & 1];
       if (step == 0) {
         T* v0 = reinterpret_cast<T*>(bt.v[0]);
         const int64_t total = a.n * Rp;
@@ -79,13 +97,9 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(BatchTask* tasks, int nta
                                     (unsigned long long)bt.realisation, e);
         cluster.sync();
       }
-      a.x = bt.v[step & 1];
-      a.y = bt.v[(step + 1) & 1];
-      a.w = a.y;
       typename CH::Acc s;
       CH::acc_zero(s);
-      if (step == 0) step_rows<CH, MODE_FIRST, OP>(a, op, rank, C, 0, s);
-      else step_rows<CH, MODE_STEP, OP>(a, op, rank, C, 0, s);
+      step_rows<CH, MODE_DYN, OP>(a, op, rank, C, 0, s, step == 0);
       cta_reduce<CH>(a, s, 0, red, part0 + ((size_t)(step & 1) * C + rank) * 2 * Rp);
       cluster.sync();
       if (rank == 0) {
@@ -100,7 +114,7 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(BatchTask* tasks, int nta
     if (bt.step_end == nsteps && bt.step_begin < bt.step_end && rank == 0) {
       __syncthreads();  // rank 0's own sums writes above
       const int R = bt.R, M = bt.M;
-      const double inv_n = 1.0 / (double)a.n;
+      const double inv_n = 1.0 / (double)s_args[0].n;
       for (int e = t; e < R * nsteps; e += blockDim.x) {
         const int r = e / nsteps, step = e % nsteps;
         const double mu0 = bt.sums[r] * inv_n, mu1 = bt.sums[Rp + r] * inv_n;
@@ -120,25 +134,27 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(BatchTask* tasks, int nta
         bt.mu[m] = acc / (double)R;
       }
     }
-    cluster.sync();  // the instance is complete on every CTA of the cluster
+    cluster.sync();  // the instance is complete on every CTA of the cluster (and s_args free)
   }
 }
 
-inline size_t batch_smem_bytes(int Gt, int block, int vec, int C, int Rp) {
-  return step_smem_bytes(Gt, block, vec) + (size_t)2 * C * 2 * Rp * sizeof(double);
+// reduction scratch, then partials [2 parities][C][2 Rp]
+template <class CH, class OP>
+inline size_t batch_smem_bytes(int Gt, int block, int C, int Rp) {
+  return step_smem_bytes(Gt, block, CH::VEC) + (size_t)2 * C * 2 * Rp * sizeof(double);
 }
+
+template <class CH, class OP>
+struct BatchTag {};
 
 template <class CH, class OP>
 cudaError_t launch_batch_one(BatchTask* tasks, int ntasks, int* queue, int grid, int C, int Gt,
                              int Rp, cudaStream_t st) {
   const int block = 256;
-  const size_t smem = batch_smem_bytes(Gt, block, CH::VEC, C, Rp);
+  const size_t smem = batch_smem_bytes<CH, OP>(Gt, block, C, Rp);
   auto kern = batch_kernel<CH, OP>;
-  cudaError_t e = cudaSuccess;
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = allow_smem<BatchTag<CH, OP>>(kern, smem);
+  if (e != cudaSuccess) return e;
   if (C > 8) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
@@ -163,10 +179,12 @@ cudaError_t launch_batch_one(BatchTask* tasks, int ntasks, int* queue, int grid,
 template <class CH, class OP>
 int batch_max_clusters(int C, int Gt, int Rp) {
   const int block = 256;
-  const size_t smem = batch_smem_bytes(Gt, block, CH::VEC, C, Rp);
+  const size_t smem = batch_smem_bytes<CH, OP>(Gt, block, C, Rp);
   auto kern = batch_kernel<CH, OP>;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (allow_smem<BatchTag<CH, OP>>(kern, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   if (C > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(C);
@@ -180,6 +198,17 @@ int batch_max_clusters(int C, int Gt, int Rp) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
+  if (C == 1) {
+    // one-CTA clusters: the block occupancy (the cluster query reports one per SM)
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, block, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return n * sms;
+  }
   if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;

@@ -58,7 +58,9 @@ struct RunParams {
 
 // ----------------------------------------------------------------- kernel launchers
 // Step modes
-enum StepMode { MODE_FIRST = 0, MODE_STEP = 1, MODE_SPMV = 2 };
+// MODE_DYN (device code only): MODE_FIRST or MODE_STEP chosen by a uniform
+// runtime flag, so that a persistent kernel carries one copy of the traversal.
+enum StepMode { MODE_FIRST = 0, MODE_STEP = 1, MODE_SPMV = 2, MODE_DYN = 3 };
 
 struct StepArgs {
   // vectors: N x Rp (row-major, Rp contiguous), element T or complex<T>

@@ -24,6 +24,7 @@
 // reproducible for a given launch shape.
 #pragma once
 
+#include <atomic>
 #include <type_traits>
 
 #include "kpm_internal.h"
@@ -301,6 +302,7 @@ struct StencilOp {
   using T = typename CH::T;
   static constexpr bool CPLX = CH::CPLX;
   static constexpr bool kLines = DIMS >= 2;
+  static constexpr int kDims = DIMS;
   static constexpr int kMinBlocks = KPM_STEP_MIN_BLOCKS;
 
   // Neighbour offsets along d >= 1 depend only on the lattice line (y, z):
@@ -578,7 +580,7 @@ struct EllOp {
 // StepArgs).  Accumulates this thread's moment dots into s.
 template <class CH, int MODE, class OP>
 __device__ __forceinline__ void step_rows(const StepArgs& a, const OP& op, int cta, int ncta,
-                                          int ycol, typename CH::Acc& s) {
+                                          int ycol, typename CH::Acc& s, bool first = false) {
   using T = typename CH::T;
   constexpr int SC = CH::SC;
   const int Gt = a.Gt;
@@ -640,7 +642,7 @@ __device__ __forceinline__ void step_rows(const StepArgs& a, const OP& op, int c
           xp.ld_x(Xc + (size_t)jf0 * rowS2);
           const size_t base = (size_t)i * rowS2;
           CH acc;
-          if constexpr (MODE == MODE_STEP) {
+          if (MODE == MODE_STEP || (MODE == MODE_DYN && !first)) {
             CH wv;
             wv.ld_cs(Wc + base);
             acc.set_neg(wv);
@@ -648,7 +650,7 @@ __device__ __forceinline__ void step_rows(const StepArgs& a, const OP& op, int c
             acc.zero();
           }
           op.apply_line_win(a, i, cx, lctx, Xc, x0, xm, xp, acc, hu_r, hu_i, du);
-          if constexpr (MODE == MODE_FIRST) acc.half();
+          if (MODE == MODE_FIRST || (MODE == MODE_DYN && first)) acc.half();
           acc.st(Yc + base);
           if constexpr (MODE != MODE_SPMV) CH::acc_add(s, x0, acc);
         }
@@ -678,7 +680,7 @@ __device__ __forceinline__ void step_rows(const StepArgs& a, const OP& op, int c
       const size_t base = (size_t)i * rowS;
       CH xi, acc;
       xi.ld_x(Xc + base);
-      if constexpr (MODE == MODE_STEP) {
+      if (MODE == MODE_STEP || (MODE == MODE_DYN && !first)) {
         CH wv;
         wv.ld_cs(Wc + base);
         acc.set_neg(wv);
@@ -691,7 +693,7 @@ __device__ __forceinline__ void step_rows(const StepArgs& a, const OP& op, int c
       } else {
         op.apply(a, i, Xc, xi, acc, hu_r, hu_i, du);
       }
-      if constexpr (MODE == MODE_FIRST) acc.half();
+      if (MODE == MODE_FIRST || (MODE == MODE_DYN && first)) acc.half();
       acc.st(Yc + base);
       if constexpr (MODE != MODE_SPMV) CH::acc_add(s, xi, acc);
     }
@@ -758,6 +760,23 @@ __global__ void __launch_bounds__(256, OP::kMinBlocks) cheb_step_kernel(const St
 __host__ __device__ inline size_t step_smem_bytes(int Gt, int block, int vec) {
   const int nq = Gt < 32 ? block / 32 : block / Gt;
   return (size_t)nq * Gt * 2 * vec * sizeof(double);
+}
+
+// Raises a kernel's dynamic shared-memory limit above the default 48 KB, once
+// per kernel (Tag: the kernel's own template instance) and device (ordinals
+// below 64), so that no attribute is set while a stream is being captured.
+template <class Tag, class K>
+cudaError_t allow_smem(K kern, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
 }
 
 template <class CH, int MODE, class OP>
