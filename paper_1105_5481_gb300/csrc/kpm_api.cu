@@ -784,6 +784,7 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
       a.y = w.v[1];
       a.w = nullptr;
       a.partial = w.ring;
+      a.reverse = 1;  // step n sweeps backwards for even n (see StepArgs)
       e = launch_step(h->stencil, fp32, h->cplx, MODE_FIRST, a, cfg, h->cap_stream);
     }
     if (e == cudaSuccess && steps == 1)
@@ -793,6 +794,7 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
       a.y = w.v[(n + 1) & 1];
       a.w = w.v[(n + 1) & 1];
       a.partial = w.ring + (size_t)(n % RING) * grid * 2 * Rp;
+      a.reverse = (n & 1) ^ 1;
       e = launch_step(h->stencil, fp32, h->cplx, MODE_STEP, a, cfg, h->cap_stream);
       if (e != cudaSuccess) break;
       if ((n + 1) % RING == 0)

@@ -94,6 +94,12 @@ struct StepArgs {
   int line_L1;            // L[1] (3D: line -> y = line % L1, z = line / L1)
   int64_t passes;         // total passes
   int chunk;              // passes per chunk
+  // 1: the chunks are taken from the last one down.  Consecutive steps of a
+  // single solve alternate, so that a step starts on the rows the previous
+  // step touched last, which are still in L2 (both vector blocks of a step
+  // are re-read by the next one).  The batched kernel keeps one direction:
+  // there a CTA's own rows of the previous step are still in its L1.
+  int reverse;
 };
 
 struct LaunchCfg {

@@ -578,7 +578,8 @@ struct EllOp {
 // Rows of one step handled by CTA `cta` of `ncta` CTAs working on the same
 // vectors: chunks of a.chunk passes taken in a stride-ncta loop (see
 // StepArgs).  Accumulates this thread's moment dots into s.
-template <class CH, int MODE, class OP>
+// SWEEP = false: always the forward chunk order (a.reverse ignored).
+template <class CH, int MODE, class OP, bool SWEEP = true>
 __device__ __forceinline__ void step_rows(const StepArgs& a, const OP& op, int cta, int ncta,
                                           int ycol, typename CH::Acc& s, bool first = false) {
   using T = typename CH::T;
@@ -598,7 +599,8 @@ __device__ __forceinline__ void step_rows(const StepArgs& a, const OP& op, int c
   const int Lx = a.line_len;
   const int u = a.chunk;
   const int64_t nchunks = (a.passes + u - 1) / u;
-  for (int64_t ch = cta; ch < nchunks; ch += ncta) {
+  for (int64_t kc = cta; kc < nchunks; kc += ncta) {
+    const int64_t ch = (SWEEP && a.reverse) ? nchunks - 1 - kc : kc;
     const int64_t p_beg = ch * (int64_t)u;
     const int np = (int)min((int64_t)u, a.passes - p_beg);
     // line traversal: x and the line context advance incrementally
