@@ -54,10 +54,11 @@ BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_batch_f32.cu"]
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture,
 # keyed by workload (and launch configuration), with the hash of the kernel sources
-# it was taken on (profiles/cheb_step_fp32_cubic_spin_L64.md,
+# it was taken on (profiles/cheb_step_fp32_cubic_spin_L64.md: steady state of
+# consecutive steps, caches not flushed between launches;
 # profiles/batch_kernel_fp32_batch_2d_256.md); reported only while the hash matches.
-MEASURED_TRAFFIC = {"cubic_spin_L64": (381.42e6, "step", "10b8caaedfe48719"),
-                    "batch_2d_256/C4/chunk2/clusters74": (77.55e9, "batch", "1c43c20496f7dd17")}
+MEASURED_TRAFFIC = {"cubic_spin_L64": (348.01e6, "step", "c75d80f4fc842f11"),
+                    "batch_2d_256/C4/chunk2/clusters74": (67.49e9, "batch", "a342f2d934eec022")}
 
 
 def step_source_hash(kind="step"):
@@ -201,7 +202,7 @@ def csr_handle(K, w):
     return K.kpm_create_csr(rp.size - 1, rp, col, val, complex_=True)
 
 
-def profile_run(prec, workload):
+def profile_run(prec, workload, batch_chunk=2):
     """Two solves of the workload with Gershgorin bounds (no Lanczos products, so
     the only fused-step launches are those of the two solves)."""
     import torch
@@ -217,7 +218,7 @@ def profile_run(prec, workload):
         ab = [K.kpm_bounds(h, 0, WORKLOAD["pad_eps"])[2:] for h in hs]
         with K.kpm_batch_create(hs, [x["M"] for x in insts], 16, [p[0] for p in ab],
                                 [p[1] for p in ab], [x["seed"] for x in insts], prec) as bt:
-            K.kpm_batch_set_config(bt, 4, 2, 100)
+            K.kpm_batch_set_config(bt, 4, batch_chunk, 100)
             for _ in range(2):
                 mu = K.kpm_batch_run(bt)
         print(json.dumps({"profile": prec, "workload": workload, "mu0": float(mu[0])}))
@@ -481,6 +482,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-chunk", type=int, default=2,
+                    help="--profile with the batch workload: passes per chunk (clusters of 4)")
     ap.add_argument("--workload", default="cubic_spin_L64",
                     choices=["cubic_spin_L64", "csr_spin_dilute_L160", "batch_2d_256",
                              "serve_poisson"],
@@ -493,7 +496,7 @@ def main():
     if args.impl == "reference":
         return reference_arm(args)
     if args.profile:
-        return profile_run(args.profile, args.workload)
+        return profile_run(args.profile, args.workload, args.batch_chunk)
     if args.workload == "csr_spin_dilute_L160":
         return csr_leg(args)
     if args.workload == "batch_2d_256":

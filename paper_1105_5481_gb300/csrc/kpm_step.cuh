@@ -153,6 +153,15 @@ __device__ __forceinline__ void pair_add2(float2& s1, float2& c1, float2 s2, flo
   s1 = t;
 }
 
+// scalar form of pair_add2: (s1, c1) += (s2, c2), s - c being the value
+__device__ __forceinline__ void pair_add(float& s1, float& c1, float s2, float c2) {
+  const float t = __fadd_rn(s1, s2);
+  const float bb = __fsub_rn(t, s1);
+  const float err = __fadd_rn(__fsub_rn(s1, __fsub_rn(t, bb)), __fsub_rn(s2, bb));
+  c1 = __fsub_rn(__fadd_rn(c1, c2), err);
+  s1 = t;
+}
+
 __device__ __forceinline__ float2 shfl2(float2 v, int off) {
   return make_float2(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off));
 }
@@ -304,6 +313,7 @@ struct StencilOp {
   static constexpr bool kLines = DIMS >= 2;
   static constexpr int kDims = DIMS;
   static constexpr int kMinBlocks = KPM_STEP_MIN_BLOCKS;
+  static constexpr bool kPairReduce = true;
 
   // Neighbour offsets along d >= 1 depend only on the lattice line (y, z):
   // computed once per chunk of passes.
@@ -472,6 +482,7 @@ struct CsrOp {
   static constexpr bool CPLX = CH::CPLX;
   static constexpr bool kLines = false;
   static constexpr int kMinBlocks = KPM_SPARSE_MIN_BLOCKS;
+  static constexpr bool kPairReduce = false;
   struct LineCtx {};
   __device__ __forceinline__ void hop(const T* V, int64_t k, T& hr, T& hi) const {
     if constexpr (CPLX) {
@@ -526,6 +537,7 @@ struct EllOp {
   static constexpr bool CPLX = CH::CPLX;
   static constexpr bool kLines = false;
   static constexpr int kMinBlocks = KPM_SPARSE_MIN_BLOCKS;
+  static constexpr bool kPairReduce = false;
   struct LineCtx {};
   __device__ __forceinline__ void apply(const StepArgs& a, int64_t i, const T* __restrict__ Xc,
                                         const CH& xi, CH& acc, T, T, T du) const {
@@ -704,11 +716,16 @@ __device__ __forceinline__ void step_rows(const StepArgs& a, const OP& op, int c
 
 // CTA-wide sum of the threads' moment dots: lanes sharing a column are
 // combined with warp shuffles in the chunk's own precision (compensated FP32
-// pairs on the FP32 path), then converted to FP64 and summed over the warps in
-// shared memory `red` in warp order.
+// pairs on the FP32 path), then summed over the warps in shared memory `red`
+// in warp order (FP64 path: in FP64; FP32 path: still in compensated pairs,
+// and only the 2 Rp column totals are converted to FP64, because GB300's FP64
+// pipe, at 1/64 of the FP32 rate, made per-thread conversions a visible tail
+// of every step).
+// PAIRS = false keeps the FP64 cross-warp stage on the FP32 path (the sparse
+// operators, whose 80-register budget fares better with it).
 // Writes dst[which * Rp + ycol * Rt + col] for which in {A, B} and the Rt
 // columns of this column slice.  All threads of the CTA must call it.
-template <class CH>
+template <class CH, bool PAIRS = true>
 __device__ __forceinline__ void cta_reduce(const StepArgs& a, typename CH::Acc s, int ycol,
                                            double* red, double* dst) {
   constexpr int VEC = CH::VEC;
@@ -716,34 +733,74 @@ __device__ __forceinline__ void cta_reduce(const StepArgs& a, typename CH::Acc s
   const int t = threadIdx.x;
   const int cl = t % Gt, q = t / Gt, spi = blockDim.x / Gt;
   if (Gt < 32) CH::warp_reduce(s, Gt);
-  double dA[VEC], dB[VEC];
-  CH::acc_out(s, dA, dB);
-  const int lane = t & 31, warp = t >> 5;
-  bool rep;
-  int qrep, nq;
-  if (Gt < 32) {
-    rep = lane < Gt;
-    qrep = warp;
-    nq = blockDim.x >> 5;
-  } else {
-    rep = true;
-    qrep = q;
-    nq = spi;
-  }
-  if (rep) {
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-      red[((qrep * Gt + cl) * 2 + 0) * VEC + k] = dA[k];
-      red[((qrep * Gt + cl) * 2 + 1) * VEC + k] = dB[k];
+  if constexpr (PAIRS && sizeof(typename CH::T) == 4) {
+    const int lane = t & 31, warp = t >> 5;
+    bool rep;
+    int qrep, nq;
+    if (Gt < 32) {
+      rep = lane < Gt;
+      qrep = warp;
+      nq = blockDim.x >> 5;
+    } else {
+      rep = true;
+      qrep = q;
+      nq = spi;
     }
-  }
-  __syncthreads();
-  const int Rp = a.Rp, Rt = Gt * VEC;
-  for (int o = t; o < 2 * Rt; o += blockDim.x) {
-    const int which = o / Rt, col = o % Rt, cc = col / VEC, k = col % VEC;
-    double sum = 0.0;
-    for (int qq = 0; qq < nq; ++qq) sum += red[((qq * Gt + cc) * 2 + which) * VEC + k];
-    dst[which * Rp + ycol * Rt + col] = sum;
+    const int Rp = a.Rp, Rt = Gt * VEC;
+    // per (qrep, cl): for each float2 j of the chunk, the pairs (a, ca, b, cb)
+    float2* r2 = reinterpret_cast<float2*>(red);
+    if (rep) {
+      float2* o = r2 + (size_t)(qrep * Gt + cl) * 2 * VEC;
+#pragma unroll
+      for (int j = 0; j < VEC / 2; ++j) {
+        o[4 * j + 0] = s.a[j];
+        o[4 * j + 1] = s.ca[j];
+        o[4 * j + 2] = s.b[j];
+        o[4 * j + 3] = s.cb[j];
+      }
+    }
+    __syncthreads();
+    const float* rf = reinterpret_cast<const float*>(red);
+    for (int o = t; o < 2 * Rt; o += blockDim.x) {
+      const int which = o / Rt, col = o % Rt, cc = col / VEC, k = col % VEC;
+      const int j = k / 2, h = k % 2;
+      float sum = 0.0f, comp = 0.0f;
+      for (int qq = 0; qq < nq; ++qq) {
+        const float* e = rf + ((size_t)(qq * Gt + cc) * 2 * VEC + 4 * j + 2 * which) * 2;
+        pair_add(sum, comp, e[h], e[2 + h]);
+      }
+      dst[which * Rp + ycol * Rt + col] = (double)sum - (double)comp;
+    }
+  } else {
+    double dA[VEC], dB[VEC];
+    CH::acc_out(s, dA, dB);
+    const int lane = t & 31, warp = t >> 5;
+    bool rep;
+    int qrep, nq;
+    if (Gt < 32) {
+      rep = lane < Gt;
+      qrep = warp;
+      nq = blockDim.x >> 5;
+    } else {
+      rep = true;
+      qrep = q;
+      nq = spi;
+    }
+    if (rep) {
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) {
+        red[((qrep * Gt + cl) * 2 + 0) * VEC + k] = dA[k];
+        red[((qrep * Gt + cl) * 2 + 1) * VEC + k] = dB[k];
+      }
+    }
+    __syncthreads();
+    const int Rp = a.Rp, Rt = Gt * VEC;
+    for (int o = t; o < 2 * Rt; o += blockDim.x) {
+      const int which = o / Rt, col = o % Rt, cc = col / VEC, k = col % VEC;
+      double sum = 0.0;
+      for (int qq = 0; qq < nq; ++qq) sum += red[((qq * Gt + cc) * 2 + which) * VEC + k];
+      dst[which * Rp + ycol * Rt + col] = sum;
+    }
   }
 }
 
@@ -755,7 +812,8 @@ __global__ void __launch_bounds__(256, OP::kMinBlocks) cheb_step_kernel(const St
   step_rows<CH, MODE, OP>(a, op, blockIdx.x, gridDim.x, blockIdx.y, s);
   if constexpr (MODE != MODE_SPMV) {
     extern __shared__ double red[];
-    cta_reduce<CH>(a, s, blockIdx.y, red, a.partial + (size_t)blockIdx.x * 2 * a.Rp);
+    cta_reduce<CH, OP::kPairReduce>(a, s, blockIdx.y, red,
+                                    a.partial + (size_t)blockIdx.x * 2 * a.Rp);
   }
 }
 
