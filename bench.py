@@ -57,8 +57,9 @@ BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
 # it was taken on (profiles/cheb_step_fp32_cubic_spin_L64.md: steady state of
 # consecutive steps, caches not flushed between launches;
 # profiles/batch_kernel_fp32_batch_2d_256.md); reported only while the hash matches.
-MEASURED_TRAFFIC = {"cubic_spin_L64": (348.01e6, "step", "c75d80f4fc842f11"),
-                    "batch_2d_256/C4/chunk2/clusters74": (67.49e9, "batch", "a342f2d934eec022")}
+MEASURED_TRAFFIC = {"cubic_spin_L64": (347.54e6, "step", "c75d80f4fc842f11"),
+                    "batch_2d_256/C4/chunk2/clusters74": (67.49e9, "batch", "a342f2d934eec022"),
+                    "batch_2d_256/C4/chunk4/clusters74": (67.49e9, "batch", "a342f2d934eec022")}
 
 
 def step_source_hash(kind="step"):
