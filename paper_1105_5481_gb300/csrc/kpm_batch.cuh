@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256, KPM_BATCH_MIN_BLOCKS) batch_kernel(BatchT
       }
       typename CH::Acc s;
       CH::acc_zero(s);
-      step_rows<CH, MODE_DYN, OP, false>(a, op, rank, C, 0, s, step == 0);
+      step_rows<CH, MODE_DYN, OP, false, true>(a, op, rank, C, 0, s, step == 0);
       cta_reduce<CH>(a, s, 0, red, part0 + ((size_t)(step & 1) * C + rank) * 2 * Rp);
       cluster.sync();
       if (rank == 0) {
