@@ -54,12 +54,13 @@ BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_batch_f32.cu"]
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture,
 # keyed by workload (and launch configuration), with the hash of the kernel sources
-# it was taken on (profiles/cheb_step_fp32_cubic_spin_L64.md: steady state of
-# consecutive steps, caches not flushed between launches;
-# profiles/batch_kernel_fp32_batch_2d_256.md); reported only while the hash matches.
-MEASURED_TRAFFIC = {"cubic_spin_L64": (347.54e6, "step", "c75d80f4fc842f11"),
-                    "batch_2d_256/C4/chunk2/clusters74": (67.49e9, "batch", "a342f2d934eec022"),
-                    "batch_2d_256/C4/chunk4/clusters74": (67.49e9, "batch", "a342f2d934eec022")}
+# it was taken on (profiles/cheb_step_fp32_cubic_spin_L64.md and
+# profiles/cheb_step_fp32_csr_spin_dilute_L160.md: steady state of consecutive steps,
+# caches not flushed between launches; profiles/batch_kernel_fp32_batch_2d_256.md);
+# reported only while the hash matches.
+MEASURED_TRAFFIC = {"cubic_spin_L64": (347.56e6, "step", "fa838511f86e9da1"),
+                    "csr_spin_dilute_L160": (3445.37e6, "step", "fa838511f86e9da1"),
+                    "batch_2d_256/C4/chunk4/clusters74": (70.08e9, "batch", "24af8e5bedbe296f")}
 
 
 def step_source_hash(kind="step"):
@@ -290,7 +291,7 @@ def csr_leg(args):
                    "bounds": {"emin": emin, "emax": emax, "a": a, "b": b},
                    "l2": "inputs larger than L2"},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "traffic": None, "bytes_per_launch": bytes_step,
+                     "traffic": measured_traffic("csr_spin_dilute_L160"), "bytes_per_launch": bytes_step,
                      "launch_ms": chain_ms / nsteps, "peak_kind": peak_kind},
         "gpu_launches": K.kpm_kernel_launches() - l0, "clocks": clk.summary()}))
     h.close()
