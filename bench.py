@@ -63,6 +63,12 @@ MEASURED_TRAFFIC = {"cubic_spin_L64": (347.56e6, "step", "fa838511f86e9da1"),
                     "batch_2d_256/C4/chunk4/clusters74": (70.08e9, "batch", "24af8e5bedbe296f")}
 
 
+def per_matvec(value):
+    """The same throughput counted per matrix-vector product (two moments per
+    product in the doubling form): nnz*R*(M/2)/t."""
+    return {"value": value / 2, "unit": "nnz*R*matvecs/s"}
+
+
 def step_source_hash(kind="step"):
     import hashlib
 
@@ -166,33 +172,69 @@ def oracle_sample(hop, L, R_s, M_s, seed):
     return H.nnz * R_s * M_s / dt, dt, H.nnz
 
 
+def oracle_c_sample(hop, L, seed):
+    """The oracle's doubling form restated in C (OpenMP over rows), on bounded samples
+    of the same workload: all host threads with R=64, M=64, and one thread with R=8,
+    M=32.  Returns (all-thread value, threads, one-thread value, seconds)."""
+    import oracle as O
+    from oracle import kpm_cpu as OC
+    from paper_1105_5481_gb300 import inputs as I
+
+    H = O.lattice_hamiltonian(L, hop=hop)
+    a, b = O.rescale(*O.gershgorin(H), 0.01)
+    nthreads = OC.max_threads()
+    v0 = I.phase_block(seed, H.n, 64)
+    OC.moments_doubling(H, a, b, v0[:, :8], 4, threads=nthreads)  # warm-up
+    t0 = time.perf_counter()
+    OC.moments_doubling(H, a, b, v0, 64, threads=nthreads)
+    dt_all = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    OC.moments_doubling(H, a, b, v0[:, :8], 32, threads=1)
+    dt_one = time.perf_counter() - t0
+    return (H.nnz * 64 * 64 / dt_all, nthreads, H.nnz * 8 * 32 / dt_one, dt_all + dt_one)
+
+
 def reference_arm(args):
-    """The oracle on the host cores, on bounded samples of the same workload."""
+    """The oracle on the machine's host cores (its C restatement, OpenMP over all host
+    threads), each step a bounded sample of the same workload: all 64 vectors,
+    M=16 moments of the doubling form, plus the DOS on 64 nodes."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    import oracle as O
+    from oracle import kpm_cpu as OC
     from paper_1105_5481_gb300 import inputs as I
 
     w = I.workload("cubic_spin_L64")
-    R_s, M_s = 4, 16
+    R_s, M_s = 64, 16
+    H = O.lattice_hamiltonian(w["L"], hop=w["hop"])
+    a, b = O.rescale(*O.gershgorin(H), 0.01)
+    v0 = I.phase_block(WORKLOAD["seed"], H.n, R_s)
+    nthreads = OC.max_threads()
+
+    def sample():
+        t0 = time.perf_counter()
+        mu, _ = OC.moments_doubling(H, a, b, v0, M_s, threads=nthreads)
+        O.dos(mu, a, b, 64)
+        return time.perf_counter() - t0
+
     for _ in range(args.warmup):
-        oracle_sample(w["hop"], w["L"], R_s, M_s, WORKLOAD["seed"])
-    vals, times = [], []
-    for _ in range(args.steps):
-        v, dt, nnz = oracle_sample(w["hop"], w["L"], R_s, M_s, WORKLOAD["seed"])
-        vals.append(v)
-        times.append(dt)
-    value = float(np.median(vals))
-    sample = (f"3D L=64 spin lattice (N=262144, nnz={nnz}), {R_s} of the 64 random-phase vectors, "
-              f"M={M_s} moments (doubling form) + DOS on 64 nodes, per step")
+        sample()
+    times = [sample() for _ in range(args.steps)]
+    dt = float(np.median(times))
+    value = H.nnz * R_s * M_s / dt
+    desc = (f"3D L=64 spin lattice (N=262144, nnz={H.nnz}), all {R_s} random-phase vectors, "
+            f"M={M_s} moments (the oracle's doubling form in C, FP64, OpenMP on {nthreads} host "
+            f"threads) + DOS on 64 nodes, per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.median(times)),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD["name"], "lattice": "3D cubic L=64 periodic, spin hoppings",
                    "R": 64, "M": 1024, "sample": "bounded oracle sample"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads,
+                         "kind": "oracle (C, OpenMP)", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -241,6 +283,66 @@ def profile_run(prec, workload, batch_chunk=2):
     return 0
 
 
+def square_leg(args):
+    """The small FP64 configuration (2D L=32, R=8, M=256, Jackson DOS on 1024 nodes):
+    latency-bound, reported as microseconds per solve with its L2-resident rate."""
+    import torch
+
+    from paper_1105_5481_gb300 import build as B
+    from paper_1105_5481_gb300 import inputs as I
+    from paper_1105_5481_gb300 import kpm as K
+
+    B.build()
+    w = I.workload("square_L32_fp64")
+    N, R, M, Kn = int(np.prod(w["L"])), w["R"], w["M"], w["K"]
+    h = K.kpm_create_stencil(2, w["L"], onsite=w["onsite"])
+    nnz = K.kpm_info(h)["nnz"]
+    emin, emax, a, b = K.kpm_bounds(h, WORKLOAD["lanczos_steps"], WORKLOAD["pad_eps"], seed=6)
+    stream = torch.cuda.Stream()
+    mu_d = torch.empty(M, dtype=torch.float64, device="cuda")
+    E_d = torch.empty(Kn, dtype=torch.float64, device="cuda")
+    rho_d = torch.empty(Kn, dtype=torch.float64, device="cuda")
+    warm = max(args.warmup, 3)
+    for i in range(warm):
+        K.kpm_moments(h, M, R, a, b, seed=10 + i, precision="fp64", out=mu_d, stream=stream)
+    stream.synchronize()
+    steps = max(args.steps, 1) * 20  # 20 solves per step: one solve is well under a millisecond
+    l0 = K.kpm_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record(stream)
+        for i in range(steps):
+            K.kpm_moments(h, M, R, a, b, seed=100 + i, precision="fp64", out=mu_d, stream=stream)
+            K.kpm_dos(mu_d, a, b, Kn, "jackson", E=E_d, rho=rho_d, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    chain_ms, nsteps = K.kpm_step_timing(h)
+    bytes_step = 3 * N * R * 8 + N * 8  # vectors + on-site energies (uniform hopping)
+    hbm, peak_kind = peaks()
+    rate = bytes_step / (chain_ms / nsteps / 1e3) / 1e9
+    value = nnz * R * M / (ms / 1e3)
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "per_matvec": per_matvec(value),
+        "steps": steps, "warmup": warm, "ms_per_step": ms, "us_per_solve": ms * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "square_L32_fp64",
+                   "lattice": "2D square L=32 periodic, t=1, on-site U[-0.5,0.5]",
+                   "N": N, "nnz": nnz, "R": R, "M": M, "K": Kn, "step": "one solve + Jackson DOS",
+                   "bounds": {"emin": emin, "emax": emax, "a": a, "b": b},
+                   "l2": "working set (vectors 128 KB) L1/L2-resident"},
+        "roofline": {"bound": "latency", "achieved": rate, "peak": hbm, "unit": "GB/s",
+                     "frac": rate / hbm, "traffic": None, "bytes_per_launch": bytes_step,
+                     "launch_ms": chain_ms / nsteps, "peak_kind": peak_kind,
+                     "note": "127 dependent steps on 128 KB of vectors: each step is one "
+                             "launch's latency; achieved = the L2-resident rate"},
+        "gpu_launches": K.kpm_kernel_launches() - l0, "clocks": clk.summary()}))
+    h.close()
+    return 0
+
+
 def csr_leg(args):
     """The large diluted CSR lattice: one solve per step (a JSON line of its own)."""
     import torch
@@ -282,6 +384,7 @@ def csr_leg(args):
     ach = bytes_step / (chain_ms / nsteps / 1e3) / 1e9
     print(json.dumps({
         "metric": METRIC, "value": nnz * R * M / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "per_matvec": per_matvec(nnz * R * M / (ms / 1e3)),
         "steps": steps, "warmup": min(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 vectors, f64 moments",
         "data": "synthetic",
@@ -373,6 +476,7 @@ def batch_leg(args):
                              "set of the active instances is L2-resident, so frac can exceed 1"},
         "per_instance_calls": {"ms": ms_single, "speedup_of_batch": ms_single / ms},
         "solves_per_s": 256 / (ms / 1e3),
+        "per_matvec": per_matvec(units / (ms / 1e3)),
         "gpu_launches": launches, "clocks": clk.summary()}))
     bt.close()
     for h in hs:
@@ -465,7 +569,8 @@ def serve_leg(args, count=48, rate_hz=40.0, K_nodes=1024):
                              "(>= 8 MB per product) as full-GPU steps on 4 streams",
                    "bounds": "Gershgorin per request, pad 0.01"},
         "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"], "mean": st["mean_s"], "max": st["max_s"]},
-        "throughput": {"solves_per_s": st["completed"] / wall, "nnz_R_moments_per_s": units / wall},
+        "throughput": {"solves_per_s": st["completed"] / wall, "nnz_R_moments_per_s": units / wall,
+                       "nnz_R_matvecs_per_s": units / wall / 2},
         "server": {k: st[k] for k in ("completed", "failed", "ticks", "peak_resident", "peak_bytes")},
         "per_request_fp64": {"solves_per_s": count / wall64, "p50_s": float(np.percentile(lat64, 50)),
                              "p99_s": float(np.percentile(lat64, 99)), "wall_s": wall64},
@@ -488,7 +593,7 @@ def main():
                     help="--profile with the batch workload: passes per chunk (clusters of 4)")
     ap.add_argument("--workload", default="cubic_spin_L64",
                     choices=["cubic_spin_L64", "csr_spin_dilute_L160", "batch_2d_256",
-                             "serve_poisson"],
+                             "serve_poisson", "square_L32_fp64"],
                     help="cubic_spin_L64 (default, the headline) or the large diluted CSR "
                          "lattice (L=160, N=4.1M, R=32, M=4096, FP32 vectors)")
     ap.add_argument("--profile", default=None, choices=["fp32", "fp64"],
@@ -499,6 +604,8 @@ def main():
         return reference_arm(args)
     if args.profile:
         return profile_run(args.profile, args.workload, args.batch_chunk)
+    if args.workload == "square_L32_fp64":
+        return square_leg(args)
     if args.workload == "csr_spin_dilute_L160":
         return csr_leg(args)
     if args.workload == "batch_2d_256":
@@ -619,12 +726,18 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
-    cpu = None
+    cpu = cpu_c = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, _ = oracle_sample(w["hop"], L, 8, 32, WORKLOAD["seed"])
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"FP64 NumPy oracle, same lattice, 8 of the 64 vectors, M=32 moments "
                          f"+ DOS ({dt:.1f} s)"}
+        v_all, nthr, v_one, dtc = oracle_c_sample(w["hop"], L, WORKLOAD["seed"])
+        cpu_c = {"value": v_all, "unit": UNIT, "cores": nthr, "kind": "oracle (C, OpenMP)",
+                 "sample": f"the oracle's doubling form in C, FP64 CSR, same lattice: all "
+                           f"{nthr} host threads with R=64, M=64; one thread with R=8, M=32 "
+                           f"({dtc:.1f} s)",
+                 "one_core": {"value": v_one, "cores": 1}}
 
     if rank == 0:
         line = {
@@ -645,7 +758,9 @@ def main():
                          "kernel": "cheb_step_kernel<float, complex, STEP, StencilOp<3,hop>>",
                          "bytes_per_launch": bytes32, "launch_ms": step_ms32,
                          "peak_kind": f"{peak_kind} (copy bandwidth)"},
+            "per_matvec": per_matvec(value),
             "fp64_path": {"value": world * units / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                          "per_matvec": per_matvec(world * units / (ms64 / 1e3)),
                           "steps": args.fp64_steps, "dtype": "f64",
                           "roofline": {"bound": "alu", "achieved": ach64_tf, "peak": FP64_PEAK_TFLOPS,
                                        "unit": "TFLOP/s", "frac": ach64_tf / FP64_PEAK_TFLOPS,
@@ -653,6 +768,7 @@ def main():
                                        "launch_ms": step_ms64},
                           "clocks": clk64, "gpu_launches": launches64},
             "cpu_baseline": cpu,
+            "cpu_baseline_c": cpu_c,
             "e2e": {"value": world * units / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(hop.nbytes),
                     "d2h_bytes_per_step": int(8 * (M + 2 * Kn)),

@@ -1,0 +1,19 @@
+"""bench.py --impl reference: the oracle (its C/OpenMP restatement) on the host
+cores prints one JSON line in the benchmark's contract."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                         timeout=600, cwd=ROOT, check=True).stdout.strip().splitlines()[-1]
+    d = json.loads(out)
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["metric"] == "Chebyshev nnz*R*moments/s" and d["config"]["workload"] == "cubic_spin_L64"
