@@ -67,7 +67,7 @@ typedef enum {
                                  FP32 partial sums; bounds and DOS in FP64 */
 } kpm_precision;
 
-typedef enum { KPM_KERNEL_JACKSON = 0, KPM_KERNEL_NONE = 1 } kpm_kernel;
+typedef enum { KPM_KERNEL_JACKSON = 0, KPM_KERNEL_NONE = 1, KPM_KERNEL_LORENTZ = 2 } kpm_kernel;
 
 /*
  * Lattice stencil description (matrix-free Hamiltonian; the paper's
@@ -165,6 +165,40 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
  * device.  1 <= M <= 1<<20, 1 <= K <= 1<<20. */
 kpm_status kpm_dos(const double* mu, int M, double a, double b, int K, int kernel,
                    double* E, double* rho, void* stream);
+
+/* kpm_dos with any damping kernel, including the Lorentz kernel
+ *   g_n = sinh(lambda (1 - n/M)) / sinh(lambda),  lambda > 0
+ * of the KPM review the paper cites (Eq. 74 there; the paper itself names only
+ * the Jackson kernel, Sec. I).  lambda is read only for KPM_KERNEL_LORENTZ.
+ * Arguments, ranges and errors as kpm_dos. */
+kpm_status kpm_dos_kernel(const double* mu, int M, double a, double b, int K, int kernel,
+                          double lambda, double* E, double* rho, void* stream);
+
+/* Stochastic error bars (the paper's estimator Eq. (munr) averages over
+ * independent random vectors, Sec. II-A-3; this reports their spread).  From
+ * the per-vector moments pv[r*M + n] of nvec independent vectors (the
+ * mu_per_vec output of kpm_moments): mu_mean[n] and mu_err[n], the mean and
+ * its standard error sqrt(sum_r (mu_n^r - mean)^2 / ((nvec-1) nvec)) (0 when
+ * nvec = 1); and the DOS of every vector on the K nodes of kpm_dos_kernel,
+ * with rho_mean[k] (equal to the DOS of mu_mean) and its standard error
+ * rho_err[k].  Any output may be NULL; inputs and outputs host or device;
+ * FP64 on the device.  nvec >= 1, M and K as kpm_dos, nvec * K <= 1<<28. */
+kpm_status kpm_stats(const double* pv, int nvec, int M, double a, double b, int K, int kernel,
+                     double lambda, double* mu_mean, double* mu_err, double* E,
+                     double* rho_mean, double* rho_err, void* stream);
+
+/* Adaptive number of random vectors: repeats kpm_moments with the parameters
+ * p (seed p->seed + round for round = 0, 1, ...) until the integrated
+ * standard error of the DOS, sum_k rho_err[k] * a pi sqrt(1 - x_k^2) / K
+ * (the Gauss-Chebyshev quadrature of int |sigma_rho(E)| dE), is at most
+ * target or max_rounds rounds have run.  Outputs are over all rounds' vectors
+ * as kpm_stats (mu, E, rho, rho_err host or device; mu_err may be NULL);
+ * *rounds and *achieved (host) receive the rounds run and the final error.
+ * Requires p->user_v0 == NULL.  Returns what kpm_moments returns on error. */
+kpm_status kpm_moments_adaptive(kpm_handle h, const kpm_params* p, int K, int kernel,
+                                double lambda, double target, int max_rounds, double* mu,
+                                double* mu_err, double* E, double* rho, double* rho_err,
+                                int* rounds, double* achieved, void* stream);
 
 /* Device time of the fused-step chain of the most recent kpm_moments call on
  * this handle: from the first fused step to the end of the last cross-CTA

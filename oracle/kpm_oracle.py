@@ -25,6 +25,11 @@ Rev. Mod. Phys. 78, 275 (2006)):
   lanczos_bounds         k-step Lanczos with full reorthogonalisation, Ritz
                          value +- residual |beta_k s_k|, clamped to Gershgorin  [pinned]
   rescale                Eq. (tilde): a = (Emax-Emin)/(2-eps), b = (Emax+Emin)/2
+  lorentz_kernel         review Eq. 74: g_n = sinh(lambda (1 - n/M)) / sinh(lambda)  [pinned]
+  dos_many, stats        the DOS of each vector's moments (Eq. (fKPM)), and the
+                         mean and standard error over the independent vectors
+                         of the moments and of the DOS (the spread behind the
+                         average of Eq. (munr))                                 [pinned]
 
 Notation: N = matrix dimension (the paper's D), M = number of moments (the
 paper's N), R = random vectors per realisation.  All arithmetic is float64 /
@@ -40,6 +45,7 @@ import numpy as np
 __all__ = [
     "CSR", "lattice_hamiltonian", "dense", "gershgorin", "lanczos_bounds", "rescale",
     "moments_direct", "moments_doubling", "exact_moments", "jackson_kernel", "dos",
+    "lorentz_kernel", "damping", "dos_many", "stats", "dos_error_integral",
 ]
 
 
@@ -141,6 +147,47 @@ def dense(H: CSR) -> np.ndarray:
     A = np.zeros((H.n, H.n), dtype=H.val.dtype)
     A[H._row, H.col] += H.val
     return A
+
+
+def dos_many(P, a: float, b: float, K: int, kernel: str = "jackson", lam: float = 0.0):
+    """Eq. (fKPM) for each row of P[nvec, M] (the moments of one vector each):
+    the same series as dos(), with the node sums done as one matrix product
+    against T[n, k] = cos(n pi (k + 1/2) / K).  Returns (E[K], rho[nvec, K])."""
+    P = np.atleast_2d(np.asarray(P, dtype=np.float64))
+    M = P.shape[1]
+    g = damping(M, kernel, lam) * np.where(np.arange(M) == 0, 1.0, 2.0)
+    phase = math.pi * (np.arange(K) + 0.5) / K
+    T = np.cos(np.arange(M)[:, None] * phase[None, :])
+    f = (P * g[None, :]) @ T / (math.pi * np.sin(phase))[None, :]
+    return a * np.cos(phase) + b, f / a
+
+
+def stats(P, a: float, b: float, K: int, kernel: str = "jackson", lam: float = 0.0):
+    """Mean and standard error over the nvec independent vectors (rows of
+    P[nvec, M]) of the moments and of the per-vector DOS:
+    err = sqrt(sum_r (x_r - mean)^2 / ((nvec - 1) nvec)), 0 for one vector.
+    Returns (mu_mean, mu_err, E, rho_mean, rho_err)."""
+    P = np.atleast_2d(np.asarray(P, dtype=np.float64))
+    nv = P.shape[0]
+    E, rho = dos_many(P, a, b, K, kernel, lam)
+
+    def mean_err(X):
+        m = X.mean(axis=0)
+        if nv < 2:
+            return m, np.zeros_like(m)
+        return m, np.sqrt(((X - m) ** 2).sum(axis=0) / ((nv - 1) * nv))
+
+    mu_m, mu_e = mean_err(P)
+    rho_m, rho_e = mean_err(rho)
+    return mu_m, mu_e, E, rho_m, rho_e
+
+
+def dos_error_integral(rho_err, a: float) -> float:
+    """int |sigma_rho(E)| dE by the Gauss-Chebyshev rule on the K nodes:
+    sum_k rho_err[k] a pi sqrt(1 - x_k^2) / K."""
+    rho_err = np.asarray(rho_err, dtype=np.float64)
+    K = rho_err.size
+    return float(np.sum(rho_err * a * math.pi * np.sin(math.pi * (np.arange(K) + 0.5) / K)) / K)
 
 
 def gershgorin(H: CSR):
@@ -270,7 +317,22 @@ def jackson_kernel(M: int) -> np.ndarray:
     return ((M - n + 1) * np.cos(q * n) + np.sin(q * n) / math.tan(q)) / (M + 1)
 
 
-def dos(mu, a: float, b: float, K: int, kernel: str = "jackson"):
+def lorentz_kernel(M: int, lam: float) -> np.ndarray:
+    """Lorentz damping factors (review Eq. 74), n = 0 .. M-1:
+    g_n = sinh(lam (1 - n/M)) / sinh(lam), lam > 0."""
+    n = np.arange(M, dtype=np.float64)
+    return np.sinh(lam * (1.0 - n / M)) / math.sinh(lam)
+
+
+def damping(M: int, kernel: str = "jackson", lam: float = 0.0) -> np.ndarray:
+    if kernel == "jackson":
+        return jackson_kernel(M)
+    if kernel == "lorentz":
+        return lorentz_kernel(M, lam)
+    return np.ones(M)
+
+
+def dos(mu, a: float, b: float, K: int, kernel: str = "jackson", lam: float = 0.0):
     """Eq. (fKPM) evaluated on the K Chebyshev nodes x_k = cos(pi (k + 1/2) / K):
 
       f(x_k) = [g_0 mu_0 + 2 sum_{n=1}^{M-1} g_n mu_n T_n(x_k)] / (pi sqrt(1 - x_k^2)),
@@ -278,10 +340,11 @@ def dos(mu, a: float, b: float, K: int, kernel: str = "jackson"):
 
     by a direct double sum; E_k = a x_k + b, rho(E_k) = f(x_k) / a (so that
     the integral of rho over E is the integral of f over x).  kernel is
-    "jackson" or "none" (g_n = 1).  Returns (E[K], rho[K]), k = 0 .. K-1."""
+    "jackson", "lorentz" (with lam) or "none" (g_n = 1).  Returns (E[K], rho[K]),
+    k = 0 .. K-1."""
     mu = np.asarray(mu, dtype=np.float64)
     M = mu.size
-    g = jackson_kernel(M) if kernel == "jackson" else np.ones(M)
+    g = damping(M, kernel, lam)
     phase = math.pi * (np.arange(K) + 0.5) / K
     x = np.cos(phase)
     f = np.empty(K)

@@ -202,8 +202,12 @@ void plan_grid(const kpm_handle_s* h, bool fp32, StepArgs& a, int* block, int* g
     }
   }
   a.chunk = KPM_STEP_CHUNK > 0 ? KPM_STEP_CHUNK : (a.line_len > 0 ? a.line_len : 4);
+  // small lattices: shorter chunks until every resident CTA has one (each
+  // CTA then walks fewer dependent passes per step)
+  const int64_t slots = (int64_t)h->num_sms * occ;
+  while (a.chunk > 1 && (a.passes + a.chunk - 1) / a.chunk < slots) a.chunk /= 2;
   const int64_t nchunks = (a.passes + a.chunk - 1) / a.chunk;
-  int64_t g = std::min<int64_t>((int64_t)h->num_sms * occ, nchunks);
+  int64_t g = std::min<int64_t>(slots, nchunks);
   *block = blk;
   *grid = (int)std::max<int64_t>(g, 1);
 }
@@ -898,13 +902,27 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
 
 kpm_status kpm_dos(const double* mu, int M, double a, double b, int K, int kernel, double* E,
                    double* rho, void* stream) {
-  if (!mu || !E || !rho) return fail(KPM_EINVAL, "NULL pointer");
+  if (kernel == KPM_KERNEL_LORENTZ) return fail(KPM_EINVAL, "the Lorentz kernel needs kpm_dos_kernel");
+  return kpm_dos_kernel(mu, M, a, b, K, kernel, 0.0, E, rho, stream);
+}
+
+static kpm_status check_series(int M, double a, double b, int K, int kernel, double lambda) {
   if (M < 1 || M > (1 << 20) || K < 1 || K > (1 << 20)) return fail(KPM_EINVAL, "bad M or K");
   if (!(a > 0.0) || !isfinite(a) || !isfinite(b)) return fail(KPM_EINVAL, "bad a or b");
-  if (kernel != KPM_KERNEL_JACKSON && kernel != KPM_KERNEL_NONE)
+  if (kernel != KPM_KERNEL_JACKSON && kernel != KPM_KERNEL_NONE && kernel != KPM_KERNEL_LORENTZ)
     return fail(KPM_EINVAL, "bad kernel");
+  if (kernel == KPM_KERNEL_LORENTZ && !(lambda > 0.0 && lambda < 700.0))
+    return fail(KPM_EINVAL, "the Lorentz kernel needs 0 < lambda < 700");
+  return KPM_OK;
+}
+
+kpm_status kpm_dos_kernel(const double* mu, int M, double a, double b, int K, int kernel,
+                          double lambda, double* E, double* rho, void* stream) {
+  if (!mu || !E || !rho) return fail(KPM_EINVAL, "NULL pointer");
+  kpm_status s_ = check_series(M, a, b, K, kernel, lambda);
+  if (s_ != KPM_OK) return s_;
   int dev = 0;
-  kpm_status s_ = check_device(&dev);
+  s_ = check_device(&dev);
   if (s_ != KPM_OK) return s_;
   cudaStream_t st = (cudaStream_t)stream;
   const bool dmu = is_device_ptr(mu), dE = is_device_ptr(E), drho = is_device_ptr(rho);
@@ -923,15 +941,136 @@ kpm_status kpm_dos(const double* mu, int M, double a, double b, int K, int kerne
   if (!dE) { E_d = cur; cur += K; }
   double* rho_d = rho;
   if (!drho) { rho_d = cur; cur += K; }
-  cudaError_t e = launch_dos(mu_d, M, a, b, K, kernel, E_d, rho_d, work, st);
+  cudaError_t e = launch_dos(mu_d, M, a, b, K, kernel, lambda, E_d, rho_d, work, st);
   if (e == cudaSuccess && !dE)
     e = cudaMemcpyAsync(E, E_d, K * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && !drho)
     e = cudaMemcpyAsync(rho, rho_d, K * sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(work, st);
-  if (e != cudaSuccess) return cuda_fail(e, "kpm_dos");
+  if (e != cudaSuccess) return cuda_fail(e, "kpm_dos_kernel");
   if (!dE || !drho) KPM_CUDA(cudaStreamSynchronize(st));
   return KPM_OK;
+}
+
+// Device-side statistics into device or host outputs (NULL: skipped); pv_d on
+// the device.  Synchronises the stream when a host output was requested.
+static kpm_status stats_to(const double* pv_d, int nvec, int M, double a, double b, int K,
+                           int kernel, double lambda, double* mu_mean, double* mu_err, double* E,
+                           double* rho_mean, double* rho_err, cudaStream_t st) {
+  double* outs[5] = {mu_mean, mu_err, E, rho_mean, rho_err};
+  const size_t len[5] = {(size_t)M, (size_t)M, (size_t)K, (size_t)K, (size_t)K};
+  bool host[5];
+  size_t stage = 0;
+  for (int i = 0; i < 5; ++i) {
+    host[i] = outs[i] && !is_device_ptr(outs[i]);
+    if (host[i]) stage += len[i];
+  }
+  const size_t nwork = (size_t)M + 4 * (size_t)K + (size_t)K * nvec + stage;
+  double* work = nullptr;
+  KPM_CUDA(cudaMallocAsync((void**)&work, nwork * sizeof(double), st));
+  double* cur = work + M + 4 * (size_t)K + (size_t)K * nvec;
+  double* dst[5];
+  for (int i = 0; i < 5; ++i) {
+    dst[i] = outs[i];
+    if (host[i]) { dst[i] = cur; cur += len[i]; }
+  }
+  cudaError_t e = launch_stats(pv_d, nvec, M, a, b, K, kernel, lambda, dst[0], dst[1], dst[2],
+                               dst[3], dst[4], work, st);
+  bool any_host = false;
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+    if (host[i]) {
+      any_host = true;
+      e = cudaMemcpyAsync(outs[i], dst[i], len[i] * sizeof(double), cudaMemcpyDeviceToHost, st);
+    }
+  cudaFreeAsync(work, st);
+  if (e != cudaSuccess) return cuda_fail(e, "kpm_stats");
+  if (any_host) KPM_CUDA(cudaStreamSynchronize(st));
+  return KPM_OK;
+}
+
+kpm_status kpm_stats(const double* pv, int nvec, int M, double a, double b, int K, int kernel,
+                     double lambda, double* mu_mean, double* mu_err, double* E,
+                     double* rho_mean, double* rho_err, void* stream) {
+  if (!pv) return fail(KPM_EINVAL, "NULL pointer");
+  if (nvec < 1) return fail(KPM_EINVAL, "nvec must be >= 1");
+  kpm_status s_ = check_series(M, a, b, K, kernel, lambda);
+  if (s_ != KPM_OK) return s_;
+  if ((int64_t)nvec * K > (1LL << 28)) return fail(KPM_EINVAL, "nvec * K too large");
+  int dev = 0;
+  s_ = check_device(&dev);
+  if (s_ != KPM_OK) return s_;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double* pv_d = pv;
+  double* pv_tmp = nullptr;
+  if (!is_device_ptr(pv)) {
+    KPM_CUDA(cudaMallocAsync((void**)&pv_tmp, (size_t)nvec * M * sizeof(double), st));
+    KPM_CUDA(cudaMemcpyAsync(pv_tmp, pv, (size_t)nvec * M * sizeof(double),
+                             cudaMemcpyHostToDevice, st));
+    pv_d = pv_tmp;
+  }
+  s_ = stats_to(pv_d, nvec, M, a, b, K, kernel, lambda, mu_mean, mu_err, E, rho_mean, rho_err, st);
+  if (pv_tmp) cudaFreeAsync(pv_tmp, st);
+  return s_;
+}
+
+kpm_status kpm_moments_adaptive(kpm_handle h, const kpm_params* p, int K, int kernel,
+                                double lambda, double target, int max_rounds, double* mu,
+                                double* mu_err, double* E, double* rho, double* rho_err,
+                                int* rounds, double* achieved, void* stream) {
+  if (!h || !p) return fail(KPM_EINVAL, "NULL handle or params");
+  if (p->user_v0) return fail(KPM_EINVAL, "adaptive rounds draw their own vectors (user_v0 must be NULL)");
+  if (max_rounds < 1 || !(target >= 0.0)) return fail(KPM_EINVAL, "bad max_rounds or target");
+  const int S = p->S > 0 ? p->S : 1, R = p->R, M = p->M;
+  if (R < 1 || M < 2 || (M & 1)) return fail(KPM_EINVAL, "M must be even and >= 2, R >= 1");
+  kpm_status s_ = check_series(M, p->a, p->b, K, kernel, lambda);
+  if (s_ != KPM_OK) return s_;
+  const int64_t per_round = (int64_t)S * R;
+  if (per_round * max_rounds > (1LL << 28) / K) return fail(KPM_EINVAL, "too many vectors for K");
+  KPM_CUDA(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  double* pv = nullptr;
+  double* rerr_d = nullptr;
+  if ((s_ = dalloc(&pv, (size_t)per_round * max_rounds * M)) != KPM_OK) return s_;
+  if ((s_ = dalloc(&rerr_d, (size_t)K)) != KPM_OK) {
+    dfree(pv);
+    return s_;
+  }
+  std::vector<double> rerr((size_t)K);
+  double err = INFINITY;
+  int done = 0;
+  for (int round = 0; round < max_rounds; ++round) {
+    kpm_params q = *p;
+    q.seed = p->seed + (uint64_t)round;
+    s_ = kpm_moments(h, &q, nullptr, pv + (size_t)round * per_round * M, st);
+    if (s_ != KPM_OK) break;
+    done = round + 1;
+    s_ = stats_to(pv, (int)(per_round * done), M, p->a, p->b, K, kernel, lambda, nullptr, nullptr,
+                  nullptr, nullptr, rerr_d, st);
+    if (s_ != KPM_OK) break;
+    cudaError_t e = cudaMemcpyAsync(rerr.data(), rerr_d, K * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      s_ = cuda_fail(e, "kpm_moments_adaptive");
+      break;
+    }
+    err = 0.0;
+    for (int k = 0; k < K; ++k) err += rerr[k] * p->a * M_PI * sin(M_PI * (k + 0.5) / K) / K;
+    if (err <= target) break;
+  }
+  if (s_ == KPM_OK)
+    s_ = stats_to(pv, (int)(per_round * done), M, p->a, p->b, K, kernel, lambda, mu, mu_err, E,
+                  rho, rho_err, st);
+  cudaStreamSynchronize(st);
+  dfree(pv);
+  dfree(rerr_d);
+  if (rounds) *rounds = done;
+  if (achieved) *achieved = err;
+  if (s_ == KPM_OK && mu && !is_device_ptr(mu)) {
+    for (int n = 0; n < M; ++n)
+      if (!(fabs(mu[n]) <= 1.0 + 1e-6)) return fail(KPM_EDIVERGE, "a moment left [-1, 1]");
+  }
+  return s_;
 }
 
 }  // extern "C"

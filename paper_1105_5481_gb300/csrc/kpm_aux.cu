@@ -700,18 +700,24 @@ __global__ void tridiag_bounds_kernel(const double* alpha, const double* beta, i
 
 // ------------------------------------------------------------------ DOS (Eq. (fKPM))
 // coef[n] = c_n g_n mu_n with c_0 = 1, c_n = 2; Jackson g_n from the closed form.
-__global__ void dos_coef_kernel(const double* __restrict__ mu, int M, int kernel, double* coef) {
+// Damping factor g_n of the kernel: Jackson (review Eq. 71), Lorentz
+// g_n = sinh(lambda (1 - n/M)) / sinh(lambda) (review Eq. 74), or 1.
+__device__ __forceinline__ double damping(int n, int M, int kernel, double lambda, double cotq) {
+  if (kernel == KPM_KERNEL_JACKSON) {
+    double sn, cn;
+    sincospi((double)n / (double)(M + 1), &sn, &cn);
+    return ((double)(M - n + 1) * cn + sn * cotq) / (double)(M + 1);
+  }
+  if (kernel == KPM_KERNEL_LORENTZ) return sinh(lambda * (1.0 - (double)n / M)) / sinh(lambda);
+  return 1.0;
+}
+
+__global__ void dos_coef_kernel(const double* __restrict__ mu, int M, int kernel, double lambda,
+                                double* coef) {
   const double q = M_PI / (double)(M + 1);
   const double cotq = cos(q) / sin(q);
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < M; n += gridDim.x * blockDim.x) {
-    double g = 1.0;
-    if (kernel == KPM_KERNEL_JACKSON) {
-      double sn, cn;
-      sincospi((double)n / (double)(M + 1), &sn, &cn);
-      g = ((double)(M - n + 1) * cn + sn * cotq) / (double)(M + 1);
-    }
-    coef[n] = (n == 0 ? 1.0 : 2.0) * g * mu[n];
-  }
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < M; n += gridDim.x * blockDim.x)
+    coef[n] = (n == 0 ? 1.0 : 2.0) * damping(n, M, kernel, lambda, cotq) * (mu ? mu[n] : 1.0);
 }
 
 // table[j] = cos(pi j / (2K)), j = 0 .. 4K-1 (exact argument reduction for the DCT)
@@ -740,6 +746,73 @@ __global__ void dct_kernel(const double* __restrict__ coef, int M, double a, dou
     sincospi(((double)warp + 0.5) / (double)K, &sx, &cx);
     E[warp] = a * cx + b;
     rho[warp] = acc / (M_PI * sx) / a;
+  }
+}
+
+// Mean and standard error over nvec vectors of each moment: pv[r * M + n].
+__global__ void moment_stats_kernel(const double* __restrict__ pv, int nvec, int M, double* mean,
+                                    double* err) {
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < M; n += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < nvec; ++r) s += pv[(size_t)r * M + n];
+    const double m = s / nvec;
+    double v = 0.0;
+    for (int r = 0; r < nvec; ++r) {
+      const double d = pv[(size_t)r * M + n] - m;
+      v = fma(d, d, v);
+    }
+    if (mean) mean[n] = m;
+    if (err) err[n] = nvec > 1 ? sqrt(v / ((double)(nvec - 1) * nvec)) : 0.0;
+  }
+}
+
+// One CTA (LZ_BLOCK threads) per node k: the DOS of every vector's moments
+// (Eq. (fKPM) with the damping in g, which carries the factor 2 of n >= 1),
+// eight vectors at a time, kept in scratch[k * nvec + r]; then their mean and
+// standard error (two passes).
+__global__ void __launch_bounds__(LZ_BLOCK) dos_stats_kernel(
+    const double* __restrict__ pv, const double* __restrict__ g, int nvec, int M, double a,
+    double b, int K, const double* __restrict__ table, double* scratch, double* E, double* rmean,
+    double* rerr) {
+  __shared__ double red[LZ_WARPS * 8];
+  __shared__ double s_mean;
+  const int k = blockIdx.x;
+  const int64_t step = 2LL * k + 1, n4 = 4LL * K;
+  double sx, cx;
+  sincospi(((double)k + 0.5) / (double)K, &sx, &cx);
+  const double scale = 1.0 / (M_PI * sx) / a;
+  double* rk = scratch + (size_t)k * nvec;
+  for (int r0 = 0; r0 < nvec; r0 += 8) {
+    double acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = 0.0;
+    for (int n = threadIdx.x; n < M; n += LZ_BLOCK) {
+      const double t = g[n] * table[((int64_t)n * step) % n4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (r0 + i < nvec) acc[i] = fma(pv[(size_t)(r0 + i) * M + n], t, acc[i]);
+    }
+    const double tot = block_multi_sum<8>(acc, red);
+    if ((int)threadIdx.x < 8 && r0 + (int)threadIdx.x < nvec) rk[r0 + threadIdx.x] = tot * scale;
+    __syncthreads();
+  }
+  double v[1] = {0.0};
+  for (int r = threadIdx.x; r < nvec; r += LZ_BLOCK) v[0] += rk[r];
+  double tot = block_multi_sum<1>(v, red);
+  if (threadIdx.x == 0) s_mean = tot / nvec;
+  __syncthreads();
+  const double m = s_mean;
+  v[0] = 0.0;
+  for (int r = threadIdx.x; r < nvec; r += LZ_BLOCK) {
+    const double d = rk[r] - m;
+    v[0] = fma(d, d, v[0]);
+  }
+  __syncthreads();
+  tot = block_multi_sum<1>(v, red);
+  if (threadIdx.x == 0) {
+    if (E) E[k] = a * cx + b;
+    if (rmean) rmean[k] = m;
+    if (rerr) rerr[k] = nvec > 1 ? sqrt(tot / ((double)(nvec - 1) * nvec)) : 0.0;
   }
 }
 
@@ -907,11 +980,38 @@ cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, int m
   return counted(cudaGetLastError());
 }
 
-cudaError_t launch_dos(const double* mu, int M, double a, double b, int K, int kernel, double* E,
-                       double* rho, double* work, cudaStream_t st) {
+cudaError_t launch_stats(const double* pv, int nvec, int M, double a, double b, int K, int kernel,
+                         double lambda, double* mu_mean, double* mu_err, double* E, double* rmean,
+                         double* rerr, double* work, cudaStream_t st) {
+  // work: g[M], table[4K], scratch[K * nvec]
+  double* g = work;
+  double* table = work + M;
+  double* scratch = table + 4 * (size_t)K;
+  if (mu_mean || mu_err) {
+    moment_stats_kernel<<<blocks_for(M, 256), 256, 0, st>>>(pv, nvec, M, mu_mean, mu_err);
+    counted(cudaSuccess);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (!E && !rmean && !rerr) return cudaSuccess;
+  dos_coef_kernel<<<blocks_for(M, 256), 256, 0, st>>>(nullptr, M, kernel, lambda, g);
+  counted(cudaSuccess);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  cos_table_kernel<<<blocks_for(4LL * K, 256), 256, 0, st>>>(K, table);
+  counted(cudaSuccess);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dos_stats_kernel<<<K, LZ_BLOCK, 0, st>>>(pv, g, nvec, M, a, b, K, table, scratch, E, rmean,
+                                           rerr);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_dos(const double* mu, int M, double a, double b, int K, int kernel,
+                       double lambda, double* E, double* rho, double* work, cudaStream_t st) {
   double* coef = work;
   double* table = work + M;
-  dos_coef_kernel<<<blocks_for(M, 256), 256, 0, st>>>(mu, M, kernel, coef);
+  dos_coef_kernel<<<blocks_for(M, 256), 256, 0, st>>>(mu, M, kernel, lambda, coef);
   counted(cudaSuccess);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -162,7 +162,12 @@ cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, int m
                                   const double* gersh, double pad_eps, double* out,
                                   cudaStream_t st);
 cudaError_t launch_dos(const double* mu, int M, double a, double b, int K, int kernel,
-                       double* E, double* rho, double* work, cudaStream_t st);
+                       double lambda, double* E, double* rho, double* work, cudaStream_t st);
+// mean and standard error over nvec vectors (pv[r*M + n]) of the moments and
+// of the per-vector DOS; any output may be NULL; work holds M + 4K + K*nvec doubles
+cudaError_t launch_stats(const double* pv, int nvec, int M, double a, double b, int K, int kernel,
+                         double lambda, double* mu_mean, double* mu_err, double* E, double* rmean,
+                         double* rerr, double* work, cudaStream_t st);
 
 // Vector columns per chunk and chunk rounding of R (shared by all entry points).
 int vec_per_chunk(bool fp32, bool cplx);

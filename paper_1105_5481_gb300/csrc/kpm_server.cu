@@ -401,7 +401,7 @@ void worker_loop(kpm_server_s* s) {
       if (err != cudaSuccess || pe.second != r->steps) continue;
       cudaStream_t rs = r->st;
       if (r->K > 0)
-        err = launch_dos(r->mu, r->p.M, r->a, r->b, r->K, KPM_KERNEL_JACKSON, r->E, r->rho,
+        err = launch_dos(r->mu, r->p.M, r->a, r->b, r->K, KPM_KERNEL_JACKSON, 0.0, r->E, r->rho,
                          r->dos_work, rs);
       r->out_mu.resize(r->p.M);
       if (err == cudaSuccess)

@@ -22,7 +22,8 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "kpm.h")
 KPM_OK, KPM_EINVAL, KPM_ENOMEM, KPM_ECUDA, KPM_ETIMEOUT, KPM_EDIVERGE, KPM_EBUSY, KPM_ENOTREADY = range(8)
 KPM_REAL, KPM_COMPLEX = 0, 1
 KPM_FP64, KPM_FP32_VEC_FP64_MOM = 0, 1
-KPM_KERNEL_JACKSON, KPM_KERNEL_NONE = 0, 1
+KPM_KERNEL_JACKSON, KPM_KERNEL_NONE, KPM_KERNEL_LORENTZ = 0, 1, 2
+KERNELS = {"jackson": KPM_KERNEL_JACKSON, "none": KPM_KERNEL_NONE, "lorentz": KPM_KERNEL_LORENTZ}
 PRECISIONS = {"fp64": KPM_FP64, "fp32": KPM_FP32_VEC_FP64_MOM, KPM_FP64: KPM_FP64,
               KPM_FP32_VEC_FP64_MOM: KPM_FP32_VEC_FP64_MOM}
 STATUS_NAMES = {0: "KPM_OK", 1: "KPM_EINVAL", 2: "KPM_ENOMEM", 3: "KPM_ECUDA", 4: "KPM_ETIMEOUT",
@@ -74,6 +75,13 @@ def lib() -> C.CDLL:
         L.kpm_moments.argtypes = [h, C.POINTER(kpm_params), C.c_void_p, C.c_void_p, C.c_void_p]
         L.kpm_dos.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                               C.c_void_p, C.c_void_p, C.c_void_p]
+        L.kpm_dos_kernel.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                                     C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.kpm_stats.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                                C.c_int, C.c_double] + [C.c_void_p] * 6
+        L.kpm_moments_adaptive.argtypes = [h, C.POINTER(kpm_params), C.c_int, C.c_int, C.c_double,
+                                           C.c_double, C.c_int] + [C.c_void_p] * 5 + [
+                                           C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
         L.kpm_info.argtypes = [h, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int),
                                C.POINTER(C.c_int)]
         L.kpm_step_timing.argtypes = [h, C.POINTER(C.c_double), C.POINTER(C.c_int)]
@@ -275,17 +283,53 @@ def kpm_moments(h: Handle, M, R, a, b, seed=0, S=1, precision="fp64", user_v0=No
     return (mu, pv) if per_vec or out_per_vec is not None else mu
 
 
-def kpm_dos(mu, a, b, K, kernel="jackson", E=None, rho=None, stream=None):
-    """Returns (E[K], rho[K]); host arrays unless device tensors are passed."""
+def kpm_dos(mu, a, b, K, kernel="jackson", E=None, rho=None, stream=None, lam=None):
+    """Returns (E[K], rho[K]); host arrays unless device tensors are passed.
+    kernel: "jackson", "none" or "lorentz" (with lam > 0)."""
     if not hasattr(mu, "data_ptr"):
         mu = np.ascontiguousarray(mu, dtype=np.float64)
     M = int(mu.shape[0])
     E = np.zeros(int(K)) if E is None else E
     rho = np.zeros(int(K)) if rho is None else rho
-    k = KPM_KERNEL_JACKSON if kernel == "jackson" else KPM_KERNEL_NONE
-    _check(lib().kpm_dos(_ptr(mu), M, float(a), float(b), int(K), k, _ptr(E), _ptr(rho),
-                         _stream(stream)))
+    if kernel == "lorentz" or lam is not None:
+        _check(lib().kpm_dos_kernel(_ptr(mu), M, float(a), float(b), int(K), KERNELS[kernel],
+                                    float(lam or 0.0), _ptr(E), _ptr(rho), _stream(stream)))
+    else:
+        _check(lib().kpm_dos(_ptr(mu), M, float(a), float(b), int(K), KERNELS[kernel], _ptr(E),
+                             _ptr(rho), _stream(stream)))
     return E, rho
+
+
+def kpm_stats(pv, a, b, K, kernel="jackson", lam=None, stream=None):
+    """Mean and standard error over the vectors (rows of pv[nvec, M]) of the
+    moments and of the per-vector DOS: returns (mu_mean, mu_err, E, rho_mean,
+    rho_err) as host arrays."""
+    if not hasattr(pv, "data_ptr"):
+        pv = np.ascontiguousarray(pv, dtype=np.float64)
+    pv2 = pv if len(pv.shape) == 2 else pv.reshape(1, -1)
+    nvec, M = int(pv2.shape[0]), int(pv2.shape[1])
+    out = [np.zeros(M), np.zeros(M), np.zeros(int(K)), np.zeros(int(K)), np.zeros(int(K))]
+    _check(lib().kpm_stats(_ptr(pv2), nvec, M, float(a), float(b), int(K), KERNELS[kernel],
+                           float(lam or 0.0), *[_ptr(o) for o in out], _stream(stream)))
+    return tuple(out)
+
+
+def kpm_moments_adaptive(h: Handle, M, R, a, b, K, target, max_rounds, seed=0, S=1,
+                         precision="fp32", kernel="jackson", lam=None, stream=None):
+    """Rounds of R (x S) new random vectors (seed + round) until the integrated
+    DOS standard error is <= target: returns dict(mu, mu_err, E, rho, rho_err,
+    rounds, error)."""
+    p = kpm_params()
+    p.M, p.R, p.S, p.seed = int(M), int(R), int(S), int(seed) & 0xFFFFFFFFFFFFFFFF
+    p.precision = PRECISIONS[precision]
+    p.a, p.b = float(a), float(b)
+    out = [np.zeros(int(M)), np.zeros(int(M)), np.zeros(int(K)), np.zeros(int(K)), np.zeros(int(K))]
+    rounds, err = C.c_int(), C.c_double()
+    _check(lib().kpm_moments_adaptive(h.raw, C.byref(p), int(K), KERNELS[kernel], float(lam or 0.0),
+                                      float(target), int(max_rounds), *[_ptr(o) for o in out],
+                                      C.byref(rounds), C.byref(err), _stream(stream)))
+    return dict(mu=out[0], mu_err=out[1], E=out[2], rho=out[3], rho_err=out[4],
+                rounds=rounds.value, error=err.value)
 
 
 def kpm_info(h: Handle):

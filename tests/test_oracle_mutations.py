@@ -31,7 +31,11 @@ MUTATIONS = {
     "jackson_off_by_one": ("((M - n + 1) * np.cos", "((M - n) * np.cos"),
     "dos_missing_two": ("s += 2.0 * g[n]", "s += g[n]"),
     "dos_missing_jacobian": ("return a * x + b, f / a", "return a * x + b, f"),
-    "dos_wrong_node": ("(np.arange(K) + 0.5) / K", "(np.arange(K) + 1.0) / K"),
+    "dos_wrong_node": ("(np.arange(K) + 0.5) / K\n    x = np.cos(phase)",
+                       "(np.arange(K) + 1.0) / K\n    x = np.cos(phase)"),
+    "lorentz_wrong_argument": ("np.sinh(lam * (1.0 - n / M))", "np.sinh(lam * (1.0 - n / (M + 1)))"),
+    "stats_biased_error": ("/ ((nv - 1) * nv))", "/ (nv * nv))"),
+    "dos_many_missing_two": ("np.where(np.arange(M) == 0, 1.0, 2.0)", "1.0"),
     "exact_missing_norm": (".mean(axis=1)", ".sum(axis=1)"),
     "gershgorin_no_abs": ("np.abs(H.val[~on])", "H.val[~on].real"),
     "lanczos_no_residual": ("emax = theta[-1] + bk * abs(S[m - 1, -1])", "emax = theta[-1]"),
@@ -94,6 +98,22 @@ def checks(O):
         c[0] = g[0] * mu[0]
         check("dos", np.allclose(E, 2.0 * xk + 0.1) and
               np.allclose(rho, C.chebval(xk, c) / (np.pi * np.sqrt(1 - xk * xk)) / 2.0, rtol=1e-12))
+        # Lorentz kernel: the damped cosine series against its geometric closed form
+        Ml, lam = 24, 3.0
+        gl = O.lorentz_kernel(Ml, lam)
+        r = math.exp(-lam / Ml)
+        z = np.exp(1j * np.array([0.4, 1.3, 2.9]))
+        G = lambda q: (1 - q ** Ml) / (1 - q)
+        closed = 2 * ((math.exp(lam) * G(r * z) - math.exp(-lam) * G(z / r)) / (2 * math.sinh(lam))).real - 1
+        nl = np.arange(Ml)
+        direct = (((2.0 - (nl == 0)) * gl)[None, :] * np.cos(nl[None, :] * np.angle(z)[:, None])).sum(1)
+        check("lorentz", np.allclose(direct, closed, atol=1e-10))
+        # error bars: two vectors x1, x2 give the standard error |x1 - x2| / 2 exactly;
+        # the mean DOS is the DOS of the mean moments
+        P = np.array([np.linspace(1, -0.5, M), np.linspace(1, 0.3, M)])
+        mu_m, mu_e, E2, rho_m, rho_e = O.stats(P, 2.0, 0.1, K)
+        check("stderr", np.allclose(mu_e, np.abs(P[0] - P[1]) / 2, atol=1e-15))
+        check("linear", np.allclose(rho_m, O.dos(P.mean(0), 2.0, 0.1, K)[1], atol=1e-12))
     except Exception as e:  # a mutant that crashes is caught too
         fails.append("exception:" + type(e).__name__)
     return fails
