@@ -26,6 +26,8 @@ Rev. Mod. Phys. 78, 275 (2006)):
                          value +- residual |beta_k s_k|, clamped to Gershgorin  [pinned]
   rescale                Eq. (tilde): a = (Emax-Emin)/(2-eps), b = (Emax+Emin)/2
   lorentz_kernel         review Eq. 74: g_n = sinh(lambda (1 - n/M)) / sinh(lambda)  [pinned]
+  ldos_exact             local moments <i|T_n(H~)|i> = sum_k |U_ik|^2 T_n(E~_k)
+                         (the KPM review's local DOS, a unit start vector)      [pinned]
   dos_many, stats        the DOS of each vector's moments (Eq. (fKPM)), and the
                          mean and standard error over the independent vectors
                          of the moments and of the DOS (the spread behind the
@@ -45,7 +47,7 @@ import numpy as np
 __all__ = [
     "CSR", "lattice_hamiltonian", "dense", "gershgorin", "lanczos_bounds", "rescale",
     "moments_direct", "moments_doubling", "exact_moments", "jackson_kernel", "dos",
-    "lorentz_kernel", "damping", "dos_many", "stats", "dos_error_integral",
+    "lorentz_kernel", "damping", "dos_many", "stats", "dos_error_integral", "ldos_exact",
 ]
 
 
@@ -307,6 +309,17 @@ def exact_moments(H: CSR, a: float, b: float, M: int) -> np.ndarray:
     x = np.clip((lam - b) / a, -1.0, 1.0)
     n = np.arange(M)[:, None]
     return np.cos(n * np.arccos(x)[None, :]).mean(axis=1)
+
+
+def ldos_exact(H: CSR, a: float, b: float, sites, M: int) -> np.ndarray:
+    """Local moments mu_n(i) = <i|T_n(H~)|i> = sum_k |U_ik|^2 cos(n arccos E~_k) for
+    each site i in `sites`, from a dense eigendecomposition (small N only).
+    Returns [len(sites), M]."""
+    lam, U = np.linalg.eigh(dense(H))
+    x = np.clip((lam - b) / a, -1.0, 1.0)
+    T = np.cos(np.arange(M)[:, None] * np.arccos(x)[None, :])  # [M, N]
+    W = np.abs(U[np.asarray(sites, dtype=np.int64), :]) ** 2      # [sites, N]
+    return W @ T.T
 
 
 def jackson_kernel(M: int) -> np.ndarray:

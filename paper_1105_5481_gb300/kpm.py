@@ -283,6 +283,19 @@ def kpm_moments(h: Handle, M, R, a, b, seed=0, S=1, precision="fp64", user_v0=No
     return (mu, pv) if per_vec or out_per_vec is not None else mu
 
 
+def kpm_ldos_moments(h: Handle, sites, M, a, b, precision="fp64", stream=None):
+    """Local Chebyshev moments <i|T_n(H~)|i> of the given sites: kpm_moments with the
+    start block of unit vectors sqrt(N) e_i (the estimator's 1/N normalisation).
+    Returns [len(sites), M]."""
+    sites = np.asarray(sites, dtype=np.int64)
+    n = int(kpm_info(h)["n"])
+    v0 = np.zeros((n, sites.size), dtype=np.complex128 if h.complex else np.float64)
+    v0[sites, np.arange(sites.size)] = np.sqrt(n)
+    _, pv = kpm_moments(h, M, sites.size, a, b, precision=precision, user_v0=v0, per_vec=True,
+                        stream=stream)
+    return pv
+
+
 def kpm_dos(mu, a, b, K, kernel="jackson", E=None, rho=None, stream=None, lam=None):
     """Returns (E[K], rho[K]); host arrays unless device tensors are passed.
     kernel: "jackson", "none" or "lorentz" (with lam > 0)."""

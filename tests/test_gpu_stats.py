@@ -57,7 +57,10 @@ def test_lorentz_dos_matches_oracle(K, lam):
     E, rho = K.kpm_dos(mu, 2.0, 0.1, 200, "lorentz", lam=lam)
     E_o, rho_o = O.dos(mu, 2.0, 0.1, 200, "lorentz", lam)
     np.testing.assert_allclose(E, E_o, rtol=0, atol=1e-14)
-    np.testing.assert_allclose(rho, rho_o, rtol=0, atol=1e-12)
+    # an FP64 series of M terms: rounding grows with M and with the largest value
+    # (weak damping leaves large values next to the band edges)
+    tol = 1e-12 * max(1.0, np.abs(rho_o).max()) * max(1, mu.size / 64)
+    np.testing.assert_allclose(rho, rho_o, rtol=0, atol=tol)
 
 
 def test_lorentz_needs_positive_lambda(K):
@@ -89,4 +92,21 @@ def test_adaptive_rounds_and_error(K):
     loose = 2.0 * res["error"]
     res2 = K.kpm_moments_adaptive(h, M, R, a, b, Kn, loose, 10, seed=50, precision="fp64")
     assert 1 <= res2["rounds"] <= 3 and res2["error"] <= loose
+    h.close()
+
+
+@pytest.mark.parametrize("complex_", [False, True], ids=["real", "complex"])
+def test_ldos_moments_match_exact(K, complex_):
+    L = (6, 5, 4)
+    n = 120
+    kw = {}
+    if complex_:
+        kw["hop"] = I.spin_hoppings(L, *I.spins(3, n))
+    onsite = I.onsite_disorder(8, n, 1.0)
+    H = O.lattice_hamiltonian(L, onsite=onsite, **kw)
+    h = K.kpm_create_stencil(3, L, onsite=onsite, complex_=complex_, **kw)
+    _, _, a, b = K.kpm_bounds(h, 0, 0.01)
+    sites = [0, 17, 119]
+    got = K.kpm_ldos_moments(h, sites, 64, a, b)
+    np.testing.assert_allclose(got, O.ldos_exact(H, a, b, sites, 64), rtol=0, atol=1e-10)
     h.close()

@@ -104,3 +104,19 @@ def test_dos_error_integral_of_a_constant():
     K, a, c = 257, 2.3, 0.01
     expect = c * a * math.pi / (K * math.sin(math.pi / (2 * K)))  # closed form of the node sum
     assert O.dos_error_integral(np.full(K, c), a) == pytest.approx(expect, rel=1e-13)
+
+
+def test_ldos_exact_sums_to_the_dos_and_is_local_for_diagonal_h():
+    # sum over all sites of <i|T_n|i> = Tr T_n = N mu_n (exact moments); for a
+    # diagonal H the local moments of site i are T_n(E~_i)
+    H = O.lattice_hamiltonian((5, 4), onsite=np.random.default_rng(2).uniform(-1, 1, 20))
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    loc = O.ldos_exact(H, a, b, np.arange(H.n), 30)
+    np.testing.assert_allclose(loc.sum(axis=0), H.n * O.exact_moments(H, a, b, 30), rtol=0,
+                               atol=1e-11)
+    d = np.array([0.3, -0.7, 1.1])
+    Hd = O.CSR(3, np.arange(4), np.arange(3), d)
+    loc = O.ldos_exact(Hd, 2.0, 0.1, [2, 0], 12)
+    x = (d - 0.1) / 2.0
+    np.testing.assert_allclose(loc, [np.cos(np.arange(12) * np.arccos(x[2])),
+                                     np.cos(np.arange(12) * np.arccos(x[0]))], atol=1e-13)
