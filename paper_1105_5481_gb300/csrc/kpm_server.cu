@@ -6,16 +6,21 @@
 //   1. admission: pending requests, first come first served, are made
 //      resident as soon as their device memory (two vector blocks, scaled
 //      operator, moment sums and outputs, DOS buffers) fits in the arena;
-//   2. advance: every resident request moves up to `steps_per_tick` products.
-//      Small and medium requests, grouped by operator kind and vector width,
-//      advance together in one batched persistent cluster launch per group
-//      (the instance task table is rewritten every tick, so requests that
-//      arrived during the previous tick join this one); large requests (a
-//      product moving >= 8 MB) advance as full-GPU fused steps on a pool of
-//      streams that overlap with the batched launches and with each other;
+//   2. advance: small and medium requests, grouped by operator kind and
+//      vector width, move up to `steps_per_tick` products together in one
+//      batched persistent cluster launch per group (the instance task table is
+//      rewritten every tick, so requests that arrived during the previous tick
+//      join this one); the tick waits for these launches only.  Large
+//      requests (a product moving >= 8 MB) run as full-GPU fused steps on a
+//      pool of streams, SOLO_CHUNK_TICKS * steps_per_tick products per
+//      enqueue, overlapping with the batched launches and with each other; the
+//      scheduler polls an event per large request and enqueues its next chunk
+//      once the previous one has finished, so the small requests' ticks are
+//      never paced by the large ones;
 //   3. retirement: finished requests get their Jackson DOS on the device,
 //      their results are copied to the host, their arena memory is released
-//      and their waiters are woken.
+//      (for a large request only after its last chunk has completed) and
+//      their waiters are woken.
 // A request's products are split among CTAs by a partition that depends only
 // on its own shape (and the server's cluster size), so its moments are the
 // same alone and in any mix, however its steps are spread over ticks.
@@ -44,6 +49,7 @@ namespace {
 constexpr size_t SOLO_STEP_BYTES = size_t(8) << 20;
 constexpr int MAX_GROUPS = 1024;
 constexpr int SOLO_STREAMS = 4;
+constexpr int SOLO_CHUNK_TICKS = 4;
 constexpr size_t ALIGN = 256;
 
 size_t al(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
@@ -138,6 +144,13 @@ struct Req {
   double a = 1.0, b = 0.0;
   std::vector<double> out_mu, out_E, out_rho;
   double t_submit = 0, t_admit = 0, t_done = 0;
+  // large requests: completion of the chunk in flight (ending at step inflight_end)
+  cudaEvent_t ev = nullptr;
+  bool inflight = false;
+  int inflight_end = 0;
+  ~Req() {
+    if (ev) cudaEventDestroy(ev);
+  }
 };
 
 uint64_t group_key(const Req* r) {
@@ -158,6 +171,7 @@ struct kpm_server_s {
   Arena arena;
   cudaStream_t stream = nullptr;                // batched groups
   cudaStream_t solo_streams[SOLO_STREAMS] = {};  // large requests (round robin)
+  cudaEvent_t ev_setup = nullptr;                // set-up of a tick's admitted requests
   BatchTask* d_tasks = nullptr;
   BatchTask* h_tasks = nullptr;  // pinned staging
   int* d_queue = nullptr;
@@ -264,6 +278,7 @@ cudaError_t solo_advance(kpm_server_s* s, Req* r, int b, int e) {
     a.y = r->v[(step + 1) & 1];
     a.w = a.y;
     a.partial = r->ring + (size_t)(step % r->ring_slots) * r->grid * 2 * r->Rp;
+    a.reverse = (step & 1) ^ 1;  // alternate sweep directions (see StepArgs)
     const StepMode mode = step == 0 ? MODE_FIRST : MODE_STEP;
     err = r->fp32 ? launch_step_f32(r->h->stencil, r->cplx, mode, a, cfg, st)
                   : launch_step_f64(r->h->stencil, r->cplx, mode, a, cfg, st);
@@ -331,11 +346,18 @@ void worker_loop(kpm_server_s* s) {
       if (e == cudaSuccess) prepare(s, r);
       if (e != cudaSuccess) fail_req(r, KPM_ECUDA, cudaGetErrorString(e));
     }
-    // the large requests' streams must see the set-up done on the main stream
+    // the large requests' streams wait for the set-up done on the main stream
     bool any_solo = false;
     for (Req* r : admitted) any_solo |= r->solo;
-    if (any_solo) cudaStreamSynchronize(st);
-    for (Req* r : admitted) r->st = r->solo ? s->solo_streams[r->id % SOLO_STREAMS] : st;
+    if (any_solo) cudaEventRecord(s->ev_setup, st);
+    for (Req* r : admitted) {
+      r->st = r->solo ? s->solo_streams[r->id % SOLO_STREAMS] : st;
+      if (r->solo) {
+        cudaError_t e = r->ev ? cudaSuccess : cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(r->st, s->ev_setup, 0);
+        if (e != cudaSuccess) fail_req(r, KPM_ECUDA, cudaGetErrorString(e));
+      }
+    }
     // advance: batched groups, then the large requests
     std::vector<Req*> live;
     for (Req* r : s->resident)
@@ -388,41 +410,95 @@ void worker_loop(kpm_server_s* s) {
                                         s->d_queue + gi, grid, s->C, st);
       ++gi;
     }
-    std::vector<std::pair<Req*, int>> advanced;
+    bool progressed = !groups.empty();
+    std::vector<std::pair<Req*, int>> advanced;  // batched requests, and large requests enqueued now
+    std::vector<Req*> enqueued;
     for (Req* r : live) {
-      const int e = std::min(r->step + s->steps_per_tick, r->steps);
-      if (r->solo && err == cudaSuccess) err = solo_advance(s, r, r->step, e);
-      advanced.emplace_back(r, e);
+      if (!r->solo) {
+        advanced.emplace_back(r, std::min(r->step + s->steps_per_tick, r->steps));
+        continue;
+      }
+      if (r->inflight || err != cudaSuccess) continue;
+      const int e = std::min(r->step + s->steps_per_tick * SOLO_CHUNK_TICKS, r->steps);
+      cudaError_t se = solo_advance(s, r, r->step, e);
+      if (se != cudaSuccess) {
+        cudaStreamSynchronize(r->st);  // nothing of it may still run when its memory is freed
+        cudaGetLastError();
+        fail_req(r, KPM_ECUDA, cudaGetErrorString(se));
+        continue;
+      }
+      r->inflight_end = e;
+      enqueued.push_back(r);
+      progressed = true;
     }
-    // DOS and result copies of the requests that finish in this tick, each on
-    // the stream that advanced it
-    for (auto& pe : advanced) {
+    // DOS and result copies of the requests that finish with this tick's work,
+    // each on the stream that advanced it
+    std::vector<std::pair<Req*, int>> finishing = advanced;
+    for (Req* r : enqueued) finishing.emplace_back(r, r->inflight_end);
+    for (auto& pe : finishing) {
       Req* r = pe.first;
-      if (err != cudaSuccess || pe.second != r->steps) continue;
+      if (pe.second != r->steps || (!r->solo && err != cudaSuccess)) continue;
       cudaStream_t rs = r->st;
+      cudaError_t fe = cudaSuccess;
       if (r->K > 0)
-        err = launch_dos(r->mu, r->p.M, r->a, r->b, r->K, KPM_KERNEL_JACKSON, 0.0, r->E, r->rho,
-                         r->dos_work, rs);
+        fe = launch_dos(r->mu, r->p.M, r->a, r->b, r->K, KPM_KERNEL_JACKSON, 0.0, r->E, r->rho,
+                        r->dos_work, rs);
       r->out_mu.resize(r->p.M);
-      if (err == cudaSuccess)
-        err = cudaMemcpyAsync(r->out_mu.data(), r->mu, r->p.M * sizeof(double),
-                              cudaMemcpyDeviceToHost, rs);
-      if (err == cudaSuccess && r->K > 0) {
+      if (fe == cudaSuccess)
+        fe = cudaMemcpyAsync(r->out_mu.data(), r->mu, r->p.M * sizeof(double),
+                             cudaMemcpyDeviceToHost, rs);
+      if (fe == cudaSuccess && r->K > 0) {
         r->out_E.resize(r->K);
         r->out_rho.resize(r->K);
-        err = cudaMemcpyAsync(r->out_E.data(), r->E, r->K * sizeof(double), cudaMemcpyDeviceToHost, rs);
-        if (err == cudaSuccess)
-          err = cudaMemcpyAsync(r->out_rho.data(), r->rho, r->K * sizeof(double),
-                                cudaMemcpyDeviceToHost, rs);
+        fe = cudaMemcpyAsync(r->out_E.data(), r->E, r->K * sizeof(double), cudaMemcpyDeviceToHost, rs);
+        if (fe == cudaSuccess)
+          fe = cudaMemcpyAsync(r->out_rho.data(), r->rho, r->K * sizeof(double),
+                               cudaMemcpyDeviceToHost, rs);
+      }
+      if (fe != cudaSuccess) {
+        if (r->solo)
+          fail_req(r, KPM_ECUDA, cudaGetErrorString(fe));  // still waits for its chunk in flight
+        else
+          err = fe;
       }
     }
+    for (Req* r : enqueued) {
+      cudaError_t e = cudaEventRecord(r->ev, r->st);
+      if (e != cudaSuccess) {
+        fail_req(r, KPM_ECUDA, cudaGetErrorString(e));
+        cudaStreamSynchronize(r->st);  // nothing of it may still run when its memory is freed
+        continue;
+      }
+      r->inflight = true;
+    }
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
-    for (int k = 0; k < SOLO_STREAMS && err == cudaSuccess; ++k)
-      err = cudaStreamSynchronize(s->solo_streams[k]);
     const double t = now_s();
     {
       std::lock_guard<std::mutex> lock(s->mu);
       ++s->ticks;
+      // large requests whose chunk in flight has completed
+      for (Req* r : s->resident) {
+        if (!r->solo || !r->inflight) continue;
+        const cudaError_t q = cudaEventQuery(r->ev);
+        if (q == cudaErrorNotReady) continue;
+        r->inflight = false;
+        progressed = true;
+        if (r->state == FAILED) continue;
+        if (q != cudaSuccess) {
+          cudaGetLastError();
+          fail_req(r, KPM_ECUDA, cudaGetErrorString(q));
+          continue;
+        }
+        r->step = r->inflight_end;
+        if (r->step == r->steps) {
+          bool bad = false;
+          for (double m : r->out_mu) bad |= !(fabs(m) <= 1.0 + 1e-6);
+          r->status = bad ? KPM_EDIVERGE : KPM_OK;
+          if (bad) r->error = "a moment left [-1, 1]: the bounds do not enclose the spectrum";
+          r->state = DONE;
+          r->t_done = now_s();
+        }
+      }
       for (auto& pe : advanced) {
         Req* r = pe.first;
         if (err != cudaSuccess) {
@@ -442,11 +518,11 @@ void worker_loop(kpm_server_s* s) {
       // retire finished, failed and cancelled requests
       std::vector<Req*> keep;
       for (Req* r : s->resident) {
-        if (r->state == RESIDENT && r->cancel) {
+        if (r->state == RESIDENT && r->cancel && !r->inflight) {
           r->state = CANCELLED;
           ++s->cancelled;
         }
-        if (r->state == RESIDENT) {
+        if (r->state == RESIDENT || r->inflight) {
           keep.push_back(r);
           continue;
         }
@@ -463,6 +539,8 @@ void worker_loop(kpm_server_s* s) {
       s->cv_done.notify_all();
     }
     if (err != cudaSuccess) cudaGetLastError();
+    // only large requests in flight and nothing to do: poll again shortly
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(100));
   }
 }
 
@@ -488,12 +566,19 @@ kpm_status kpm_server_create(size_t hbm_budget_bytes, int steps_per_tick, int cl
   s->steps_per_tick = steps_per_tick;
   s->C = cluster;
   cudaError_t e = s->arena.init(hbm_budget_bytes);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  // the batched groups (many small requests) get the highest stream priority,
+  // the large requests the lowest: the block scheduler then starts the small
+  // requests' CTAs first and fills the rest of the GPU with the large ones
+  int prio_low = 0, prio_high = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  if (e == cudaSuccess)
+    e = cudaStreamCreateWithPriority(&s->stream, cudaStreamNonBlocking, prio_high);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_setup, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_tasks, s->max_tasks * sizeof(BatchTask));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s->h_tasks, s->max_tasks * sizeof(BatchTask));
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_queue, MAX_GROUPS * sizeof(int));
   for (int k = 0; k < SOLO_STREAMS && e == cudaSuccess; ++k)
-    e = cudaStreamCreateWithFlags(&s->solo_streams[k], cudaStreamNonBlocking);
+    e = cudaStreamCreateWithPriority(&s->solo_streams[k], cudaStreamNonBlocking, prio_low);
   if (e != cudaSuccess) {
     kpm_status st = cuda_fail(e, "server set-up");
     s->arena.destroy();
@@ -537,7 +622,7 @@ kpm_status kpm_server_submit(kpm_server s, kpm_handle h, const kpm_params* p, in
     StepArgs probe{};
     operator_args(probe, h, nullptr, nullptr, nullptr, r->Rp, r->G);
     plan_step_grid(h, r->fp32, probe, &r->block, &r->grid);
-    r->ring_slots = s->steps_per_tick;
+    r->ring_slots = s->steps_per_tick * SOLO_CHUNK_TICKS;
   }
   r->bytes = layout(r, false, nullptr);
   if (r->bytes > s->arena.capacity()) {
@@ -654,6 +739,7 @@ void kpm_server_destroy(kpm_server s) {
   s->arena.destroy();
   cudaStreamDestroy(s->stream);
   for (int k = 0; k < SOLO_STREAMS; ++k) cudaStreamDestroy(s->solo_streams[k]);
+  if (s->ev_setup) cudaEventDestroy(s->ev_setup);
   cudaFree(s->d_tasks);
   cudaFreeHost(s->h_tasks);
   cudaFree(s->d_queue);
