@@ -48,7 +48,7 @@ def peaks():
 STEP_SOURCES = ["paper_1105_5481_gb300/csrc/kpm_step.cuh",
                 "paper_1105_5481_gb300/csrc/kpm_step_dispatch.cuh",
                 "paper_1105_5481_gb300/csrc/kpm_step_f32.cu",
-                "paper_1105_5481_gb300/csrc/kpm_internal.h"]
+                "paper_1105_5481_gb300/csrc/kpm_args.h"]
 BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_batch_dispatch.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_batch_f32.cu"]

@@ -118,3 +118,36 @@ def test_admission_under_a_small_budget_and_cancel(K):
     srv.close()
     for b_ in built:
         b_[0].close()
+
+
+def test_cancel_a_large_request_in_flight_returns_its_memory(K):
+    import time
+
+    # 3D L = 52 with R = 64: a full-GPU request (its products run on the large
+    # requests' streams, chunk after chunk, while the scheduler only polls)
+    h, H, a, b = build(K, "real", (52, 52, 52), 7)
+    M, R = 65536, 64
+    srv = K.kpm_server_create(2 << 30, 16, 4)
+    rid = K.kpm_server_submit(srv, h, M, R, a, b, seed=1)
+    K.kpm_server_wait(srv, rid, 300.0)
+    ref = K.kpm_server_poll(srv, rid)[0]
+    one = K.kpm_server_stats(srv)["peak_bytes"]
+    srv.close()
+    # a budget for one such request at a time
+    srv = K.kpm_server_create(int(one * 1.5), 16, 4)
+    big = K.kpm_server_submit(srv, h, M, R, a, b, seed=2)
+    time.sleep(0.15)  # a fraction of its 32768 products
+    K.kpm_server_cancel(srv, big)
+    K.kpm_server_wait(srv, big, 300.0)
+    with pytest.raises(K.KPMError):
+        K.kpm_server_poll(srv, big)
+    # its memory has come back: the same footprint is admitted and completes,
+    # with the moments of the same request served alone
+    again = K.kpm_server_submit(srv, h, M, R, a, b, seed=1)
+    K.kpm_server_wait(srv, again, 300.0)
+    mu = K.kpm_server_poll(srv, again)[0]
+    assert np.array_equal(mu, ref)
+    st = K.kpm_server_stats(srv)
+    assert st["cancelled"] == 1 and st["completed"] == 1 and st["peak_bytes"] <= int(one * 1.5)
+    srv.close()
+    h.close()
