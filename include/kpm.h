@@ -174,6 +174,18 @@ kpm_status kpm_dos(const double* mu, int M, double a, double b, int K, int kerne
 kpm_status kpm_dos_kernel(const double* mu, int M, double a, double b, int K, int kernel,
                           double lambda, double* E, double* rho, void* stream);
 
+/* Local Green's function from moments mu (e.g. the local moments of a unit
+ * start vector) by the KPM review's expansion (Eq. 86 there; the paper names
+ * Green's functions among the KPM quantities, Sec. I):
+ *   G(x + i0) = -i / sqrt(1 - x^2) [g_0 mu_0 + 2 sum_{n>=1} g_n mu_n exp(-i n arccos x)]
+ * on the K Chebyshev nodes of kpm_dos (E[k] = a x_k + b), in energy units
+ * (divided by a): g_re[k] = Re G, g_im[k] = Im G = -pi rho[k].  Damping as
+ * kpm_dos_kernel (the review recommends the Lorentz kernel for G).  mu, E,
+ * g_re, g_im host or device (E may be NULL); FP64 on the device; ranges and
+ * errors as kpm_dos_kernel. */
+kpm_status kpm_green(const double* mu, int M, double a, double b, int K, int kernel,
+                     double lambda, double* E, double* g_re, double* g_im, void* stream);
+
 /* Stochastic error bars (the paper's estimator Eq. (munr) averages over
  * independent random vectors, Sec. II-A-3; this reports their spread).  From
  * the per-vector moments pv[r*M + n] of nvec independent vectors (the

@@ -26,6 +26,8 @@ Rev. Mod. Phys. 78, 275 (2006)):
                          value +- residual |beta_k s_k|, clamped to Gershgorin  [pinned]
   rescale                Eq. (tilde): a = (Emax-Emin)/(2-eps), b = (Emax+Emin)/2
   lorentz_kernel         review Eq. 74: g_n = sinh(lambda (1 - n/M)) / sinh(lambda)  [pinned]
+  green                  local Green's function by the review's expansion
+                         G(x+i0) = -i/sqrt(1-x^2) [g_0 mu_0 + 2 sum g_n mu_n e^{-in arccos x}] [pinned]
   ldos_exact             local moments <i|T_n(H~)|i> = sum_k |U_ik|^2 T_n(E~_k)
                          (the KPM review's local DOS, a unit start vector)      [pinned]
   dos_many, stats        the DOS of each vector's moments (Eq. (fKPM)), and the
@@ -48,6 +50,7 @@ __all__ = [
     "CSR", "lattice_hamiltonian", "dense", "gershgorin", "lanczos_bounds", "rescale",
     "moments_direct", "moments_doubling", "exact_moments", "jackson_kernel", "dos",
     "lorentz_kernel", "damping", "dos_many", "stats", "dos_error_integral", "ldos_exact",
+    "green",
 ]
 
 
@@ -149,6 +152,25 @@ def dense(H: CSR) -> np.ndarray:
     A = np.zeros((H.n, H.n), dtype=H.val.dtype)
     A[H._row, H.col] += H.val
     return A
+
+
+def green(mu, a: float, b: float, K: int, kernel: str = "lorentz", lam: float = 4.0):
+    """Local Green's function on the K Chebyshev nodes by the KPM review's expansion
+    (Eq. 86 there), by a direct double sum:
+      G(x_k + i0) = -i/sqrt(1 - x_k^2) [g_0 mu_0 + 2 sum_{n=1}^{M-1} g_n mu_n e^{-i n theta_k}],
+    theta_k = pi (k + 1/2)/K, x_k = cos theta_k, in energy units (divided by a).
+    Returns (E[K], G[K] complex)."""
+    mu = np.asarray(mu, dtype=np.float64)
+    M = mu.size
+    g = damping(M, kernel, lam)
+    th = math.pi * (np.arange(K) + 0.5) / K
+    G = np.empty(K, dtype=np.complex128)
+    for k in range(K):
+        s = complex(g[0] * mu[0])
+        for n in range(1, M):
+            s += 2.0 * g[n] * mu[n] * complex(math.cos(n * th[k]), -math.sin(n * th[k]))
+        G[k] = -1j * s / math.sin(th[k]) / a
+    return a * np.cos(th) + b, G
 
 
 def dos_many(P, a: float, b: float, K: int, kernel: str = "jackson", lam: float = 0.0):

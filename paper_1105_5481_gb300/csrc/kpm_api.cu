@@ -952,6 +952,53 @@ kpm_status kpm_dos_kernel(const double* mu, int M, double a, double b, int K, in
   return KPM_OK;
 }
 
+kpm_status kpm_green(const double* mu, int M, double a, double b, int K, int kernel,
+                     double lambda, double* E, double* g_re, double* g_im, void* stream) {
+  if (!mu || !g_re || !g_im) return fail(KPM_EINVAL, "NULL pointer");
+  kpm_status s_ = check_series(M, a, b, K, kernel, lambda);
+  if (s_ != KPM_OK) return s_;
+  int dev = 0;
+  s_ = check_device(&dev);
+  if (s_ != KPM_OK) return s_;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* outs[3] = {E, g_re, g_im};
+  bool host[3];
+  size_t stage = 0;
+  for (int i = 0; i < 3; ++i) {
+    host[i] = outs[i] && !is_device_ptr(outs[i]);
+    if (host[i]) stage += K;
+  }
+  const bool dmu = is_device_ptr(mu);
+  const size_t nwork = (size_t)M + 4 * (size_t)K + (dmu ? 0 : M) + stage;
+  double* work = nullptr;
+  KPM_CUDA(cudaMallocAsync((void**)&work, nwork * sizeof(double), st));
+  double* cur = work + M + 4 * (size_t)K;
+  const double* mu_d = mu;
+  cudaError_t e = cudaSuccess;
+  if (!dmu) {
+    e = cudaMemcpyAsync(cur, mu, M * sizeof(double), cudaMemcpyHostToDevice, st);
+    mu_d = cur;
+    cur += M;
+  }
+  double* dst[3];
+  for (int i = 0; i < 3; ++i) {
+    dst[i] = outs[i];
+    if (host[i]) { dst[i] = cur; cur += K; }
+  }
+  if (e == cudaSuccess)
+    e = launch_green(mu_d, M, a, b, K, kernel, lambda, dst[0], dst[1], dst[2], work, st);
+  bool any_host = false;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+    if (host[i]) {
+      any_host = true;
+      e = cudaMemcpyAsync(outs[i], dst[i], K * sizeof(double), cudaMemcpyDeviceToHost, st);
+    }
+  cudaFreeAsync(work, st);
+  if (e != cudaSuccess) return cuda_fail(e, "kpm_green");
+  if (any_host) KPM_CUDA(cudaStreamSynchronize(st));
+  return KPM_OK;
+}
+
 // Device-side statistics into device or host outputs (NULL: skipped); pv_d on
 // the device.  Synchronises the stream when a host output was requested.
 static kpm_status stats_to(const double* pv_d, int nvec, int M, double a, double b, int K,

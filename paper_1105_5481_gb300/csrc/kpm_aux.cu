@@ -749,6 +749,37 @@ __global__ void dct_kernel(const double* __restrict__ coef, int M, double a, dou
   }
 }
 
+// Local Green's function on the nodes (one warp per node k): with c_n the
+// damped coefficients (factor 2 for n >= 1 included),
+//   C_k = sum_n c_n cos(n theta_k),  S_k = sum_n c_n sin(n theta_k),
+//   G(E_k + i0) = (-S_k - i C_k) / (a sin theta_k)   (Im G = -pi rho);
+// sin(pi j / (2K)) = cos(pi (j - K) / (2K)) = table[(j + 3K) mod 4K].
+__global__ void green_kernel(const double* __restrict__ coef, int M, double a, double b, int K,
+                             const double* __restrict__ table, double* E, double* g_re,
+                             double* g_im) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= K) return;
+  const int64_t step = 2LL * warp + 1, n4 = 4LL * K, k3 = 3LL * K;
+  double c = 0.0, sn = 0.0;
+  for (int n = lane; n < M; n += 32) {
+    const int64_t j = ((int64_t)n * step) % n4;
+    c = fma(coef[n], table[j], c);
+    sn = fma(coef[n], table[(j + k3) % n4], sn);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    sn += __shfl_xor_sync(0xffffffffu, sn, o);
+  }
+  if (lane == 0) {
+    double sx, cx;
+    sincospi(((double)warp + 0.5) / (double)K, &sx, &cx);
+    if (E) E[warp] = a * cx + b;
+    g_re[warp] = -sn / (a * sx);
+    g_im[warp] = -c / (a * sx);
+  }
+}
+
 // Mean and standard error over nvec vectors of each moment: pv[r * M + n].
 __global__ void moment_stats_kernel(const double* __restrict__ pv, int nvec, int M, double* mean,
                                     double* err) {
@@ -1004,6 +1035,23 @@ cudaError_t launch_stats(const double* pv, int nvec, int M, double a, double b, 
   if (e != cudaSuccess) return e;
   dos_stats_kernel<<<K, LZ_BLOCK, 0, st>>>(pv, g, nvec, M, a, b, K, table, scratch, E, rmean,
                                            rerr);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_green(const double* mu, int M, double a, double b, int K, int kernel,
+                         double lambda, double* E, double* g_re, double* g_im, double* work,
+                         cudaStream_t st) {
+  double* coef = work;
+  double* table = work + M;
+  dos_coef_kernel<<<blocks_for(M, 256), 256, 0, st>>>(mu, M, kernel, lambda, coef);
+  counted(cudaSuccess);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  cos_table_kernel<<<blocks_for(4LL * K, 256), 256, 0, st>>>(K, table);
+  counted(cudaSuccess);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  green_kernel<<<blocks_for(32LL * K, 256), 256, 0, st>>>(coef, M, a, b, K, table, E, g_re, g_im);
   return counted(cudaGetLastError());
 }
 

@@ -83,6 +83,10 @@ cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, int m
                                   cudaStream_t st);
 cudaError_t launch_dos(const double* mu, int M, double a, double b, int K, int kernel,
                        double lambda, double* E, double* rho, double* work, cudaStream_t st);
+// local Green's function on the K nodes (work holds M + 4K doubles)
+cudaError_t launch_green(const double* mu, int M, double a, double b, int K, int kernel,
+                         double lambda, double* E, double* g_re, double* g_im, double* work,
+                         cudaStream_t st);
 // mean and standard error over nvec vectors (pv[r*M + n]) of the moments and
 // of the per-vector DOS; any output may be NULL; work holds M + 4K + K*nvec doubles
 cudaError_t launch_stats(const double* pv, int nvec, int M, double a, double b, int K, int kernel,

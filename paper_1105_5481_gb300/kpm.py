@@ -77,6 +77,8 @@ def lib() -> C.CDLL:
                               C.c_void_p, C.c_void_p, C.c_void_p]
         L.kpm_dos_kernel.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.kpm_green.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                                C.c_double] + [C.c_void_p] * 4
         L.kpm_stats.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                 C.c_int, C.c_double] + [C.c_void_p] * 6
         L.kpm_moments_adaptive.argtypes = [h, C.POINTER(kpm_params), C.c_int, C.c_int, C.c_double,
@@ -311,6 +313,18 @@ def kpm_dos(mu, a, b, K, kernel="jackson", E=None, rho=None, stream=None, lam=No
         _check(lib().kpm_dos(_ptr(mu), M, float(a), float(b), int(K), KERNELS[kernel], _ptr(E),
                              _ptr(rho), _stream(stream)))
     return E, rho
+
+
+def kpm_green(mu, a, b, K, kernel="lorentz", lam=4.0, stream=None):
+    """Local Green's function G(E + i0) on the K Chebyshev nodes: returns
+    (E[K], G[K] complex) as host arrays (Im G = -pi rho)."""
+    if not hasattr(mu, "data_ptr"):
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+    M = int(mu.shape[0])
+    E, gr, gi = np.zeros(int(K)), np.zeros(int(K)), np.zeros(int(K))
+    _check(lib().kpm_green(_ptr(mu), M, float(a), float(b), int(K), KERNELS[kernel],
+                           float(lam or 0.0), _ptr(E), _ptr(gr), _ptr(gi), _stream(stream)))
+    return E, gr + 1j * gi
 
 
 def kpm_stats(pv, a, b, K, kernel="jackson", lam=None, stream=None):

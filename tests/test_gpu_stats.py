@@ -110,3 +110,15 @@ def test_ldos_moments_match_exact(K, complex_):
     got = K.kpm_ldos_moments(h, sites, 64, a, b)
     np.testing.assert_allclose(got, O.ldos_exact(H, a, b, sites, 64), rtol=0, atol=1e-10)
     h.close()
+
+
+@pytest.mark.parametrize("kernel", ["lorentz", "jackson"])
+def test_green_matches_oracle(K, kernel):
+    mu = _pv(13, 1, 400)[0]
+    mu[0] = 1.0
+    E, G = K.kpm_green(mu, 1.8, -0.3, 160, kernel, lam=4.0)
+    E_o, G_o = O.green(mu, 1.8, -0.3, 160, kernel, 4.0)
+    tol = 1e-12 * max(1.0, np.abs(G_o).max()) * (mu.size / 64)
+    np.testing.assert_allclose(E, E_o, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(G.real, G_o.real, rtol=0, atol=tol)
+    np.testing.assert_allclose(G.imag, G_o.imag, rtol=0, atol=tol)

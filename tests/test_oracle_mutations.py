@@ -29,7 +29,8 @@ MUTATIONS = {
     "rescale_shift_sign": ("return (H.matvec(X) - b * X) / a", "return (H.matvec(X) + b * X) / a"),
     "rescale_no_padding": ("return (emax - emin) / (2.0 - eps)", "return (emax - emin) / 2.0"),
     "jackson_off_by_one": ("((M - n + 1) * np.cos", "((M - n) * np.cos"),
-    "dos_missing_two": ("s += 2.0 * g[n]", "s += g[n]"),
+    "dos_missing_two": ("s += 2.0 * g[n] * mu[n] * math.cos", "s += g[n] * mu[n] * math.cos"),
+    "green_wrong_sign": ("-math.sin(n * th[k])", "math.sin(n * th[k])"),
     "dos_missing_jacobian": ("return a * x + b, f / a", "return a * x + b, f"),
     "dos_wrong_node": ("(np.arange(K) + 0.5) / K\n    x = np.cos(phase)",
                        "(np.arange(K) + 1.0) / K\n    x = np.cos(phase)"),
@@ -114,6 +115,17 @@ def checks(O):
         mu_m, mu_e, E2, rho_m, rho_e = O.stats(P, 2.0, 0.1, K)
         check("stderr", np.allclose(mu_e, np.abs(P[0] - P[1]) / 2, atol=1e-15))
         check("linear", np.allclose(rho_m, O.dos(P.mean(0), 2.0, 0.1, K)[1], atol=1e-12))
+        # Green's function of one level x0 (undamped limit checked through a damped
+        # series against its closed form): Re G from the sine series
+        x0 = 0.3
+        mu1 = np.cos(np.arange(Ml) * math.acos(x0))
+        _, Gf = O.green(mu1, 1.0, 0.0, 16, "lorentz", lam)
+        th = math.pi * (np.arange(16) + 0.5) / 16
+        t0 = math.acos(x0)
+        sines = lambda phi: 2 * ((math.exp(lam) * G(r * np.exp(1j * phi)) -
+                                  math.exp(-lam) * G(np.exp(1j * phi) / r)) / (2 * math.sinh(lam))).imag
+        Sk = 0.5 * (sines(th + t0) + sines(th - t0))
+        check("green", np.allclose(Gf.real, -Sk / np.sin(th), atol=1e-9))
     except Exception as e:  # a mutant that crashes is caught too
         fails.append("exception:" + type(e).__name__)
     return fails

@@ -120,3 +120,41 @@ def test_ldos_exact_sums_to_the_dos_and_is_local_for_diagonal_h():
     x = (d - 0.1) / 2.0
     np.testing.assert_allclose(loc, [np.cos(np.arange(12) * np.arccos(x[2])),
                                      np.cos(np.arange(12) * np.arccos(x[0]))], atol=1e-13)
+
+
+def lorentz_sine_closed(M, lam, phi):
+    """sum_{n<M} (2 - delta_n0) sinh(lam (1 - n/M))/sinh(lam) sin(n phi) (two finite
+    geometric sums, as lorentz_series_closed)."""
+    r = math.exp(-lam / M)
+
+    def G(z):
+        return (1.0 - z ** M) / (1.0 - z)
+
+    z = np.exp(1j * np.asarray(phi, dtype=np.float64))
+    s = (math.exp(lam) * G(r * z) - math.exp(-lam) * G(z / r)) / (2.0 * math.sinh(lam))
+    return 2.0 * s.imag
+
+
+@pytest.mark.parametrize("x0", [0.2, -0.55])
+def test_green_of_one_level_closed_form(x0):
+    # H = [x0], a = 1, b = 0: mu_n = T_n(x0); 2 cos(n t0) e^{-i n t} splits into the
+    # damped cosine and sine series at t -+ t0
+    M, K, lam = 256, 48, 4.0
+    mu = np.cos(np.arange(M) * math.acos(x0))
+    E, G = O.green(mu, 1.0, 0.0, K, "lorentz", lam)
+    th = math.pi * (np.arange(K) + 0.5) / K
+    t0 = math.acos(x0)
+    C = 0.5 * (lorentz_series_closed(M, lam, th - t0) + lorentz_series_closed(M, lam, th + t0))
+    S = 0.5 * (lorentz_sine_closed(M, lam, th + t0) + lorentz_sine_closed(M, lam, th - t0))
+    np.testing.assert_allclose(G.real, -S / np.sin(th), rtol=0, atol=1e-9)
+    np.testing.assert_allclose(G.imag, -C / np.sin(th), rtol=0, atol=1e-9)
+
+
+def test_green_imaginary_part_is_minus_pi_rho():
+    rng = np.random.default_rng(4)
+    mu = rng.uniform(-1, 1, 60) * np.exp(-np.arange(60) / 15.0)
+    for kernel in ("jackson", "lorentz", "none"):
+        E, G = O.green(mu, 2.2, 0.4, 37, kernel, 3.0)
+        E2, rho = O.dos(mu, 2.2, 0.4, 37, kernel, 3.0)
+        np.testing.assert_allclose(G.imag, -math.pi * rho, rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(E, E2, rtol=0, atol=1e-15)
