@@ -58,9 +58,9 @@ BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
 # profiles/cheb_step_fp32_csr_spin_dilute_L160.md: steady state of consecutive steps,
 # caches not flushed between launches; profiles/batch_kernel_fp32_batch_2d_256.md);
 # reported only while the hash matches.
-MEASURED_TRAFFIC = {"cubic_spin_L64": (347.56e6, "step", "fa838511f86e9da1"),
-                    "csr_spin_dilute_L160": (3445.37e6, "step", "fa838511f86e9da1"),
-                    "batch_2d_256/C4/chunk4/clusters74": (70.08e9, "batch", "24af8e5bedbe296f")}
+MEASURED_TRAFFIC = {"cubic_spin_L64": (347.85e6, "step", "450f06339ae280e0"),
+                    "csr_spin_dilute_L160": (3437.64e6, "step", "450f06339ae280e0"),
+                    "batch_2d_256/C4/chunk4/clusters74": (69.37e9, "batch", "69d68de30fea5c07")}
 
 
 def per_matvec(value):
