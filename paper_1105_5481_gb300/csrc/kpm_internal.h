@@ -166,6 +166,8 @@ struct kpm_handle_s {
     size_t v0stage_bytes = 0;
     cudaGraphExec_t exec = nullptr;
     uint64_t kernels_per_replay = 0;
+    bool ready = false;        // buffers and launch plan match the current shape
+    bool direct_done = false;  // one call of this shape ran without a graph
     kpm::StepArgs proto{};                    // launch arguments common to all steps
     cudaEvent_t ev[2] = {nullptr, nullptr};  // recorded around the step chain in the graph
     bool timed = false;
