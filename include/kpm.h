@@ -186,6 +186,22 @@ kpm_status kpm_dos_kernel(const double* mu, int M, double a, double b, int K, in
 kpm_status kpm_green(const double* mu, int M, double a, double b, int K, int kernel,
                      double lambda, double* E, double* g_re, double* g_im, void* stream);
 
+/* Finite-temperature integrals of the DOS (the thermodynamic quantities the
+ * KPM review obtains from the moments, Sec. IV there; the paper lists them
+ * among the KPM's uses, Sec. I).  For each inverse temperature beta[t]
+ * (+INFINITY: the ground state) and chemical potential mu_c, with Fermi
+ * occupation f(E) = 1/(1 + exp(beta (E - mu_c))), per site:
+ *   out[4t+0] = n = int rho f dE,   out[4t+1] = u = int E rho f dE,
+ *   out[4t+2] = s = -int rho [f ln f + (1-f) ln(1-f)] dE   (k_B = 1),
+ *   out[4t+3] = c = beta^2 int rho (E - mu_c)^2 f (1-f) dE = d(u - mu_c n)/dT,
+ * by the Gauss-Chebyshev rule on the K nodes of the damped DOS
+ * (kpm_dos_kernel): int g rho dE = sum_k g(E_k) rho_k a pi sqrt(1 - x_k^2) / K.
+ * mu, beta, out host or device; 1 <= nT <= 65535, beta >= 0; FP64 on the
+ * device; other ranges and errors as kpm_dos_kernel. */
+kpm_status kpm_thermo(const double* mu, int M, double a, double b, int K, int kernel,
+                      double lambda, const double* beta, int nT, double mu_c, double* out,
+                      void* stream);
+
 /* Stochastic error bars (the paper's estimator Eq. (munr) averages over
  * independent random vectors, Sec. II-A-3; this reports their spread).  From
  * the per-vector moments pv[r*M + n] of nvec independent vectors (the

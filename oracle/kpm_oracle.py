@@ -28,6 +28,8 @@ Rev. Mod. Phys. 78, 275 (2006)):
   lorentz_kernel         review Eq. 74: g_n = sinh(lambda (1 - n/M)) / sinh(lambda)  [pinned]
   green                  local Green's function by the review's expansion
                          G(x+i0) = -i/sqrt(1-x^2) [g_0 mu_0 + 2 sum g_n mu_n e^{-in arccos x}] [pinned]
+  thermo                 Fermi-occupation integrals of the DOS (n, u, s, c per
+                         site) by the Gauss-Chebyshev rule on the DOS nodes       [pinned]
   ldos_exact             local moments <i|T_n(H~)|i> = sum_k |U_ik|^2 T_n(E~_k)
                          (the KPM review's local DOS, a unit start vector)      [pinned]
   dos_many, stats        the DOS of each vector's moments (Eq. (fKPM)), and the
@@ -50,7 +52,7 @@ __all__ = [
     "CSR", "lattice_hamiltonian", "dense", "gershgorin", "lanczos_bounds", "rescale",
     "moments_direct", "moments_doubling", "exact_moments", "jackson_kernel", "dos",
     "lorentz_kernel", "damping", "dos_many", "stats", "dos_error_integral", "ldos_exact",
-    "green",
+    "green", "thermo",
 ]
 
 
@@ -171,6 +173,35 @@ def green(mu, a: float, b: float, K: int, kernel: str = "lorentz", lam: float = 
             s += 2.0 * g[n] * mu[n] * complex(math.cos(n * th[k]), -math.sin(n * th[k]))
         G[k] = -1j * s / math.sin(th[k]) / a
     return a * np.cos(th) + b, G
+
+
+def thermo(mu, a: float, b: float, K: int, betas, mu_c: float = 0.0, kernel: str = "jackson",
+           lam: float = 0.0):
+    """For each inverse temperature beta (inf: ground state), with the Fermi
+    occupation f = 1/(1 + exp(beta (E - mu_c))), the integrals per site
+      n = int rho f,  u = int E rho f,  s = -int rho [f ln f + (1-f) ln(1-f)],
+      c = beta^2 int rho (E - mu_c)^2 f (1-f)
+    by the Gauss-Chebyshev rule on the K nodes of dos():
+    int g rho dE = sum_k g(E_k) rho_k a pi sqrt(1 - x_k^2) / K.  Returns [nT, 4]."""
+    E, rho = dos(mu, a, b, K, kernel, lam)
+    w = a * math.pi * np.sin(math.pi * (np.arange(K) + 0.5) / K) / K
+    out = []
+    for beta in np.atleast_1d(betas):
+        d = E - mu_c
+        if math.isinf(beta):
+            f = np.where(d < 0, 1.0, np.where(d > 0, 0.0, 0.5))
+            ent = np.zeros(K)
+            cv = np.zeros(K)
+        else:
+            x = beta * d
+            f = 1.0 / (1.0 + np.exp(x))
+            with np.errstate(divide="ignore", invalid="ignore"):
+                ent = -(np.where(f > 0, f * np.log(f), 0.0) +
+                        np.where(f < 1, (1 - f) * np.log1p(-f), 0.0))
+            cv = x * x * f * (1 - f)
+        out.append([np.sum(w * rho * f), np.sum(w * rho * E * f), np.sum(w * rho * ent),
+                    np.sum(w * rho * cv)])
+    return np.array(out)
 
 
 def dos_many(P, a: float, b: float, K: int, kernel: str = "jackson", lam: float = 0.0):

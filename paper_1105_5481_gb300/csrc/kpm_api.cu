@@ -1023,6 +1023,56 @@ kpm_status kpm_green(const double* mu, int M, double a, double b, int K, int ker
   return KPM_OK;
 }
 
+kpm_status kpm_thermo(const double* mu, int M, double a, double b, int K, int kernel,
+                      double lambda, const double* beta, int nT, double mu_c, double* out,
+                      void* stream) {
+  if (!mu || !beta || !out) return fail(KPM_EINVAL, "NULL pointer");
+  if (nT < 1 || nT > 65535) return fail(KPM_EINVAL, "nT must be in 1..65535");
+  if (!isfinite(mu_c)) return fail(KPM_EINVAL, "mu_c must be finite");
+  kpm_status s_ = check_series(M, a, b, K, kernel, lambda);
+  if (s_ != KPM_OK) return s_;
+  const bool dbeta = is_device_ptr(beta);
+  if (!dbeta)
+    for (int t = 0; t < nT; ++t)
+      if (!(beta[t] >= 0.0)) return fail(KPM_EINVAL, "beta must be >= 0 (or +inf)");
+  int dev = 0;
+  s_ = check_device(&dev);
+  if (s_ != KPM_OK) return s_;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dmu = is_device_ptr(mu), dout = is_device_ptr(out);
+  // work: coef[M] table[4K] E[K] rho[K] (+ mu[M] beta[nT] out[4 nT] staging)
+  const size_t nwork = (size_t)M + 6 * (size_t)K + (dmu ? 0 : M) + (dbeta ? 0 : nT) +
+                       (dout ? 0 : 4 * (size_t)nT);
+  double* work = nullptr;
+  KPM_CUDA(cudaMallocAsync((void**)&work, nwork * sizeof(double), st));
+  double* E_d = work + M + 4 * (size_t)K;
+  double* rho_d = E_d + K;
+  double* cur = rho_d + K;
+  const double* mu_d = mu;
+  const double* beta_d = beta;
+  double* out_d = out;
+  cudaError_t e = cudaSuccess;
+  if (!dmu) {
+    e = cudaMemcpyAsync(cur, mu, M * sizeof(double), cudaMemcpyHostToDevice, st);
+    mu_d = cur;
+    cur += M;
+  }
+  if (e == cudaSuccess && !dbeta) {
+    e = cudaMemcpyAsync(cur, beta, nT * sizeof(double), cudaMemcpyHostToDevice, st);
+    beta_d = cur;
+    cur += nT;
+  }
+  if (!dout) { out_d = cur; cur += 4 * (size_t)nT; }
+  if (e == cudaSuccess) e = launch_dos(mu_d, M, a, b, K, kernel, lambda, E_d, rho_d, work, st);
+  if (e == cudaSuccess) e = launch_thermo(E_d, rho_d, K, a, beta_d, nT, mu_c, out_d, st);
+  if (e == cudaSuccess && !dout)
+    e = cudaMemcpyAsync(out, out_d, 4 * (size_t)nT * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(work, st);
+  if (e != cudaSuccess) return cuda_fail(e, "kpm_thermo");
+  if (!dout || !dmu || !dbeta) KPM_CUDA(cudaStreamSynchronize(st));
+  return KPM_OK;
+}
+
 // Device-side statistics into device or host outputs (NULL: skipped); pv_d on
 // the device.  Synchronises the stream when a host output was requested.
 static kpm_status stats_to(const double* pv_d, int nvec, int M, double a, double b, int K,

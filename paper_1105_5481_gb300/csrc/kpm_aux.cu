@@ -780,6 +780,43 @@ __global__ void green_kernel(const double* __restrict__ coef, int M, double a, d
   }
 }
 
+// Fermi-occupation integrals of the DOS on the K nodes, one CTA per inverse
+// temperature beta[t] (Gauss-Chebyshev weights w_k = a pi sin(theta_k) / K):
+// out[t] = (n, u, s, c) per site with f = 1/(1 + e^x), x = beta (E - mu_c):
+//   n = sum w rho f,  u = sum w rho E f,
+//   s = sum w rho [min(f, 1-f) |x| + log1p(e^-|x|)],  c = sum w rho x^2 f (1-f);
+// beta = +inf is the ground state (f = step, s = c = 0).
+__global__ void __launch_bounds__(LZ_BLOCK) thermo_kernel(const double* __restrict__ E,
+                                                          const double* __restrict__ rho, int K,
+                                                          double a, const double* __restrict__ beta,
+                                                          double mu_c, double* out) {
+  __shared__ double red[LZ_WARPS * 4];
+  const double bt = beta[blockIdx.x];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = threadIdx.x; k < K; k += LZ_BLOCK) {
+    double sx, cx;
+    sincospi(((double)k + 0.5) / (double)K, &sx, &cx);
+    const double wr = a * M_PI * sx / (double)K * rho[k];
+    const double e = E[k], d = e - mu_c;
+    double f, ent = 0.0, cv = 0.0;
+    if (isinf(bt)) {
+      f = d < 0.0 ? 1.0 : (d > 0.0 ? 0.0 : 0.5);
+    } else {
+      const double x = bt * d, ax = fabs(x), q = exp(-ax);  // q in (0, 1]
+      f = x >= 0.0 ? q / (1.0 + q) : 1.0 / (1.0 + q);
+      const double g = fmin(f, 1.0 - f);
+      ent = g * ax + log1p(q);
+      cv = x * x * f * (1.0 - f);
+    }
+    acc[0] = fma(wr, f, acc[0]);
+    acc[1] = fma(wr * e, f, acc[1]);
+    acc[2] = fma(wr, ent, acc[2]);
+    acc[3] = fma(wr, cv, acc[3]);
+  }
+  const double tot = block_multi_sum<4>(acc, red);
+  if (threadIdx.x < 4) out[(size_t)blockIdx.x * 4 + threadIdx.x] = tot;
+}
+
 // Mean and standard error over nvec vectors of each moment: pv[r * M + n].
 __global__ void moment_stats_kernel(const double* __restrict__ pv, int nvec, int M, double* mean,
                                     double* err) {
@@ -1052,6 +1089,12 @@ cudaError_t launch_green(const double* mu, int M, double a, double b, int K, int
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   green_kernel<<<blocks_for(32LL * K, 256), 256, 0, st>>>(coef, M, a, b, K, table, E, g_re, g_im);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_thermo(const double* E, const double* rho, int K, double a,
+                          const double* beta, int nT, double mu_c, double* out, cudaStream_t st) {
+  thermo_kernel<<<nT, LZ_BLOCK, 0, st>>>(E, rho, K, a, beta, mu_c, out);
   return counted(cudaGetLastError());
 }
 

@@ -83,6 +83,9 @@ cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, int m
                                   cudaStream_t st);
 cudaError_t launch_dos(const double* mu, int M, double a, double b, int K, int kernel,
                        double lambda, double* E, double* rho, double* work, cudaStream_t st);
+// Fermi-occupation integrals (n, u, s, c per site) of a DOS on the K nodes
+cudaError_t launch_thermo(const double* E, const double* rho, int K, double a,
+                          const double* beta, int nT, double mu_c, double* out, cudaStream_t st);
 // local Green's function on the K nodes (work holds M + 4K doubles)
 cudaError_t launch_green(const double* mu, int M, double a, double b, int K, int kernel,
                          double lambda, double* E, double* g_re, double* g_im, double* work,

@@ -79,6 +79,9 @@ def lib() -> C.CDLL:
                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
         L.kpm_green.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                                 C.c_double] + [C.c_void_p] * 4
+        L.kpm_thermo.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                                 C.c_double, C.c_void_p, C.c_int, C.c_double, C.c_void_p,
+                                 C.c_void_p]
         L.kpm_stats.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                 C.c_int, C.c_double] + [C.c_void_p] * 6
         L.kpm_moments_adaptive.argtypes = [h, C.POINTER(kpm_params), C.c_int, C.c_int, C.c_double,
@@ -325,6 +328,19 @@ def kpm_green(mu, a, b, K, kernel="lorentz", lam=4.0, stream=None):
     _check(lib().kpm_green(_ptr(mu), M, float(a), float(b), int(K), KERNELS[kernel],
                            float(lam or 0.0), _ptr(E), _ptr(gr), _ptr(gi), _stream(stream)))
     return E, gr + 1j * gi
+
+
+def kpm_thermo(mu, a, b, K, betas, mu_c=0.0, kernel="jackson", lam=None, stream=None):
+    """Fermi-occupation integrals of the DOS per inverse temperature: returns an
+    [nT, 4] array of (n, u, s, c) per site (beta = inf: the ground state)."""
+    if not hasattr(mu, "data_ptr"):
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+    betas = np.ascontiguousarray(np.atleast_1d(betas), dtype=np.float64)
+    out = np.zeros((betas.size, 4))
+    _check(lib().kpm_thermo(_ptr(mu), int(mu.shape[0]), float(a), float(b), int(K),
+                            KERNELS[kernel], float(lam or 0.0), _ptr(betas), betas.size,
+                            float(mu_c), _ptr(out), _stream(stream)))
+    return out
 
 
 def kpm_stats(pv, a, b, K, kernel="jackson", lam=None, stream=None):

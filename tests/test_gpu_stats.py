@@ -122,3 +122,13 @@ def test_green_matches_oracle(K, kernel):
     np.testing.assert_allclose(E, E_o, rtol=0, atol=1e-14)
     np.testing.assert_allclose(G.real, G_o.real, rtol=0, atol=tol)
     np.testing.assert_allclose(G.imag, G_o.imag, rtol=0, atol=tol)
+
+
+def test_thermo_matches_oracle(K):
+    rng = np.random.default_rng(21)
+    mu = rng.uniform(-1, 1, 200) * np.exp(-np.arange(200) / 40.0)
+    mu[0] = 1.0
+    betas = np.array([0.0, 0.5, 3.0, 40.0, np.inf])
+    got = K.kpm_thermo(mu, 2.4, 0.2, 300, betas, mu_c=0.35)
+    ref = O.thermo(mu, 2.4, 0.2, 300, betas, 0.35)
+    np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-12)

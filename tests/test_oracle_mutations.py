@@ -31,6 +31,7 @@ MUTATIONS = {
     "jackson_off_by_one": ("((M - n + 1) * np.cos", "((M - n) * np.cos"),
     "dos_missing_two": ("s += 2.0 * g[n] * mu[n] * math.cos", "s += g[n] * mu[n] * math.cos"),
     "green_wrong_sign": ("-math.sin(n * th[k])", "math.sin(n * th[k])"),
+    "thermo_missing_scale": ("w = a * math.pi * np.sin(", "w = math.pi * np.sin("),
     "dos_missing_jacobian": ("return a * x + b, f / a", "return a * x + b, f"),
     "dos_wrong_node": ("(np.arange(K) + 0.5) / K\n    x = np.cos(phase)",
                        "(np.arange(K) + 1.0) / K\n    x = np.cos(phase)"),
@@ -126,6 +127,11 @@ def checks(O):
                                   math.exp(-lam) * G(np.exp(1j * phi) / r)) / (2 * math.sinh(lam))).imag
         Sk = 0.5 * (sines(th + t0) + sines(th - t0))
         check("green", np.allclose(Gf.real, -Sk / np.sin(th), atol=1e-9))
+        # finite temperature: at beta = 0 every state is half filled and s = ln 2
+        mu0 = np.zeros(8)
+        mu0[0] = 1.0
+        hot = O.thermo(mu0, 2.0, 0.0, 256, [0.0], 0.3, "none")[0]
+        check("thermo", abs(hot[0] - 0.5) < 1e-12 and abs(hot[2] - math.log(2)) < 1e-12)
     except Exception as e:  # a mutant that crashes is caught too
         fails.append("exception:" + type(e).__name__)
     return fails

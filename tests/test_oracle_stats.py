@@ -158,3 +158,31 @@ def test_green_imaginary_part_is_minus_pi_rho():
         E2, rho = O.dos(mu, 2.2, 0.4, 37, kernel, 3.0)
         np.testing.assert_allclose(G.imag, -math.pi * rho, rtol=1e-13, atol=1e-13)
         np.testing.assert_allclose(E, E2, rtol=0, atol=1e-15)
+
+
+def test_thermo_closed_forms():
+    # clean chain with the band [-2, 2] exactly (a = 2): the DOS is the arcsine law,
+    # whose only nonzero moment is mu_0; at T = 0 and mu_c = 0, n = 1/2 and
+    # u = -2/pi; at beta = 0 every state is half filled: n = 1/2, s = ln 2, c = 0
+    mu = np.zeros(64)
+    mu[0] = 1.0
+    K = 4096
+    t0 = O.thermo(mu, 2.0, 0.0, K, [np.inf], 0.0, "none")[0]
+    assert t0[0] == pytest.approx(0.5, abs=1.0 / K) and t0[1] == pytest.approx(-2 / math.pi, abs=2.0 / K)
+    assert t0[2] == 0.0 and t0[3] == 0.0
+    hot = O.thermo(mu, 2.0, 0.0, K, [0.0], 0.3, "none")[0]
+    assert hot[0] == pytest.approx(0.5, abs=1e-12) and hot[2] == pytest.approx(math.log(2), abs=1e-12)
+    assert hot[3] == 0.0
+
+
+def test_thermo_identities():
+    # c = -beta^2 d(u - mu_c n)/dbeta and ds/dbeta = -c/beta (at fixed mu_c), by
+    # central differences on a disordered lattice's moments
+    H = O.lattice_hamiltonian((10, 10), onsite=np.random.default_rng(6).uniform(-1, 1, 100))
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    mu = O.exact_moments(H, a, b, 128)
+    mu_c, beta, h = 0.3, 2.5, 1e-4
+    r = O.thermo(mu, a, b, 2048, [beta - h, beta, beta + h], mu_c)
+    g = r[:, 1] - mu_c * r[:, 0]
+    assert -beta ** 2 * (g[2] - g[0]) / (2 * h) == pytest.approx(r[1, 3], rel=1e-6)
+    assert (r[2, 2] - r[0, 2]) / (2 * h) == pytest.approx(-r[1, 3] / beta, rel=1e-6)
