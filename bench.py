@@ -248,7 +248,9 @@ def csr_handle(K, w):
 
 def profile_run(prec, workload, batch_chunk=2):
     """Two solves of the workload with Gershgorin bounds (no Lanczos products, so
-    the only fused-step launches are those of the two solves)."""
+    the only fused-step launches are those of the two solves); prec "bounds":
+    three spectral-bound estimates of the headline lattice (Gershgorin and the
+    30-step FP64 Lanczos), for captures of the bound kernels."""
     import torch
 
     from paper_1105_5481_gb300 import build as B
@@ -256,6 +258,17 @@ def profile_run(prec, workload, batch_chunk=2):
     from paper_1105_5481_gb300 import kpm as K
 
     B.build()
+    if prec == "bounds":
+        w = I.workload("cubic_spin_L64")
+        h = K.kpm_create_stencil(3, w["L"], hop=w["hop"], complex_=True)
+        t = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            r = K.kpm_bounds(h, WORKLOAD["lanczos_steps"], WORKLOAD["pad_eps"], seed=6)
+            t.append(1e3 * (time.perf_counter() - t0))
+        h.close()
+        print(json.dumps({"profile": "bounds", "ms_per_call": t, "emin": r[0], "emax": r[1]}))
+        return 0
     if workload == "batch_2d_256":
         insts = I.batch_workload(3, 256)
         hs = [K.kpm_create_stencil(2, x["L"], onsite=x["onsite"]) for x in insts]
@@ -596,7 +609,7 @@ def main():
                              "serve_poisson", "square_L32_fp64"],
                     help="cubic_spin_L64 (default, the headline) or the large diluted CSR "
                          "lattice (L=160, N=4.1M, R=32, M=4096, FP32 vectors)")
-    ap.add_argument("--profile", default=None, choices=["fp32", "fp64"],
+    ap.add_argument("--profile", default=None, choices=["fp32", "fp64", "bounds"],
                     help="run two solves of the workload at the given precision and exit "
                          "(a short command for ncu captures of the fused step)")
     args = ap.parse_args()
