@@ -12,6 +12,8 @@ Processing Units", arXiv:1105.5481), Sec. II-A, and, where the paper only
 names a piece, the KPM review it cites (Weisse, Wellein, Alvermann, Fehske,
 Rev. Mod. Phys. 78, 275 (2006)):
 
+  from_dense             the paper's dense formulation: all n*n elements of H
+                         stored (Sec. II-A-4 without CRS)                      [pinned]
   exact_moments          Eq. (DoStr): mu_n = (1/D) Tr T_n(H~), via eigh      [pinned]
   moments_direct         Eqs. (rn), (munr): r_{n+2} = 2 H~ r_{n+1} - r_n,
                          mu_n = <<(1/DR) sum_r <r_0|r_n>>>                     [pinned]
@@ -49,7 +51,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "CSR", "lattice_hamiltonian", "dense", "gershgorin", "lanczos_bounds", "rescale",
+    "CSR", "lattice_hamiltonian", "dense", "from_dense", "gershgorin", "lanczos_bounds", "rescale",
     "moments_direct", "moments_doubling", "exact_moments", "jackson_kernel", "dos",
     "lorentz_kernel", "damping", "dos_many", "stats", "dos_error_integral", "ldos_exact",
     "green", "thermo",
@@ -154,6 +156,17 @@ def dense(H: CSR) -> np.ndarray:
     A = np.zeros((H.n, H.n), dtype=H.val.dtype)
     A[H._row, H.col] += H.val
     return A
+
+
+def from_dense(A) -> CSR:
+    """The paper's dense formulation (Sec. II-A-4, CRS not applied): every one
+    of the n*n elements of H, zeros included, is stored and takes part in
+    every product."""
+    A = np.asarray(A)
+    n = A.shape[0]
+    rowptr = np.arange(n + 1, dtype=np.int64) * n
+    col = np.tile(np.arange(n, dtype=np.int64), n)
+    return CSR(n, rowptr, col, A.reshape(-1).copy())
 
 
 def green(mu, a: float, b: float, K: int, kernel: str = "lorentz", lam: float = 4.0):

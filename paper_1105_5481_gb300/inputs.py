@@ -14,7 +14,8 @@ side can regenerate the same numbers independently:
 
 (SplitMix64 as published by Steele, Lea and Flood, OOPSLA 2014.)  Streams:
 0 random vectors, 1 on-site energies, 2 spin polar angle, 3 spin azimuth,
-4 bond dilution, 5 batch instance shapes, 6 Lanczos start vector.
+4 bond dilution, 5 batch instance shapes, 6 Lanczos start vector, 7 dense
+matrix entries.
 
 Random vectors follow the paper's stochastic trace (Sec. II-A-3): entries
 xi_{r,i} with zero mean and unit variance.  Real vectors are Rademacher +-1
@@ -43,6 +44,7 @@ STREAM_PHI = 3
 STREAM_DILUTION = 4
 STREAM_SHAPES = 5
 STREAM_LANCZOS = 6
+STREAM_DENSE = 7
 
 
 def splitmix64(z):
@@ -110,6 +112,29 @@ def lanczos_start(seed: int, N: int) -> np.ndarray:
 def onsite_disorder(seed: int, N: int, W: float) -> np.ndarray:
     """On-site energies eps_i uniform in [-W/2, W/2)."""
     return W * (uniform(seed, STREAM_ONSITE, np.arange(N, dtype=np.uint64)) - 0.5)
+
+
+def dense_hermitian(seed: int, n: int, complex_: bool = False) -> np.ndarray:
+    """A dense n x n Hermitian matrix with independent entries on and above the
+    diagonal (a Wigner matrix), for the paper's dense formulation: H_ij =
+    (2u - 1)/sqrt(n) for i <= j (stream 7, counter i*n + j), plus i (2u' - 1)/sqrt(n)
+    with u' at counter n*n + i*n + j off the diagonal when complex;
+    H_ji = conj(H_ij)."""
+    iu, ju = np.triu_indices(n)
+    cnt = (iu.astype(np.uint64) * np.uint64(n) + ju.astype(np.uint64))
+    scale = 1.0 / np.sqrt(n)
+    re = (2.0 * uniform(seed, STREAM_DENSE, cnt) - 1.0) * scale
+    if complex_:
+        im = (2.0 * uniform(seed, STREAM_DENSE, cnt + np.uint64(n * n)) - 1.0) * scale
+        im[iu == ju] = 0.0
+        H = np.zeros((n, n), dtype=np.complex128)
+        H[iu, ju] = re + 1j * im
+        H[ju, iu] = re - 1j * im
+    else:
+        H = np.zeros((n, n))
+        H[iu, ju] = re
+        H[ju, iu] = re
+    return H
 
 
 def lattice_sites(L) -> int:
@@ -278,4 +303,12 @@ def workload(name: str, seed: int | None = None) -> dict:
         return dict(dims=3, L=L, periodic=(True, True, True), onsite=None,
                     hop=spin_hoppings(L, th, ph), t=1.0, complex=True, mask=None,
                     R=64, M=1024, seed=seed, K=1024)
+    if name.startswith("dense_wigner_D"):
+        # the paper's dense formulation at its largest matrix (Sec. IV-C: H_SIZE
+        # up to 4096, N = 128 moments, R x S = 14 x 128 = 1792 random vectors):
+        # a real Wigner matrix, FP64, all 1792 vectors in one block
+        D = int(name[len("dense_wigner_D"):])
+        seed = 8 if seed is None else seed
+        return dict(D=D, H=dense_hermitian(seed, D), complex=False, R=1792, M=128, seed=seed,
+                    K=1024)
     raise KeyError(name)

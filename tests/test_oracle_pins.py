@@ -251,3 +251,36 @@ def test_dos_integrates_to_one_and_is_nonnegative():
     integral = np.sum(np.pi / K * np.sqrt(1 - x * x) * rho * a)
     assert abs(integral - 1.0) < 1e-13
     assert rho.min() > -1e-12                                   # Jackson kernel keeps rho >= 0
+
+
+# ---------------------------------------------------------------- dense formulation
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_dense_formulation_stores_every_element(complex_):
+    A = I.dense_hermitian(4, 37, complex_)
+    A[3, 5] = A[5, 3] = 0.0                         # a zero stays a stored element
+    H = O.from_dense(A)
+    assert H.nnz == 37 * 37
+    np.testing.assert_array_equal(O.dense(H), A)
+    X = I.random_block(2, 37, 5, complex_)
+    np.testing.assert_allclose(H.matvec(X), A @ X, rtol=1e-13, atol=1e-14)
+    offdiag = np.abs(A).sum(axis=1) - np.abs(np.diag(A))
+    gmin, gmax = O.gershgorin(H)
+    assert abs(gmin - np.min(np.diag(A).real - offdiag)) < 1e-13
+    assert abs(gmax - np.max(np.diag(A).real + offdiag)) < 1e-13
+
+
+def test_dense_wigner_moments_follow_the_semicircle():
+    # Wigner's semicircle law: entries of variance s^2 = 1/(3n) give a spectrum
+    # on [-2/sqrt(3), 2/sqrt(3)] with density (2/pi) sqrt(1 - x^2) in units of
+    # the radius, whose Chebyshev moments are 1, 0, -1/2, 0, 0, ...; at n = 400
+    # the finite-size deviations are O(1/n) in mu_2 and mu_4.
+    n = 400
+    A = I.dense_hermitian(9, n)
+    a = 2.0 / math.sqrt(3.0)
+    mu = O.exact_moments(O.from_dense(A), a, 0.0, 8)
+    assert abs(mu[0] - 1.0) < 1e-14
+    assert abs(mu[2] + 0.5) < 0.02 and abs(mu[4]) < 0.03 and abs(mu[6]) < 0.03
+    assert abs(mu[1]) < 0.01 and abs(mu[3]) < 0.01
+    # mu_2 exactly: 2 ||H~||_F^2 / n - 1
+    assert abs(mu[2] - (2.0 * np.linalg.norm(A / a, "fro") ** 2 / n - 1.0)) < 1e-12
