@@ -414,6 +414,110 @@ def csr_leg(args):
     return 0
 
 
+def dense_leg(args):
+    """The paper's dense formulation at its largest matrix (Sec. IV-C: H_SIZE =
+    4096, N = 128 moments, R x S = 1792 vectors), FP64 as in the paper: a real
+    Wigner matrix, all 1792 vectors in one block, one solve per step."""
+    import torch
+
+    from paper_1105_5481_gb300 import build as B
+    from paper_1105_5481_gb300 import inputs as I
+    from paper_1105_5481_gb300 import kpm as K
+
+    B.build()
+    w = I.workload(args.workload)
+    A, D, R, M, Kn = w["H"], w["D"], w["R"], w["M"], w["K"]
+    h = K.kpm_create_dense(A)
+    nnz = K.kpm_info(h)["nnz"]
+    emin, emax, a, b = K.kpm_bounds(h, WORKLOAD["lanczos_steps"], WORKLOAD["pad_eps"], seed=6)
+    stream = torch.cuda.Stream()
+    mu_d = torch.empty(M, dtype=torch.float64, device="cuda")
+    E_d = torch.empty(Kn, dtype=torch.float64, device="cuda")
+    rho_d = torch.empty(Kn, dtype=torch.float64, device="cuda")
+    mu_chk = K.kpm_moments(h, M, R, a, b, seed=1, stream=stream)
+    assert abs(mu_chk[0] - 1.0) < 1e-12 and np.all(np.abs(mu_chk) <= 1 + 1e-9)
+    steps = max(1, min(args.steps, 3))
+    warm = 3
+    for i in range(warm):
+        K.kpm_moments(h, M, R, a, b, seed=10 + i, out=mu_d, stream=stream)
+    stream.synchronize()
+    l0 = K.kpm_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record(stream)
+        for i in range(steps):
+            K.kpm_moments(h, M, R, a, b, seed=100 + i, out=mu_d, stream=stream)
+            K.kpm_dos(mu_d, a, b, Kn, "jackson", E=E_d, rho=rho_d, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = K.kpm_kernel_launches() - l0
+    chain_ms, nsteps = K.kpm_step_timing(h)
+    h.close()
+    # the contraction dominates: 2 D^2 FP64 FMA-flops per vector and product
+    flops_step = 2.0 * D * D * R
+    ach = flops_step / (chain_ms / nsteps / 1e3) / 1e12
+    value = nnz * R * M / (ms / 1e3)
+
+    # end to end through the public API: pinned host matrix -> handle -> bounds ->
+    # moments -> DOS -> host results
+    A_pin = torch.from_numpy(A).pin_memory().numpy()
+
+    def e2e_once(i):
+        with K.kpm_create_dense(A_pin) as he:
+            _, _, ae, be = K.kpm_bounds(he, WORKLOAD["lanczos_steps"], WORKLOAD["pad_eps"], seed=6)
+            mu = K.kpm_moments(he, M, R, ae, be, seed=200 + i, stream=stream)
+            K.kpm_dos(mu, ae, be, Kn, stream=stream)
+
+    e2e_once(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(2):
+        e2e_once(i + 1)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / 2
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle as O
+        from oracle import kpm_cpu as OC
+
+        H = O.from_dense(A)
+        R_s, M_s = 448, 64
+        v0 = I.rademacher_block(1, D, R_s)
+        nthreads = OC.max_threads()
+        t0 = time.perf_counter()
+        OC.moments_doubling(H, a, b, v0, M_s, threads=nthreads)
+        dt = time.perf_counter() - t0
+        cpu = {"value": nnz * R_s * M_s / dt, "unit": UNIT, "cores": nthreads,
+               "kind": "oracle (C, OpenMP)",
+               "sample": f"the oracle's doubling form in C over all {D * D} stored elements, "
+                         f"{R_s} of the {R} vectors, M={M_s} ({dt:.1f} s)"}
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "per_matvec": per_matvec(value),
+        "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload,
+                   "matrix": f"dense real Wigner matrix D={D} (entries U[-1,1)/sqrt(D)), every "
+                             "element stored and used (the paper's formulation)",
+                   "N": D, "nnz": nnz, "R": R, "M": M, "K": Kn,
+                   "bounds": {"emin": emin, "emax": emax, "a": a, "b": b},
+                   "step": "random block + M/2 dense products + moment reduction + Jackson DOS",
+                   "l2": "matrix (134 MB) larger than L2"},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "dense_step_kernel<real, STEP, 64-row tiles>",
+                     "flops_per_launch": flops_step, "launch_ms": chain_ms / nsteps,
+                     "peak_kind": "FP64 pipe, 2 FMA per SM and clock at 1.97 GHz (measured)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": nnz * R * M / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(A.nbytes), "d2h_bytes_per_step": int(8 * (M + 2 * Kn)),
+                "includes": "create from a pinned host matrix, bounds, moments, DOS, destroy"},
+        "gpu_launches": launches, "clocks": clk.summary()}))
+    return 0
+
+
 def batch_leg(args):
     """256 independent 2D disorder realisations of uneven size, R=16 FP32 real
     vectors, one persistent cluster launch per batch (graph replay, autotuned),
@@ -606,7 +710,7 @@ def main():
                     help="--profile with the batch workload: passes per chunk (clusters of 4)")
     ap.add_argument("--workload", default="cubic_spin_L64",
                     choices=["cubic_spin_L64", "csr_spin_dilute_L160", "batch_2d_256",
-                             "serve_poisson", "square_L32_fp64"],
+                             "serve_poisson", "square_L32_fp64", "dense_wigner_D4096"],
                     help="cubic_spin_L64 (default, the headline) or the large diluted CSR "
                          "lattice (L=160, N=4.1M, R=32, M=4096, FP32 vectors)")
     ap.add_argument("--profile", default=None, choices=["fp32", "fp64", "bounds"],
@@ -623,6 +727,8 @@ def main():
         return csr_leg(args)
     if args.workload == "batch_2d_256":
         return batch_leg(args)
+    if args.workload.startswith("dense_wigner_D"):
+        return dense_leg(args)
     if args.workload == "serve_poisson":
         return serve_leg(args)
 

@@ -109,6 +109,18 @@ kpm_status kpm_create_stencil(const kpm_stencil_desc* desc, kpm_field field, kpm
 kpm_status kpm_create_csr(int64_t n, const int64_t* rowptr, const int32_t* col,
                           const double* val, kpm_field field, kpm_handle* out);
 
+/* Builds a dense Hamiltonian: the paper's own formulation (Sec. II-A-4 with
+ * CRS not applied, Sec. III), in which every element of H~ takes part in
+ * every product.  H is a host array of n*n FP64 values, row-major (real
+ * field) or n*n (re, im) pairs (complex field), copied to the device; it must
+ * be Hermitian to rounding (|H_ij - conj(H_ji)| <= 1e-12 max|H|).  Dense
+ * handles compute in FP64 (kpm_moments with KPM_FP64; KPM_FP32_VEC_FP64_MOM
+ * returns KPM_EINVAL) and work with kpm_bounds, kpm_moments and the calls
+ * built on them, not with the batch or the server.  kpm_info reports
+ * nnz = n*n and is_stencil = 0.  Returns KPM_EINVAL for n outside
+ * [1, 65536], a NULL H, a non-finite entry or a non-Hermitian H. */
+kpm_status kpm_create_dense(int64_t n, const double* H, kpm_field field, kpm_handle* out);
+
 /* Converts a stencil description into CSR arrays on the host (library-side
  * builder; rows sorted by column, duplicates summed, zero-valued bonds from the
  * mask dropped, diagonal stored only where onsite != NULL).  Call once with
@@ -152,7 +164,9 @@ typedef struct {
  * matrix product (v_{n+1} = 2 H~ v_n - v_{n-1} plus the two moment dots),
  * replayed from a captured CUDA graph.  Returns KPM_EDIVERGE (after writing
  * the outputs) when host outputs show |mu_n^r| > 1 + 1e-6 or a non-finite
- * value. */
+ * value, and KPM_EINVAL when R exceeds one block of vectors (more than 1024
+ * chunks of 16 bytes (FP64) or 32 bytes (FP32) per row, after rounding the
+ * chunk count up to a power of two; dense handles have no such limit). */
 kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu_per_vec,
                        void* stream);
 

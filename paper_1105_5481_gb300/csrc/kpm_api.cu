@@ -172,6 +172,13 @@ cudaError_t launch_step(bool stencil, bool fp32, bool cplx, StepMode mode, const
               : launch_step_f64(stencil, cplx, mode, a, cfg, st);
 }
 
+// One product of the handle's operator (stencil, CSR / ELL, or dense FP64).
+cudaError_t launch_op(const kpm_handle_s* h, bool fp32, StepMode mode, const StepArgs& a,
+                      const LaunchCfg& cfg, cudaStream_t st) {
+  if (h->dense) return fp32 ? cudaErrorInvalidValue : launch_dense_step(h->cplx, mode, a, cfg, st);
+  return launch_step(h->stencil, fp32, h->cplx, mode, a, cfg, st);
+}
+
 // Traversal and grid of the fused step (see StepArgs).  Stencils with enough
 // lattice lines are walked in line blocks so that the rows of one pass are
 // each other's y-neighbours; CSR matrices and small or 1D lattices use the
@@ -182,6 +189,17 @@ cudaError_t launch_step(bool stencil, bool fp32, bool cplx, StepMode mode, const
 #endif
 
 void plan_grid(const kpm_handle_s* h, bool fp32, StepArgs& a, int* block, int* grid) {
+  if (h->dense) {
+    // one CTA per tile of rows (and of columns, in the launch's y dimension)
+    const int bm = dense_row_tile(h->n, a.Rp, h->cplx, h->num_sms);
+    a.line_len = 0;
+    a.lines = 0;
+    a.passes = (h->n + bm - 1) / bm;
+    a.chunk = 1;
+    *block = BLOCK;
+    *grid = (int)a.passes;
+    return;
+  }
   const int G = a.Gt;            // chunks per row handled by one CTA (<= BLOCK)
   const int blk = BLOCK;
   const int spi = blk / G;
@@ -556,6 +574,46 @@ kpm_status kpm_create_csr(int64_t n, const int64_t* rowptr, const int32_t* col, 
   return KPM_OK;
 }
 
+kpm_status kpm_create_dense(int64_t n, const double* H, kpm_field field, kpm_handle* out) {
+  if (!out) return fail(KPM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > 65536) return fail(KPM_EINVAL, "n must be in [1, 65536]");
+  if (!H) return fail(KPM_EINVAL, "H is NULL");
+  if (field != KPM_REAL && field != KPM_COMPLEX) return fail(KPM_EINVAL, "bad field");
+  const int c = field == KPM_COMPLEX ? 2 : 1;
+  // Hermitian to rounding: |H_ij - conj(H_ji)| <= 1e-12 max|H|
+  double hmax = 0.0;
+  for (int64_t q = 0; q < n * n * c; ++q) {
+    if (!isfinite(H[q])) return fail(KPM_EINVAL, "H has a non-finite entry");
+    hmax = std::max(hmax, fabs(H[q]));
+  }
+  const double tol = 1e-12 * hmax;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = i; j < n; ++j) {
+      const double* u = H + (i * n + j) * c;
+      const double* v = H + (j * n + i) * c;
+      const double dre = u[0] - v[0], dim = c == 2 ? u[1] + v[1] : 0.0;
+      if (fabs(dre) > tol || fabs(dim) > tol)
+        return fail(KPM_EINVAL, "H is not Hermitian");
+    }
+  auto* h = new kpm_handle_s();
+  h->stencil = false;
+  h->dense = true;
+  h->cplx = field == KPM_COMPLEX;
+  h->n = n;
+  h->nnz = n * n;
+  kpm_status st = common_init(h);
+  if (st != KPM_OK) { destroy_handle(h); return st; }
+  if ((st = dalloc(&h->d_val, (size_t)n * n * c)) != KPM_OK) {
+    destroy_handle(h);
+    return st;
+  }
+  cudaError_t e = cudaMemcpy(h->d_val, H, (size_t)n * n * c * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { destroy_handle(h); return cuda_fail(e, "copy dense H"); }
+  *out = h;
+  return KPM_OK;
+}
+
 kpm_status kpm_stencil_to_csr(const kpm_stencil_desc* d, kpm_field field, int64_t* nnz_out,
                               int64_t* rowptr, int32_t* col, double* val) {
   int64_t n = 0;
@@ -643,6 +701,8 @@ kpm_status kpm_bounds(kpm_handle h, int lanczos_steps, double pad_eps, uint64_t 
   if (h->stencil)
     KPM_TRY(launch_gershgorin_stencil(h->cplx, h->n, h->geom, h->d_onsite, h->d_hop, h->t_re,
                                       h->t_im, pmin, pmax, nblk, st));
+  else if (h->dense)
+    KPM_TRY(launch_gershgorin_dense(h->cplx, h->n, h->d_val, pmin, pmax, nblk, st));
   else
     KPM_TRY(launch_gershgorin_csr(h->cplx, h->n, h->d_rowptr, h->d_col, h->d_val, pmin, pmax,
                                   nblk, st));
@@ -672,7 +732,7 @@ kpm_status kpm_bounds(kpm_handle h, int lanczos_steps, double pad_eps, uint64_t 
       sa.y = y;
       sa.w = nullptr;
       sa.partial = nullptr;
-      KPM_TRY(launch_step(h->stencil, false, h->cplx, MODE_SPMV, sa, LaunchCfg{block, grid}, st));
+      KPM_TRY(launch_op(h, false, MODE_SPMV, sa, LaunchCfg{block, grid}, st));
       // three-term step against q_j, q_{j-1}, then one full Gram-Schmidt pass
       KPM_TRY(launch_lz_local_dots(h->cplx, h->n, Q, len, j, y, part_loc, nblk, st));
       KPM_TRY(launch_lz_reorth_dots(h->cplx, h->n, Q, len, j, part_loc, y, part, alpha, nblk, st));
@@ -706,6 +766,8 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
   if (p->precision != KPM_FP64 && p->precision != KPM_FP32_VEC_FP64_MOM)
     return fail(KPM_EINVAL, "bad precision");
   if (p->user_v0 && S != 1) return fail(KPM_EINVAL, "user_v0 requires S == 1");
+  if (h->dense && p->precision != KPM_FP64)
+    return fail(KPM_EINVAL, "dense handles compute in FP64 (the paper's formulation)");
   if (!mu && !mu_per_vec) return fail(KPM_EINVAL, "no output requested");
   if ((int64_t)S * R * (int64_t)M > ((int64_t)1 << 40)) return fail(KPM_EINVAL, "S*R*M too large");
   KPM_CUDA(cudaSetDevice(h->device));
@@ -713,7 +775,14 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
   const bool fp32 = p->precision == KPM_FP32_VEC_FP64_MOM;
   int Rp, G;
   padded_width(R, fp32, h->cplx, &Rp, &G);
-  if (G > 1024) return fail(KPM_EINVAL, "R too large for one block of vectors");
+  if (h->dense) {
+    // the dense step tiles columns itself: pad only to whole 16-byte chunks
+    const int vec = vec_per_chunk(fp32, h->cplx);
+    G = (R + vec - 1) / vec;
+    Rp = G * vec;
+  } else if (G > 1024) {
+    return fail(KPM_EINVAL, "R too large for one block of vectors");
+  }
   const int slot = fp32 ? 1 : 0;
   const bool user_v0 = p->user_v0 != nullptr;
   const int steps = M / 2;
@@ -748,7 +817,7 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
       a.w = nullptr;
       a.partial = w.ring;
       a.reverse = 1;  // step n sweeps backwards for even n (see StepArgs)
-      e = launch_step(h->stencil, fp32, h->cplx, MODE_FIRST, a, cfg, cs);
+      e = launch_op(h, fp32, MODE_FIRST, a, cfg, cs);
     }
     if (e == cudaSuccess && steps == 1)
       e = launch_reduce_ring(w.ring, RING, 0, 1, grid, Rp, h->d_prm, steps, w.sums, cs);
@@ -758,7 +827,7 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
       a.w = w.v[(n + 1) & 1];
       a.partial = w.ring + (size_t)(n % RING) * grid * 2 * Rp;
       a.reverse = (n & 1) ^ 1;
-      e = launch_step(h->stencil, fp32, h->cplx, MODE_STEP, a, cfg, cs);
+      e = launch_op(h, fp32, MODE_STEP, a, cfg, cs);
       if (e != cudaSuccess) break;
       if ((n + 1) % RING == 0)
         e = launch_reduce_ring(w.ring, RING, n + 1 - RING, RING, grid, Rp, h->d_prm, steps,

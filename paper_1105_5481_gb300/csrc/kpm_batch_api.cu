@@ -202,6 +202,7 @@ kpm_status kpm_batch_create(int count, const kpm_handle* handles, const kpm_para
     const kpm_handle_s* h = handles[i];
     const kpm_params& p = params[i];
     if (!h) return fail(KPM_EINVAL, "NULL handle");
+    if (h->dense) return fail(KPM_EINVAL, "dense handles are not batched (use kpm_moments)");
     if (h->device != h0->device || h->cplx != h0->cplx || h->stencil != h0->stencil ||
         h->geom.dims != h0->geom.dims || h->has_hop != h0->has_hop ||
         h->has_onsite != h0->has_onsite || h->ell_w != h0->ell_w)

@@ -36,6 +36,14 @@ cudaError_t launch_step_f64(bool stencil, bool cplx, StepMode mode, const StepAr
 int occ_step_f32(bool stencil, bool cplx, const StepArgs& a, int block);
 int occ_step_f64(bool stencil, bool cplx, const StepArgs& a, int block);
 
+// dense operators (kpm_dense.cu): FP64 only
+cudaError_t launch_dense_step(bool cplx, StepMode mode, const StepArgs& a, const LaunchCfg& cfg,
+                              cudaStream_t st);
+cudaError_t launch_gershgorin_dense(bool cplx, int64_t n, const double* H, double* part_min,
+                                    double* part_max, int nblk, cudaStream_t st);
+// rows per CTA of the dense step (64, or 16 when 64-row tiles would leave SMs idle)
+int dense_row_tile(int64_t n, int Rp, bool cplx, int num_sms);
+
 // auxiliary kernels (kpm_aux.cu)
 cudaError_t launch_prescale_stencil(bool fp32, bool cplx, int64_t n, int dims, const double* onsite,
                                     const double* hop, double t_re, double t_im,
@@ -131,6 +139,7 @@ struct kpm_handle_s {
   int device = 0;
   bool cplx = false;
   bool stencil = false;
+  bool dense = false;  // dense n x n matrix in d_val (nnz = n*n), no rowptr / col
   int64_t n = 0;
   int64_t nnz = 0;
   // stencil

@@ -605,6 +605,7 @@ kpm_status kpm_server_submit(kpm_server s, kpm_handle h, const kpm_params* p, in
   if (!(p->a > 0.0) || !isfinite(p->a) || !isfinite(p->b)) return fail(KPM_EINVAL, "bad a or b");
   if (K < 0 || K > (1 << 20)) return fail(KPM_EINVAL, "bad K");
   if (h->device != s->device) return fail(KPM_EINVAL, "handle on another device");
+  if (h->dense) return fail(KPM_EINVAL, "dense handles are not served (use kpm_moments)");
   auto* r = new Req();
   r->h = h;
   r->p = *p;

@@ -69,6 +69,7 @@ def lib() -> C.CDLL:
         h = C.c_void_p
         L.kpm_create_stencil.argtypes = [C.POINTER(kpm_stencil_desc), C.c_int, C.POINTER(h)]
         L.kpm_create_csr.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(h)]
+        L.kpm_create_dense.argtypes = [C.c_int64, C.c_void_p, C.c_int, C.POINTER(h)]
         L.kpm_stencil_to_csr.argtypes = [C.POINTER(kpm_stencil_desc), C.c_int, C.POINTER(C.c_int64),
                                          C.c_void_p, C.c_void_p, C.c_void_p]
         L.kpm_bounds.argtypes = [h, C.c_int, C.c_double, C.c_uint64] + [C.POINTER(C.c_double)] * 4 + [C.c_void_p]
@@ -114,7 +115,8 @@ def lib() -> C.CDLL:
         L.kpm_destroy.restype = None
         L.kpm_last_error.restype = C.c_char_p
         L.kpm_kernel_launches.restype = C.c_uint64
-        for name in ("kpm_create_stencil", "kpm_create_csr", "kpm_stencil_to_csr", "kpm_bounds",
+        for name in ("kpm_create_stencil", "kpm_create_csr", "kpm_create_dense", "kpm_stencil_to_csr",
+                     "kpm_bounds",
                      "kpm_moments", "kpm_dos", "kpm_info", "kpm_step_timing",
                      "kpm_moments_csr_noalloc", "kpm_batch_create", "kpm_batch_run", "kpm_batch_tune",
                      "kpm_batch_set_config", "kpm_batch_info", "kpm_server_create",
@@ -233,6 +235,20 @@ def kpm_create_csr(n, rowptr, col, val, complex_=False) -> Handle:
     raw = C.c_void_p()
     _check(lib().kpm_create_csr(int(n), _ptr(rp), _ptr(cl), _ptr(vl),
                                 KPM_COMPLEX if complex_ else KPM_REAL, C.byref(raw)))
+    return Handle(raw, complex_)
+
+
+def kpm_create_dense(H) -> Handle:
+    """Dense Hermitian n x n matrix (float64 or complex128 array): the paper's
+    dense formulation, FP64 moments only."""
+    H = np.asarray(H)
+    if H.ndim != 2 or H.shape[0] != H.shape[1]:
+        raise ValueError("H must be a square matrix")
+    complex_ = bool(np.iscomplexobj(H))
+    v = _f64(H, complex_)
+    raw = C.c_void_p()
+    _check(lib().kpm_create_dense(int(H.shape[0]), _ptr(v), KPM_COMPLEX if complex_ else KPM_REAL,
+                                  C.byref(raw)))
     return Handle(raw, complex_)
 
 
