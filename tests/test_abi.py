@@ -55,6 +55,21 @@ def test_invalid_arguments_are_rejected_before_the_device(K):
     mu = np.ones(4)
     assert L.kpm_dos(mu.ctypes.data, 4, -1.0, 0.0, 8, 0, mu.ctypes.data, mu.ctypes.data, None) == K.KPM_EINVAL
     assert L.kpm_bounds(None, 10, 0.01, 0, None, None, None, None, None) == K.KPM_EINVAL
+    # dense matrices: size, NULL, non-finite and non-Hermitian input
+    A = I.dense_hermitian(3, 6)
+    assert L.kpm_create_dense(0, A.ctypes.data, K.KPM_REAL, C.byref(h)) == K.KPM_EINVAL
+    assert L.kpm_create_dense(6, None, K.KPM_REAL, C.byref(h)) == K.KPM_EINVAL
+    B = A.copy()
+    B[1, 4] += 1e-6
+    assert L.kpm_create_dense(6, B.ctypes.data, K.KPM_REAL, C.byref(h)) == K.KPM_EINVAL
+    assert "Hermitian" in K.kpm_last_error()
+    B = A.copy()
+    B[2, 2] = np.nan
+    assert L.kpm_create_dense(6, B.ctypes.data, K.KPM_REAL, C.byref(h)) == K.KPM_EINVAL
+    Z = np.ascontiguousarray(I.dense_hermitian(3, 6, True))
+    Zb = Z.copy()
+    Zb[0, 0] += 1e-3j                                  # a diagonal entry must be real
+    assert L.kpm_create_dense(6, Zb.view(np.float64).ctypes.data, K.KPM_COMPLEX, C.byref(h)) == K.KPM_EINVAL
 
 
 def _oracle_csr(L, periodic, onsite, hop, mask, t=1.0):
