@@ -106,16 +106,17 @@ struct ChunkF64 {
 #pragma unroll
     for (int k = 0; k < VEC; ++k) s.a[k] = s.b[k] = 0.0;
   }
-  // s.a_k += |x_k|^2,  s.b_k += Re(conj(y_k) x_k)
+  // s.a_k += |x_k|^2,  s.b_k += Re(conj(y_k) x_k), accumulated by FMAs only
+  // (the FP64 pipe is the step's limit: one instruction per product term)
   static __device__ __forceinline__ void acc_add(Acc& s, const ChunkF64& x, const ChunkF64& y) {
     if constexpr (CPLX) {
-      s.a[0] += fma(x.v[0], x.v[0], x.v[1] * x.v[1]);
-      s.b[0] += fma(y.v[0], x.v[0], y.v[1] * x.v[1]);
+      s.a[0] = fma(x.v[1], x.v[1], fma(x.v[0], x.v[0], s.a[0]));
+      s.b[0] = fma(y.v[1], x.v[1], fma(y.v[0], x.v[0], s.b[0]));
     } else {
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        s.a[k] += x.v[k] * x.v[k];
-        s.b[k] += y.v[k] * x.v[k];
+        s.a[k] = fma(x.v[k], x.v[k], s.a[k]);
+        s.b[k] = fma(y.v[k], x.v[k], s.b[k]);
       }
     }
   }
