@@ -284,3 +284,19 @@ def test_dense_wigner_moments_follow_the_semicircle():
     assert abs(mu[1]) < 0.01 and abs(mu[3]) < 0.01
     # mu_2 exactly: 2 ||H~||_F^2 / n - 1
     assert abs(mu[2] - (2.0 * np.linalg.norm(A / a, "fro") ** 2 / n - 1.0)) < 1e-12
+
+
+@pytest.mark.parametrize("M", [128, 256, 512])
+def test_jackson_broadens_a_level_to_width_pi_over_M(M):
+    # the Jackson-damped series of one level at x0 = 0 (mu_n = T_n(0)) is a
+    # near-Gaussian of standard deviation pi/M (the KPM review's resolution of
+    # the Jackson kernel), so doubling M halves the width (the paper's Fig. 6:
+    # more moments, finer DOS); integrated by the K-node Gauss-Chebyshev rule
+    mu = np.cos(np.arange(M) * np.pi / 2)
+    K = 4 * M
+    E, rho = O.dos(mu, 1.0, 0.0, K)
+    w = np.pi / K * np.sqrt(1.0 - E * E)
+    m0, m2 = np.sum(w * rho), np.sum(w * rho * E * E)
+    assert abs(m0 - 1.0) < 1e-12
+    sigma = math.sqrt(m2 / m0)
+    assert abs(sigma * M / math.pi - 1.0) < 3.0 / M
