@@ -1,5 +1,5 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
-same seeded inputs.  Tolerances (spec contract): |d mu_n| <= 1e-10 on
+same seeded inputs.  Tolerances: |d mu_n| <= 1e-10 on
 the FP64 path, <= 1e-5 on the FP32-vector / FP64-moment path."""
 import math
 

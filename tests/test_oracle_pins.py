@@ -141,7 +141,7 @@ def test_low_order_moments_closed_form():
 
 @pytest.mark.parametrize("H", list(_test_matrices()), ids=["spin3d", "dis2d", "mixed3d"])
 def test_full_basis_gives_exact_trace(H):
-    # north star pin: the estimator with the full basis is Tr T_n(H~)/N exactly
+    # the estimator with the full basis is Tr T_n(H~)/N exactly
     gmin, gmax = O.gershgorin(H)
     a, b = O.rescale(gmin, gmax)
     M = 96
@@ -214,7 +214,7 @@ def test_jackson_kernel_is_sine_window_autocorrelation(M):
 
 
 def test_clean_chain_dos_is_arcsine():
-    # north star pin: clean chain, t=1, M <= L: mu = (1,0,0,...), DOS = 1/(pi sqrt(4 t^2 - E^2))
+    # clean chain, t=1, M <= L: mu = (1,0,0,...), DOS = 1/(pi sqrt(4 t^2 - E^2))
     L, M, K = 300, 256, 512
     H = O.lattice_hamiltonian((L,))
     a, b = O.rescale(*O.gershgorin(H), eps=0.0)
