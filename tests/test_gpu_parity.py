@@ -222,3 +222,26 @@ def test_generic_csr_long_rows_match_oracle(K, prec):
     with K.kpm_create_csr(n, rp, col, val, complex_=True) as h:
         mu, per = K.kpm_moments(h, M, R, a, b, seed=5, precision=prec, per_vec=True)
     assert np.abs(per - per_o).max() <= TOL[prec]
+
+
+# the widest vector blocks one fused step takes (1024 chunks per row: four
+# column blocks of 256 chunks in the grid's y dimension), and one beyond
+@pytest.mark.parametrize("prec,cplx,R", [("fp64", True, 1024), ("fp32", False, 8192),
+                                         ("fp32", True, 4096)])
+def test_widest_vector_block_matches_oracle(K, prec, cplx, R):
+    L = (6, 5, 7)
+    N = 210
+    kw = dict(dims=3, L=L, onsite=I.onsite_disorder(8, N, 1.0))
+    if cplx:
+        kw["hop"] = I.spin_hoppings(L, *I.spins(8, N))
+    H = oracle_H(kw)
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    M, seed = 24, 13
+    mu_o, per_o = O.moments_doubling(H, a, b, I.random_block(seed, N, R, cplx), M)
+    with handle(K, kw, cplx) as h:
+        mu, per = K.kpm_moments(h, M, R, a, b, seed=seed, precision=prec, per_vec=True)
+        with pytest.raises(K.KPMError) as e:
+            K.kpm_moments(h, M, R + 1, a, b, seed=seed, precision=prec)
+        assert e.value.status == K.KPM_EINVAL
+    assert np.abs(per - per_o).max() <= TOL[prec]
+    assert np.abs(mu - mu_o).max() <= TOL[prec]
