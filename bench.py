@@ -58,9 +58,9 @@ BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
 # profiles/cheb_step_fp32_csr_spin_dilute_L160.md: steady state of consecutive steps,
 # caches not flushed between launches; profiles/batch_kernel_fp32_batch_2d_256.md);
 # reported only while the hash matches.
-MEASURED_TRAFFIC = {"cubic_spin_L64": (347.69e6, "step", "1ecb6378a2b8da6c"),
-                    "csr_spin_dilute_L160": (3445.43e6, "step", "1ecb6378a2b8da6c"),
-                    "batch_2d_256/C4/chunk4/clusters74": (70.23e9, "batch", "1b3375f0211c143d")}
+MEASURED_TRAFFIC = {"cubic_spin_L64": (347.67e6, "step", "3b00c719cc0d365a"),
+                    "csr_spin_dilute_L160": (3438.84e6, "step", "3b00c719cc0d365a"),
+                    "batch_2d_256/C4/chunk4/clusters74": (69.80e9, "batch", "00a18ffaf3f56c44")}
 
 
 def per_matvec(value):

@@ -829,8 +829,27 @@ __device__ __forceinline__ void cta_reduce(const StepArgs& a, typename CH::Acc s
   }
 }
 
+// Programmatic dependent launch: consecutive short steps of a chain are
+// launched with programmatic stream serialisation, so the next step's CTAs
+// are set up while this step finishes; each step waits for its
+// predecessor's completion (and memory) before touching any data.  Without
+// the launch attribute both instructions are no-ops.  Measured on the 2D
+// L = 32 FP64 solve (64 KB vector blocks): 4.37 -> 3.98 us per step; on the
+// 134 MB blocks of the 3D L = 64 FP32 solve no gain (75.45 -> 75.57 us), so
+// only steps on vector blocks up to KPM_PDL_MAX_BYTES use it.
+#ifndef KPM_PDL
+#define KPM_PDL 1
+#endif
+#ifndef KPM_PDL_MAX_BYTES
+#define KPM_PDL_MAX_BYTES (16u << 20)
+#endif
+
 template <class CH, int MODE, class OP>
 __global__ void __launch_bounds__(256, OP::kMinBlocks) cheb_step_kernel(const StepArgs a) {
+#if KPM_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
   const OP op;
   typename CH::Acc s;
   CH::acc_zero(s);
@@ -867,8 +886,24 @@ cudaError_t allow_smem(K kern, size_t smem) {
 template <class CH, int MODE, class OP>
 cudaError_t launch_one(const StepArgs& a, const LaunchCfg& cfg, cudaStream_t st) {
   const size_t smem = MODE == MODE_SPMV ? 0 : step_smem_bytes(a.Gt, cfg.block, CH::VEC);
-  cheb_step_kernel<CH, MODE, OP><<<dim3(cfg.grid, a.G / a.Gt), cfg.block, smem, st>>>(a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
+  const size_t block_bytes =
+      (size_t)a.n * a.Rp * sizeof(typename CH::T) * (CH::CPLX ? 2 : 1);
+  if (KPM_PDL && MODE == MODE_STEP && block_bytes <= KPM_PDL_MAX_BYTES) {
+    // a regular step follows the first step or another step of the same chain
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3(cfg.grid, a.G / a.Gt);
+    lc.blockDim = dim3(cfg.block);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, cheb_step_kernel<CH, MODE, OP>, a);
+  }
+  cheb_step_kernel<CH, MODE, OP><<<dim3(cfg.grid, a.G / a.Gt), cfg.block, smem, st>>>(a);
   return cudaGetLastError();
 }
 
