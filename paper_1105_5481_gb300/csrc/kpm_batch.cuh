@@ -45,6 +45,13 @@ struct BatchTask {
   unsigned long long seed;
   int realisation;
   int flags;          // set by the kernel: bit0 = a moment left [-1, 1]
+  // R-tiling: an instance's vector columns split into `ntiles` independent
+  // tasks (tile `ycol` holds columns ycol*Rt .. ycol*Rt + Rt - 1, Rt = Gt*VEC);
+  // the last tile to finish averages the per-vector moments.  ntiles 0 or 1:
+  // one task holds all columns.
+  int ycol;
+  int ntiles;
+  int* tiles_done;    // per-instance count of finished tiles (zeroed per launch)
 };
 
 template <class CH, class OP>
@@ -57,6 +64,10 @@ __global__ void __launch_bounds__(256, KPM_BATCH_MIN_BLOCKS) batch_kernel(BatchT
   const int t = threadIdx.x;
   extern __shared__ double smem[];
   __shared__ int s_task;
+  __shared__ int s_last;
+  // the task's column tile (first column, columns): read where used, after a
+  // barrier, so that the values are not held in registers across the steps
+  __shared__ int s_tile[2];
   // The task's step arguments for even and odd steps (x and y swapped), kept
   // in shared memory: read where used instead of held in registers across
   // the step loop.
@@ -73,11 +84,18 @@ __global__ void __launch_bounds__(256, KPM_BATCH_MIN_BLOCKS) batch_kernel(BatchT
     if (task >= ntasks) break;
     BatchTask& bt = tasks[task];
     if (t < 2) {
+      // a column tile is addressed as a block whose rows start at the tile's
+      // first chunk (the row stride stays G chunks)
+      const size_t coff = (size_t)bt.ycol * bt.a.Gt * CH::SC * sizeof(T);
       StepArgs a = bt.a;
-      a.x = bt.v[t];
-      a.y = bt.v[t ^ 1];
+      a.x = reinterpret_cast<const char*>(bt.v[t]) + coff;
+      a.y = reinterpret_cast<char*>(bt.v[t ^ 1]) + coff;
       a.w = a.y;
       s_args[t] = a;
+      if (t == 0) {
+        s_tile[0] = bt.ycol * bt.a.Gt * CH::VEC;
+        s_tile[1] = bt.a.Gt * CH::VEC;
+      }
     }
     __syncthreads();
     const int Rp = s_args[0].Rp;
@@ -91,23 +109,26 @@ __global__ void __launch_bounds__(256, KPM_BATCH_MIN_BLOCKS) batch_kernel(BatchT
       const StepArgs& a = s_args[step & 1];
       if (step == 0) {
         T* v0 = reinterpret_cast<T*>(bt.v[0]);
-        const int64_t total = a.n * Rp;
+        const int c0 = s_tile[0], Rt = s_tile[1];
+        const int64_t total = a.n * Rt;
         for (int64_t e = (int64_t)rank * blockDim.x + t; e < total; e += (int64_t)C * blockDim.x)
-          random_entry<T, CH::CPLX>(v0, a.n, Rp, bt.R, bt.seed,
-                                    (unsigned long long)bt.realisation, e);
+          random_entry<T, CH::CPLX>(v0, a.n, Rp, bt.R, bt.seed, (unsigned long long)bt.realisation,
+                                    (e / Rt) * Rp + c0 + e % Rt);
         cluster.sync();
       }
       typename CH::Acc s;
       CH::acc_zero(s);
       step_rows<CH, MODE_DYN, OP, false, true>(a, op, rank, C, 0, s, step == 0);
-      cta_reduce<CH>(a, s, 0, red, part0 + ((size_t)(step & 1) * C + rank) * 2 * Rp);
+      cta_reduce<CH>(a, s, 0, red, part0 + ((size_t)(step & 1) * C + rank) * 2 * Rp + s_tile[0]);
       cluster.sync();
       if (rank == 0) {
         const double* pp = part + (size_t)(step & 1) * C * 2 * Rp;
-        for (int o = t; o < 2 * Rp; o += blockDim.x) {
+        const int c0 = s_tile[0], Rt = s_tile[1];
+        for (int o = t; o < 2 * Rt; o += blockDim.x) {
+          const int q = (o / Rt) * Rp + c0 + o % Rt;  // (A or B, column)
           double sum = 0.0;
-          for (int r = 0; r < C; ++r) sum += pp[(size_t)r * 2 * Rp + o];
-          bt.sums[(size_t)step * 2 * Rp + o] = sum;
+          for (int r = 0; r < C; ++r) sum += pp[(size_t)r * 2 * Rp + q];
+          bt.sums[(size_t)step * 2 * Rp + q] = sum;
         }
       }
     }
@@ -115,8 +136,9 @@ __global__ void __launch_bounds__(256, KPM_BATCH_MIN_BLOCKS) batch_kernel(BatchT
       __syncthreads();  // rank 0's own sums writes above
       const int R = bt.R, M = bt.M;
       const double inv_n = 1.0 / (double)s_args[0].n;
-      for (int e = t; e < R * nsteps; e += blockDim.x) {
-        const int r = e / nsteps, step = e % nsteps;
+      const int r0 = s_tile[0], nr = max(0, min(R, r0 + s_tile[1]) - r0);  // this task's vectors
+      for (int e = t; e < nr * nsteps; e += blockDim.x) {
+        const int r = r0 + e / nsteps, step = e % nsteps;
         const double mu0 = bt.sums[r] * inv_n, mu1 = bt.sums[Rp + r] * inv_n;
         double me = mu0, mo = mu1;
         if (step > 0) {
@@ -128,11 +150,22 @@ __global__ void __launch_bounds__(256, KPM_BATCH_MIN_BLOCKS) batch_kernel(BatchT
         if (!(fabs(me) <= 1.0 + 1e-6) || !(fabs(mo) <= 1.0 + 1e-6)) atomicOr(&bt.flags, 1);
       }
       __syncthreads();
-      for (int m = t; m < M; m += blockDim.x) {
-        double acc = 0.0;
-        for (int r = 0; r < R; ++r) acc += bt.per_vec[(size_t)r * M + m];
-        bt.mu[m] = acc / (double)R;
+      bool last = true;
+      if (bt.ntiles > 1) {
+        // the other tiles' per-vector moments: written by other clusters,
+        // published by their fence before their count, read through L2
+        __threadfence();
+        if (t == 0) s_last = atomicAdd(bt.tiles_done, 1) == bt.ntiles - 1;
+        __syncthreads();
+        last = s_last != 0;
+        if (last) __threadfence();
       }
+      if (last)
+        for (int m = t; m < M; m += blockDim.x) {
+          double acc = 0.0;
+          for (int r = 0; r < R; ++r) acc += __ldcg(bt.per_vec + (size_t)r * M + m);
+          bt.mu[m] = acc / (double)R;
+        }
     }
     cluster.sync();  // the instance is complete on every CTA of the cluster (and s_args free)
   }

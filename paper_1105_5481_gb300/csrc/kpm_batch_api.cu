@@ -1,7 +1,8 @@
 // C ABI of the batched persistent launch (kpm_batch_*): many independent KPM
 // solves of uneven size advanced by one cluster kernel launch that is captured
 // once into a CUDA graph and replayed, with an autotuner choosing the cluster
-// size, the number of resident clusters and the traversal chunk.
+// size, the number of resident clusters, the traversal chunk and the R-tiling
+// (an instance's vector columns split into independent tasks).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -22,7 +23,10 @@ struct BatchConfig {
   int C = 4;          // CTAs per cluster
   int chunk = 4;      // passes per traversal chunk
   int frac = 100;     // percent of the co-resident clusters launched
+  int rtiles = 1;     // column tiles per instance (divides the chunks per row)
 };
+
+constexpr int MAX_RTILES = 4;
 
 struct kpm_batch_s {
   int device = 0;
@@ -33,10 +37,11 @@ struct kpm_batch_s {
   std::vector<int> M;                // per instance (original order)
   std::vector<size_t> mu_off;        // offsets of each instance's moments in the output
   size_t mu_total = 0;
-  std::vector<int> order;            // task slot -> instance (decreasing work)
-  std::vector<BatchTask> host_tasks; // task slot order
+  std::vector<int> order;            // instance slots in decreasing work
+  std::vector<BatchTask> inst_tasks; // one untiled task per instance (instance order)
+  std::vector<BatchTask> host_tasks; // task slot order of the current configuration
   BatchTask* d_tasks = nullptr;
-  int* d_queue = nullptr;
+  int* d_queue = nullptr;            // [0] task queue, [1 + i] tiles finished of instance i
   void* d_pool = nullptr;            // vectors, sums, per-vector moments, operators
   double* d_mu = nullptr;            // [mu_total] in instance order (inside the pool)
   StepArgs proto{};                  // template-selecting prototype (first instance)
@@ -87,28 +92,46 @@ int max_clusters(kpm_batch_s* b, int C) {
 }
 
 kpm_status build_graph(kpm_batch_s* b, const BatchConfig& c) {
-  if (b->exec && b->exec_cfg.C == c.C && b->exec_cfg.chunk == c.chunk && b->exec_cfg.frac == c.frac)
+  if (b->exec && b->exec_cfg.C == c.C && b->exec_cfg.chunk == c.chunk &&
+      b->exec_cfg.frac == c.frac && b->exec_cfg.rtiles == c.rtiles)
     return KPM_OK;
+  if (c.rtiles < 1 || c.rtiles > MAX_RTILES || b->G % c.rtiles)
+    return fail(KPM_EINVAL, "R-tiles must divide the chunks per row");
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
+  // tasks of this configuration: the tiles of an instance are consecutive in
+  // the queue, instances in decreasing work
+  b->host_tasks.clear();
+  for (int i : b->order) {
+    for (int j = 0; j < c.rtiles; ++j) {
+      BatchTask t = b->inst_tasks[i];
+      t.a.Gt = b->G / c.rtiles;
+      plan_instance(t.a, b->handles[i], c.chunk);
+      t.ycol = j;
+      t.ntiles = c.rtiles;
+      t.tiles_done = b->d_queue + 1 + i;
+      b->host_tasks.push_back(t);
+    }
+  }
+  b->proto = b->host_tasks[0].a;
+  const int ntasks = (int)b->host_tasks.size();
   const int nclu = max_clusters(b, c.C);
   if (nclu <= 0) return fail(KPM_EINVAL, "cluster size " + std::to_string(c.C) + " cannot be launched");
-  const int use = std::max(1, std::min(b->count, nclu * c.frac / 100));
+  const int use = std::max(1, std::min(ntasks, nclu * c.frac / 100));
   b->grid = use * c.C;
-  for (auto& t : b->host_tasks) t.a.chunk = c.chunk;
   KPM_CUDA(cudaMemcpy(b->d_tasks, b->host_tasks.data(), b->host_tasks.size() * sizeof(BatchTask),
                       cudaMemcpyHostToDevice));
   const uint64_t before = g_launches.load();
   KPM_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->cap_stream);
+  cudaError_t e = cudaMemsetAsync(b->d_queue, 0, (1 + (size_t)b->count) * sizeof(int), b->cap_stream);
   if (e == cudaSuccess)
     e = cudaEventRecordWithFlags(b->ev[0], b->cap_stream, cudaEventRecordExternal);
   if (e == cudaSuccess)
-    e = b->fp32 ? launch_batch_f32(b->cplx, b->proto, b->d_tasks, b->count, b->d_queue, b->grid,
+    e = b->fp32 ? launch_batch_f32(b->cplx, b->proto, b->d_tasks, ntasks, b->d_queue, b->grid,
                                    c.C, b->cap_stream)
-                : launch_batch_f64(b->cplx, b->proto, b->d_tasks, b->count, b->d_queue, b->grid,
+                : launch_batch_f64(b->cplx, b->proto, b->d_tasks, ntasks, b->d_queue, b->grid,
                                    c.C, b->cap_stream);
   if (e == cudaSuccess)
     e = cudaEventRecordWithFlags(b->ev[1], b->cap_stream, cudaEventRecordExternal);
@@ -165,7 +188,9 @@ bool cache_lookup(const std::string& key, BatchConfig* c) {
     const size_t sep = s.rfind(" = ");
     if (sep == std::string::npos || s.substr(0, sep) != key) continue;
     BatchConfig t;
-    if (sscanf(s.c_str() + sep + 3, "%d %d %d", &t.C, &t.chunk, &t.frac) == 3) {
+    const int got = sscanf(s.c_str() + sep + 3, "%d %d %d %d", &t.C, &t.chunk, &t.frac, &t.rtiles);
+    if (got == 3) t.rtiles = 1;  // entries written before R-tiling was tuned
+    if (got >= 3) {
       *c = t;
       found = true;
     }
@@ -180,7 +205,7 @@ void cache_store(const std::string& key, const BatchConfig& c) {
   if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
   FILE* f = fopen(path.c_str(), "a");
   if (!f) return;  // an unwritable cache only costs a re-tune
-  fprintf(f, "%s = %d %d %d\n", key.c_str(), c.C, c.chunk, c.frac);
+  fprintf(f, "%s = %d %d %d %d\n", key.c_str(), c.C, c.chunk, c.frac, c.rtiles);
   fclose(f);
 }
 
@@ -277,8 +302,8 @@ kpm_status kpm_batch_create(int count, const kpm_handle* handles, const kpm_para
   off = align_up(off + b->mu_total * 8, 256);
   e = cudaMalloc(&b->d_pool, std::max<size_t>(off, 256));
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc(batch pool)"));
-  e = cudaMalloc((void**)&b->d_tasks, count * sizeof(BatchTask));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_queue, sizeof(int));
+  e = cudaMalloc((void**)&b->d_tasks, (size_t)count * MAX_RTILES * sizeof(BatchTask));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_queue, (1 + (size_t)count) * sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
@@ -357,9 +382,8 @@ kpm_status kpm_batch_create(int count, const kpm_handle* handles, const kpm_para
   std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
     return (double)handles[x]->n * params[x].M > (double)handles[y]->n * params[y].M;
   });
-  b->host_tasks.resize(count);
-  for (int k = 0; k < count; ++k) b->host_tasks[k] = tasks[b->order[k]];
-  b->proto = b->host_tasks[0].a;
+  b->inst_tasks = tasks;
+  b->proto = tasks[b->order[0]].a;
   BatchConfig cached;
   if (cache_lookup(tune_key(b), &cached)) {
     b->cfg = cached;
@@ -391,8 +415,8 @@ kpm_status kpm_batch_run(kpm_batch b, double* mu, void* stream) {
     if (cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess) b->last_ms = ms;
     cudaGetLastError();
     // divergence flags of the instances
-    std::vector<BatchTask> back(b->count);
-    KPM_CUDA(cudaMemcpy(back.data(), b->d_tasks, b->count * sizeof(BatchTask),
+    std::vector<BatchTask> back(b->host_tasks.size());
+    KPM_CUDA(cudaMemcpy(back.data(), b->d_tasks, back.size() * sizeof(BatchTask),
                         cudaMemcpyDeviceToHost));
     int bad = 0;
     for (auto& t : back) bad |= t.flags;
@@ -414,31 +438,33 @@ kpm_status kpm_batch_tune(kpm_batch b, int reps, void* stream) {
   double best_ms = 1e30;
   for (int C : Cs)
     for (int ch : chunks)
-      for (int fr : fracs) {
-        BatchConfig c;
-        c.C = C;
-        c.chunk = ch;
-        c.frac = fr;
-        if (max_clusters(b, C) <= 0) continue;
-        if (build_graph(b, c) != KPM_OK) {
-          cudaGetLastError();
-          continue;
-        }
-        if (replay(b, st) != KPM_OK) return fail(KPM_ECUDA, "batch replay failed while tuning");
-        double tot = 0.0;
-        for (int r = 0; r < reps; ++r) {
+      for (int fr : fracs)
+        for (int rt = 1; rt <= MAX_RTILES && b->G % rt == 0; rt *= 2) {
+          BatchConfig c;
+          c.C = C;
+          c.chunk = ch;
+          c.frac = fr;
+          c.rtiles = rt;
+          if (max_clusters(b, C) <= 0) continue;
+          if (build_graph(b, c) != KPM_OK) {
+            cudaGetLastError();
+            continue;
+          }
           if (replay(b, st) != KPM_OK) return fail(KPM_ECUDA, "batch replay failed while tuning");
-          KPM_CUDA(cudaStreamSynchronize(st));
-          float ms = 0.f;
-          KPM_CUDA(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
-          tot += ms;
+          double tot = 0.0;
+          for (int r = 0; r < reps; ++r) {
+            if (replay(b, st) != KPM_OK) return fail(KPM_ECUDA, "batch replay failed while tuning");
+            KPM_CUDA(cudaStreamSynchronize(st));
+            float ms = 0.f;
+            KPM_CUDA(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+            tot += ms;
+          }
+          const double ms = tot / reps;
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+          }
         }
-        const double ms = tot / reps;
-        if (ms < best_ms) {
-          best_ms = ms;
-          best = c;
-        }
-      }
   if (best_ms >= 1e30) return fail(KPM_ECUDA, "no launchable batch configuration");
   b->cfg = best;
   b->tuned = true;
@@ -472,6 +498,22 @@ kpm_status kpm_batch_set_config(kpm_batch b, int cluster, int chunk, int percent
   b->cfg.C = cluster;
   b->cfg.chunk = chunk;
   b->cfg.frac = percent;
+  return KPM_OK;
+}
+
+kpm_status kpm_batch_set_rtiles(kpm_batch b, int rtiles) {
+  if (!b) return fail(KPM_EINVAL, "batch is NULL");
+  if (rtiles < 1 || rtiles > MAX_RTILES || (rtiles & (rtiles - 1)) || b->G % rtiles)
+    return fail(KPM_EINVAL, "R-tiles must be 1, 2 or 4 and divide the chunks per row (" +
+                                std::to_string(b->G) + ")");
+  b->cfg.rtiles = rtiles;
+  return KPM_OK;
+}
+
+kpm_status kpm_batch_get_rtiles(kpm_batch b, int* rtiles, int* max_rtiles) {
+  if (!b) return fail(KPM_EINVAL, "batch is NULL");
+  if (rtiles) *rtiles = b->cfg.rtiles;
+  if (max_rtiles) *max_rtiles = std::min(MAX_RTILES, b->G);
   return KPM_OK;
 }
 

@@ -119,7 +119,8 @@ def lib() -> C.CDLL:
                      "kpm_bounds",
                      "kpm_moments", "kpm_dos", "kpm_info", "kpm_step_timing",
                      "kpm_moments_csr_noalloc", "kpm_batch_create", "kpm_batch_run", "kpm_batch_tune",
-                     "kpm_batch_set_config", "kpm_batch_info", "kpm_server_create",
+                     "kpm_batch_set_config", "kpm_batch_info", "kpm_batch_set_rtiles",
+                     "kpm_batch_get_rtiles", "kpm_server_create",
                      "kpm_server_submit", "kpm_server_wait", "kpm_server_poll", "kpm_server_cancel",
                      "kpm_server_stats"):
             getattr(L, name).restype = C.c_int
@@ -480,6 +481,17 @@ def kpm_batch_tune(bt: Batch, reps=1, stream=None):
 
 def kpm_batch_set_config(bt: Batch, cluster, chunk=4, percent=100):
     _check(lib().kpm_batch_set_config(bt.raw, int(cluster), int(chunk), int(percent)))
+
+
+def kpm_batch_set_rtiles(bt: Batch, rtiles):
+    _check(lib().kpm_batch_set_rtiles(bt.raw, int(rtiles)))
+
+
+def kpm_batch_get_rtiles(bt: Batch):
+    """(current R-tiles, largest admissible)."""
+    rt, mx = C.c_int(), C.c_int()
+    _check(lib().kpm_batch_get_rtiles(bt.raw, C.byref(rt), C.byref(mx)))
+    return rt.value, mx.value
 
 
 def kpm_batch_info(bt: Batch):

@@ -1,6 +1,7 @@
 """The batched persistent launch: every instance against the oracle, the same
 instance alone and in a mix (bitwise, for a fixed cluster size), all cluster
-sizes, and the autotuner with its on-disk cache."""
+sizes, R-tiling (an instance's columns split into independent tasks), and the
+autotuner with its on-disk cache."""
 import numpy as np
 import pytest
 
@@ -91,6 +92,46 @@ def test_every_cluster_size(K, C):
         assert np.abs(mu - mu_o).max() <= 1e-10
 
 
+# R = 16 real FP32 is 2 chunks per row; R = 32 real FP32, R = 16 complex FP32
+# and R = 8 real FP64 are 4 (the most tiles); R = 13 leaves padded columns
+@pytest.mark.parametrize("prec,R,tiles", [("fp32", 16, 2), ("fp32", 32, 4), ("fp64", 8, 4),
+                                          ("fp32", 13, 2), ("fp64", 8, 2)])
+def test_rtiles_match_oracle(K, prec, R, tiles):
+    insts = instances(8)
+    with make_batch(K, insts, prec, R) as bt:
+        assert K.kpm_batch_get_rtiles(bt) == (1, min(4, -(-R // {"fp32": 8, "fp64": 2}[prec])))
+        K.kpm_batch_set_config(bt, 2, 4, 100)
+        K.kpm_batch_set_rtiles(bt, tiles)
+        assert K.kpm_batch_get_rtiles(bt)[0] == tiles
+        parts = bt.split(K.kpm_batch_run(bt))
+        again = bt.split(K.kpm_batch_run(bt))      # the tile counters restart on each replay
+    for x, mu, mu2 in zip(insts, parts, again):
+        mu_o, _ = O.moments_doubling(x["H"], x["a"], x["b"], I.rademacher_block(x["seed"], x["H"].n, R),
+                                     x["M"])
+        assert np.abs(mu - mu_o).max() <= TOL[prec]
+        assert np.array_equal(mu, mu2)
+
+
+def test_rtiles_complex_and_refusals(K):
+    L = (12, 10)
+    N = 120
+    hop = I.spin_hoppings(L, *I.spins(3, N))
+    H = O.lattice_hamiltonian(L, hop=hop)
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    with K.kpm_create_stencil(2, L, hop=hop, complex_=True) as h:
+        bt = K.kpm_batch_create([h, h], [40, 62], 16, [a, a], [b, b], [5, 6], precision="fp32")
+        with bt:
+            for bad in (3, 8):
+                with pytest.raises(K.KPMError) as e:
+                    K.kpm_batch_set_rtiles(bt, bad)
+                assert e.value.status == K.KPM_EINVAL
+            K.kpm_batch_set_rtiles(bt, 4)
+            parts = bt.split(K.kpm_batch_run(bt))
+    for M, seed, mu in zip((40, 62), (5, 6), parts):
+        mu_o, _ = O.moments_doubling(H, a, b, I.phase_block(seed, N, 16), M)
+        assert np.abs(mu - mu_o).max() <= 1e-5
+
+
 def test_autotuner_writes_and_reuses_its_cache(K, tmp_path, monkeypatch):
     cache = tmp_path / "tune.txt"
     monkeypatch.setenv("KPM_TUNE_CACHE", str(cache))
@@ -98,10 +139,13 @@ def test_autotuner_writes_and_reuses_its_cache(K, tmp_path, monkeypatch):
     with make_batch(K, insts, "fp32") as bt:
         info = K.kpm_batch_tune(bt, reps=1)
         mu = K.kpm_batch_run(bt)
+        tiles = K.kpm_batch_get_rtiles(bt)[0]
     text = cache.read_text()
     assert "batch|" in text and f"= {info['cluster']} {info['chunk']}" in text
+    assert text.strip().endswith(f" {tiles}")
     with make_batch(K, insts, "fp32") as bt2:
         info2 = K.kpm_batch_info(bt2)
         mu2 = K.kpm_batch_run(bt2)
+        assert K.kpm_batch_get_rtiles(bt2)[0] == tiles
     assert (info2["cluster"], info2["chunk"]) == (info["cluster"], info["chunk"])
     assert np.array_equal(mu, mu2)
