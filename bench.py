@@ -60,7 +60,7 @@ BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
 # reported only while the hash matches.
 MEASURED_TRAFFIC = {"cubic_spin_L64": (347.67e6, "step", "3b00c719cc0d365a"),
                     "csr_spin_dilute_L160": (3438.84e6, "step", "3b00c719cc0d365a"),
-                    "batch_2d_256/C4/chunk4/clusters74/rt1": (69.75e9, "batch", "5b1fff3fe9c367cb")}
+                    "batch_2d_256/C4/chunk4/clusters74/rt1/top0": (69.75e9, "batch", "5b1fff3fe9c367cb")}
 
 
 def per_matvec(value):
@@ -538,7 +538,7 @@ def batch_leg(args):
     bt = K.kpm_batch_create(hs, Ms, R, [p[0] for p in ab], [p[1] for p in ab], seeds, "fp32")
     t0 = time.perf_counter()
     info = K.kpm_batch_tune(bt, reps=1)
-    info["rtiles"] = K.kpm_batch_get_rtiles(bt)[0]
+    info["rtiles"], info["tiled_instances"], _ = K.kpm_batch_get_rtiles(bt)
     tune_s = time.perf_counter() - t0
     mu_host = K.kpm_batch_run(bt)  # host output: divergence check
     assert np.all(np.abs(mu_host) <= 1 + 1e-5)
@@ -587,8 +587,9 @@ def batch_leg(args):
                    "launch": "one persistent cluster kernel per batch, CUDA graph replay",
                    "autotuned": info, "tune_s": tune_s, "l2": "instances' vectors mostly L2-resident"},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "traffic": measured_traffic("batch_2d_256/C%d/chunk%d/clusters%d/rt%d" % (
-                         info["cluster"], info["chunk"], info["clusters"], info["rtiles"])),
+                     "traffic": measured_traffic("batch_2d_256/C%d/chunk%d/clusters%d/rt%d/top%d" % (
+                         info["cluster"], info["chunk"], info["clusters"], info["rtiles"],
+                         info["tiled_instances"])),
                      "bytes_per_launch": byts, "peak_kind": peak_kind,
                      "note": "algorithmic bytes of all instances per batch launch; the working "
                              "set of the active instances is L2-resident, so frac can exceed 1"},

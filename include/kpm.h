@@ -284,10 +284,12 @@ kpm_status kpm_batch_create(int count, const kpm_handle* handles, const kpm_para
  * report KPM_EDIVERGE like kpm_moments. */
 kpm_status kpm_batch_run(kpm_batch b, double* mu, void* stream);
 
-/* Autotuner: times `reps` replays of every launchable configuration (cluster
- * size C in {1, 2, 4, 8, 16}, traversal chunk in {2, 4, 16} passes, 100 % or
- * 50 % of the co-resident clusters, R-tiles in {1, 2, 4} dividing the chunks
- * per row), keeps the fastest for this batch and appends it to the tuning
+/* Autotuner: times `reps` replays of every launchable untiled configuration
+ * (cluster size C in {1, 2, 4, 8, 16}, traversal chunk in {2, 4, 16} passes,
+ * 100 % or 50 % of the co-resident clusters), then, at the best of them and
+ * at half its cluster size, R-tiling (2 or 4 tiles dividing the chunks per
+ * row) of all, half, an eighth or a thirty-second of the instances, largest
+ * work first; keeps the fastest for this batch and appends it to the tuning
  * cache. */
 kpm_status kpm_batch_tune(kpm_batch b, int reps, void* stream);
 
@@ -300,17 +302,19 @@ kpm_status kpm_batch_set_config(kpm_batch b, int cluster, int chunk, int percent
 kpm_status kpm_batch_info(kpm_batch b, int* cluster, int* chunk, int* clusters_launched,
                           double* last_ms);
 
-/* R-tiling: each instance's padded vector block (Rp columns in G chunks per
- * row) is split into `rtiles` column tiles run as independent tasks, possibly
- * on different clusters at the same time (each tile a self-contained KPM
+/* R-tiling: the padded vector block (Rp columns in G chunks per row) of each
+ * of the `top` instances of largest work (N*M; top <= 0 or >= count: all) is
+ * split into `rtiles` column tiles run as independent tasks, possibly on
+ * different clusters at the same time (each tile a self-contained KPM
  * recursion on its vectors, Eq. (rn)); the last tile to finish averages the
  * per-vector moments.  rtiles in {1, 2, 4} and dividing G (KPM_EINVAL
- * otherwise); 1 = no tiling.  An instance's moments depend only on C, rtiles
- * and the instance. */
-kpm_status kpm_batch_set_rtiles(kpm_batch b, int rtiles);
+ * otherwise); 1 = no tiling.  An instance's moments depend only on C, its
+ * tile count and the instance. */
+kpm_status kpm_batch_set_rtiles(kpm_batch b, int rtiles, int top);
 
-/* Current R-tiles and the largest value this batch admits (min(4, G)). */
-kpm_status kpm_batch_get_rtiles(kpm_batch b, int* rtiles, int* max_rtiles);
+/* Current R-tiles, the number of instances tiled, and the largest R-tiles
+ * this batch admits (min(4, G)). */
+kpm_status kpm_batch_get_rtiles(kpm_batch b, int* rtiles, int* top, int* max_rtiles);
 
 void kpm_batch_destroy(kpm_batch b);
 

@@ -23,7 +23,8 @@ struct BatchConfig {
   int C = 4;          // CTAs per cluster
   int chunk = 4;      // passes per traversal chunk
   int frac = 100;     // percent of the co-resident clusters launched
-  int rtiles = 1;     // column tiles per instance (divides the chunks per row)
+  int rtiles = 1;     // column tiles of a tiled instance (divides the chunks per row)
+  int top = 0;        // the `top` instances of largest work are tiled (<= 0: all)
 };
 
 constexpr int MAX_RTILES = 4;
@@ -93,7 +94,7 @@ int max_clusters(kpm_batch_s* b, int C) {
 
 kpm_status build_graph(kpm_batch_s* b, const BatchConfig& c) {
   if (b->exec && b->exec_cfg.C == c.C && b->exec_cfg.chunk == c.chunk &&
-      b->exec_cfg.frac == c.frac && b->exec_cfg.rtiles == c.rtiles)
+      b->exec_cfg.frac == c.frac && b->exec_cfg.rtiles == c.rtiles && b->exec_cfg.top == c.top)
     return KPM_OK;
   if (c.rtiles < 1 || c.rtiles > MAX_RTILES || b->G % c.rtiles)
     return fail(KPM_EINVAL, "R-tiles must divide the chunks per row");
@@ -101,21 +102,25 @@ kpm_status build_graph(kpm_batch_s* b, const BatchConfig& c) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
-  // tasks of this configuration: the tiles of an instance are consecutive in
-  // the queue, instances in decreasing work
+  // tasks of this configuration: instances in decreasing work, the `top`
+  // largest split into rtiles column tiles (consecutive in the queue)
   b->host_tasks.clear();
-  for (int i : b->order) {
-    for (int j = 0; j < c.rtiles; ++j) {
+  const int ntiled = c.rtiles > 1 ? (c.top <= 0 ? b->count : std::min(c.top, b->count)) : 0;
+  for (int k = 0; k < b->count; ++k) {
+    const int i = b->order[k];
+    const int T = k < ntiled ? c.rtiles : 1;
+    for (int j = 0; j < T; ++j) {
       BatchTask t = b->inst_tasks[i];
-      t.a.Gt = b->G / c.rtiles;
+      t.a.Gt = b->G / T;
       plan_instance(t.a, b->handles[i], c.chunk);
       t.ycol = j;
-      t.ntiles = c.rtiles;
+      t.ntiles = T;
       t.tiles_done = b->d_queue + 1 + i;
       b->host_tasks.push_back(t);
     }
   }
-  b->proto = b->host_tasks[0].a;
+  // the kernel's shared memory is sized for the widest task
+  b->proto = b->host_tasks.back().a;
   const int ntasks = (int)b->host_tasks.size();
   const int nclu = max_clusters(b, c.C);
   if (nclu <= 0) return fail(KPM_EINVAL, "cluster size " + std::to_string(c.C) + " cannot be launched");
@@ -188,8 +193,10 @@ bool cache_lookup(const std::string& key, BatchConfig* c) {
     const size_t sep = s.rfind(" = ");
     if (sep == std::string::npos || s.substr(0, sep) != key) continue;
     BatchConfig t;
-    const int got = sscanf(s.c_str() + sep + 3, "%d %d %d %d", &t.C, &t.chunk, &t.frac, &t.rtiles);
+    const int got =
+        sscanf(s.c_str() + sep + 3, "%d %d %d %d %d", &t.C, &t.chunk, &t.frac, &t.rtiles, &t.top);
     if (got == 3) t.rtiles = 1;  // entries written before R-tiling was tuned
+    if (got == 4) t.top = 0;
     if (got >= 3) {
       *c = t;
       found = true;
@@ -205,7 +212,7 @@ void cache_store(const std::string& key, const BatchConfig& c) {
   if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
   FILE* f = fopen(path.c_str(), "a");
   if (!f) return;  // an unwritable cache only costs a re-tune
-  fprintf(f, "%s = %d %d %d %d\n", key.c_str(), c.C, c.chunk, c.frac, c.rtiles);
+  fprintf(f, "%s = %d %d %d %d %d\n", key.c_str(), c.C, c.chunk, c.frac, c.rtiles, c.top);
   fclose(f);
 }
 
@@ -436,35 +443,63 @@ kpm_status kpm_batch_tune(kpm_batch b, int reps, void* stream) {
   const int fracs[] = {100, 50};
   BatchConfig best;
   double best_ms = 1e30;
+  auto time_cfg = [&](const BatchConfig& c) -> kpm_status {
+    if (max_clusters(b, c.C) <= 0) return KPM_OK;
+    if (build_graph(b, c) != KPM_OK) {
+      cudaGetLastError();
+      return KPM_OK;
+    }
+    if (replay(b, st) != KPM_OK) return fail(KPM_ECUDA, "batch replay failed while tuning");
+    double tot = 0.0;
+    for (int r = 0; r < reps; ++r) {
+      if (replay(b, st) != KPM_OK) return fail(KPM_ECUDA, "batch replay failed while tuning");
+      KPM_CUDA(cudaStreamSynchronize(st));
+      float ms = 0.f;
+      KPM_CUDA(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+      tot += ms;
+    }
+    const double ms = tot / reps;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+    return KPM_OK;
+  };
+  // untiled: cluster size, chunk, resident clusters
   for (int C : Cs)
     for (int ch : chunks)
-      for (int fr : fracs)
-        for (int rt = 1; rt <= MAX_RTILES && b->G % rt == 0; rt *= 2) {
-          BatchConfig c;
+      for (int fr : fracs) {
+        BatchConfig c;
+        c.C = C;
+        c.chunk = ch;
+        c.frac = fr;
+        kpm_status s_ = time_cfg(c);
+        if (s_ != KPM_OK) return s_;
+      }
+  // then R-tiling of the largest instances (all, a half, an eighth, a
+  // thirty-second of them) at the best configuration and half its cluster;
+  // a tiling is kept only if it beats the untiled best by more than 2 %
+  // (the timing noise of a few replays)
+  if (best_ms < 1e30) {
+    const BatchConfig base = best;
+    const double base_ms = best_ms;
+    best_ms = base_ms * 0.98;
+    for (int C : {base.C, base.C / 2}) {
+      if (C < 1) continue;
+      for (int rt = 2; rt <= MAX_RTILES && b->G % rt == 0; rt *= 2)
+        for (int div : {1, 2, 8, 32}) {
+          const int top = std::max(1, b->count / div);
+          if (div > 1 && top == b->count) continue;
+          BatchConfig c = base;
           c.C = C;
-          c.chunk = ch;
-          c.frac = fr;
           c.rtiles = rt;
-          if (max_clusters(b, C) <= 0) continue;
-          if (build_graph(b, c) != KPM_OK) {
-            cudaGetLastError();
-            continue;
-          }
-          if (replay(b, st) != KPM_OK) return fail(KPM_ECUDA, "batch replay failed while tuning");
-          double tot = 0.0;
-          for (int r = 0; r < reps; ++r) {
-            if (replay(b, st) != KPM_OK) return fail(KPM_ECUDA, "batch replay failed while tuning");
-            KPM_CUDA(cudaStreamSynchronize(st));
-            float ms = 0.f;
-            KPM_CUDA(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
-            tot += ms;
-          }
-          const double ms = tot / reps;
-          if (ms < best_ms) {
-            best_ms = ms;
-            best = c;
-          }
+          c.top = div == 1 ? 0 : top;
+          kpm_status s_ = time_cfg(c);
+          if (s_ != KPM_OK) return s_;
         }
+    }
+    if (best.rtiles == 1) best_ms = base_ms;  // no tiling beat the margin: best is base
+  }
   if (best_ms >= 1e30) return fail(KPM_ECUDA, "no launchable batch configuration");
   b->cfg = best;
   b->tuned = true;
@@ -501,18 +536,20 @@ kpm_status kpm_batch_set_config(kpm_batch b, int cluster, int chunk, int percent
   return KPM_OK;
 }
 
-kpm_status kpm_batch_set_rtiles(kpm_batch b, int rtiles) {
+kpm_status kpm_batch_set_rtiles(kpm_batch b, int rtiles, int top) {
   if (!b) return fail(KPM_EINVAL, "batch is NULL");
   if (rtiles < 1 || rtiles > MAX_RTILES || (rtiles & (rtiles - 1)) || b->G % rtiles)
     return fail(KPM_EINVAL, "R-tiles must be 1, 2 or 4 and divide the chunks per row (" +
                                 std::to_string(b->G) + ")");
   b->cfg.rtiles = rtiles;
+  b->cfg.top = top <= 0 || top >= b->count ? 0 : top;
   return KPM_OK;
 }
 
-kpm_status kpm_batch_get_rtiles(kpm_batch b, int* rtiles, int* max_rtiles) {
+kpm_status kpm_batch_get_rtiles(kpm_batch b, int* rtiles, int* top, int* max_rtiles) {
   if (!b) return fail(KPM_EINVAL, "batch is NULL");
   if (rtiles) *rtiles = b->cfg.rtiles;
+  if (top) *top = b->cfg.rtiles > 1 ? (b->cfg.top <= 0 ? b->count : b->cfg.top) : 0;
   if (max_rtiles) *max_rtiles = std::min(MAX_RTILES, b->G);
   return KPM_OK;
 }

@@ -483,15 +483,16 @@ def kpm_batch_set_config(bt: Batch, cluster, chunk=4, percent=100):
     _check(lib().kpm_batch_set_config(bt.raw, int(cluster), int(chunk), int(percent)))
 
 
-def kpm_batch_set_rtiles(bt: Batch, rtiles):
-    _check(lib().kpm_batch_set_rtiles(bt.raw, int(rtiles)))
+def kpm_batch_set_rtiles(bt: Batch, rtiles, top=0):
+    """Split the `top` largest instances (0: all) into `rtiles` column tiles."""
+    _check(lib().kpm_batch_set_rtiles(bt.raw, int(rtiles), int(top)))
 
 
 def kpm_batch_get_rtiles(bt: Batch):
-    """(current R-tiles, largest admissible)."""
-    rt, mx = C.c_int(), C.c_int()
-    _check(lib().kpm_batch_get_rtiles(bt.raw, C.byref(rt), C.byref(mx)))
-    return rt.value, mx.value
+    """(current R-tiles, instances tiled, largest admissible R-tiles)."""
+    rt, tp, mx = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().kpm_batch_get_rtiles(bt.raw, C.byref(rt), C.byref(tp), C.byref(mx)))
+    return rt.value, tp.value, mx.value
 
 
 def kpm_batch_info(bt: Batch):

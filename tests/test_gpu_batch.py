@@ -99,10 +99,10 @@ def test_every_cluster_size(K, C):
 def test_rtiles_match_oracle(K, prec, R, tiles):
     insts = instances(8)
     with make_batch(K, insts, prec, R) as bt:
-        assert K.kpm_batch_get_rtiles(bt) == (1, min(4, -(-R // {"fp32": 8, "fp64": 2}[prec])))
+        assert K.kpm_batch_get_rtiles(bt) == (1, 0, min(4, -(-R // {"fp32": 8, "fp64": 2}[prec])))
         K.kpm_batch_set_config(bt, 2, 4, 100)
         K.kpm_batch_set_rtiles(bt, tiles)
-        assert K.kpm_batch_get_rtiles(bt)[0] == tiles
+        assert K.kpm_batch_get_rtiles(bt)[:2] == (tiles, len(insts))
         parts = bt.split(K.kpm_batch_run(bt))
         again = bt.split(K.kpm_batch_run(bt))      # the tile counters restart on each replay
     for x, mu, mu2 in zip(insts, parts, again):
@@ -110,6 +110,21 @@ def test_rtiles_match_oracle(K, prec, R, tiles):
                                      x["M"])
         assert np.abs(mu - mu_o).max() <= TOL[prec]
         assert np.array_equal(mu, mu2)
+
+
+@pytest.mark.parametrize("top", [1, 3])
+def test_rtiles_of_the_largest_instances_only(K, top):
+    # only the `top` instances of largest N*M are tiled; the others run whole
+    insts = instances(10)
+    with make_batch(K, insts, "fp32", 32) as bt:
+        K.kpm_batch_set_config(bt, 4, 4, 100)
+        K.kpm_batch_set_rtiles(bt, 4, top)
+        assert K.kpm_batch_get_rtiles(bt)[:2] == (4, top)
+        parts = bt.split(K.kpm_batch_run(bt))
+    for x, mu in zip(insts, parts):
+        mu_o, _ = O.moments_doubling(x["H"], x["a"], x["b"], I.rademacher_block(x["seed"], x["H"].n, 32),
+                                     x["M"])
+        assert np.abs(mu - mu_o).max() <= 1e-5
 
 
 def test_rtiles_complex_and_refusals(K):
@@ -139,13 +154,14 @@ def test_autotuner_writes_and_reuses_its_cache(K, tmp_path, monkeypatch):
     with make_batch(K, insts, "fp32") as bt:
         info = K.kpm_batch_tune(bt, reps=1)
         mu = K.kpm_batch_run(bt)
-        tiles = K.kpm_batch_get_rtiles(bt)[0]
+        tiles, tiled, _ = K.kpm_batch_get_rtiles(bt)
     text = cache.read_text()
     assert "batch|" in text and f"= {info['cluster']} {info['chunk']}" in text
-    assert text.strip().endswith(f" {tiles}")
+    fields = text.strip().splitlines()[-1].split(" = ")[1].split()
+    assert int(fields[3]) == tiles and (tiles == 1 or int(fields[4]) in (0, tiled))
     with make_batch(K, insts, "fp32") as bt2:
         info2 = K.kpm_batch_info(bt2)
         mu2 = K.kpm_batch_run(bt2)
-        assert K.kpm_batch_get_rtiles(bt2)[0] == tiles
+        assert K.kpm_batch_get_rtiles(bt2)[:2] == (tiles, tiled)
     assert (info2["cluster"], info2["chunk"]) == (info["cluster"], info["chunk"])
     assert np.array_equal(mu, mu2)
