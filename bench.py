@@ -50,6 +50,7 @@ STEP_SOURCES = ["paper_1105_5481_gb300/csrc/kpm_step.cuh",
                 "paper_1105_5481_gb300/csrc/kpm_step_f32.cu",
                 "paper_1105_5481_gb300/csrc/kpm_args.h"]
 BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
+                                "paper_1105_5481_gb300/csrc/kpm_batch_res.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_batch_dispatch.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_batch_f32.cu"]
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture,
@@ -60,7 +61,7 @@ BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
 # reported only while the hash matches.
 MEASURED_TRAFFIC = {"cubic_spin_L64": (347.67e6, "step", "3b00c719cc0d365a"),
                     "csr_spin_dilute_L160": (3438.84e6, "step", "3b00c719cc0d365a"),
-                    "batch_2d_256/C4/chunk4/clusters74/rt1/top0": (69.75e9, "batch", "5b1fff3fe9c367cb")}
+                    "batch_2d_256/C4/chunk4/clusters74/rt1/top0": (68.17e9, "batch", "4782c8361760af5b")}
 
 
 def per_matvec(value):
@@ -331,7 +332,25 @@ def square_leg(args):
         e1.record(stream)
         stream.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    launches = K.kpm_kernel_launches() - l0
     chain_ms, nsteps = K.kpm_step_timing(h)
+    # the same solve as a batch of one: one persistent cluster launch, vectors in
+    # global memory or resident in the cluster's shared memory
+    batch_of_one = {}
+    with K.kpm_batch_create([h], [M], R, [a], [b], [100], "fp64") as b1:
+        for resident in (False, True):
+            K.kpm_batch_set_resident(b1, resident)
+            for C in (8, 16):
+                K.kpm_batch_set_config(b1, C, 1, 100)
+                for _ in range(3):
+                    K.kpm_batch_run(b1, out=mu_d, stream=stream)
+                e0.record(stream)
+                for _ in range(steps):
+                    K.kpm_batch_run(b1, out=mu_d, stream=stream)
+                e1.record(stream)
+                stream.synchronize()
+                batch_of_one["%s_C%d_us" % ("resident" if resident else "global", C)] = (
+                    e0.elapsed_time(e1) / steps * 1e3)
     bytes_step = 3 * N * R * 8 + N * 8  # vectors + on-site energies (uniform hopping)
     hbm, peak_kind = peaks()
     rate = bytes_step / (chain_ms / nsteps / 1e3) / 1e9
@@ -351,7 +370,8 @@ def square_leg(args):
                      "launch_ms": chain_ms / nsteps, "peak_kind": peak_kind,
                      "note": "127 dependent steps on 128 KB of vectors: each step is one "
                              "launch's latency; achieved = the L2-resident rate"},
-        "gpu_launches": K.kpm_kernel_launches() - l0, "clocks": clk.summary()}))
+        "batch_of_one_moments": batch_of_one,
+        "gpu_launches": launches, "clocks": clk.summary()}))
     h.close()
     return 0
 
@@ -391,6 +411,7 @@ def csr_leg(args):
         e1.record(stream)
         stream.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    launches = K.kpm_kernel_launches() - l0
     chain_ms, nsteps = K.kpm_step_timing(h)
     bytes_step = 3 * N * R * 8 + nnz * (8 + 4) + 8 * (N + 1)
     hbm, peak_kind = peaks()
@@ -409,7 +430,8 @@ def csr_leg(args):
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                      "traffic": measured_traffic("csr_spin_dilute_L160"), "bytes_per_launch": bytes_step,
                      "launch_ms": chain_ms / nsteps, "peak_kind": peak_kind},
-        "gpu_launches": K.kpm_kernel_launches() - l0, "clocks": clk.summary()}))
+        "batch_of_one_moments": batch_of_one,
+        "gpu_launches": launches, "clocks": clk.summary()}))
     h.close()
     return 0
 
@@ -539,6 +561,7 @@ def batch_leg(args):
     t0 = time.perf_counter()
     info = K.kpm_batch_tune(bt, reps=1)
     info["rtiles"], info["tiled_instances"], _ = K.kpm_batch_get_rtiles(bt)
+    info["resident"] = K.kpm_batch_get_resident(bt)[0]
     tune_s = time.perf_counter() - t0
     mu_host = K.kpm_batch_run(bt)  # host output: divergence check
     assert np.all(np.abs(mu_host) <= 1 + 1e-5)
@@ -573,6 +596,22 @@ def batch_leg(args):
     e1.record(stream)
     stream.synchronize()
     ms_single = e0.elapsed_time(e1)
+    # the resident form (each instance's vectors in its cluster's shared memory)
+    # at the smallest cluster size where the largest instance fits
+    resident = None
+    K.kpm_batch_set_resident(bt, True)
+    cmin = K.kpm_batch_get_resident(bt)[1]
+    if cmin:
+        K.kpm_batch_set_config(bt, cmin, info["chunk"], 100)
+        K.kpm_batch_run(bt, out=out, stream=stream)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(2):
+            K.kpm_batch_run(bt, out=out, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        resident = {"cluster": cmin, "clusters": K.kpm_batch_info(bt)["clusters"],
+                    "ms": e0.elapsed_time(e1) / 2}
     hbm, peak_kind = peaks()
     ach = byts / (ms / 1e3) / 1e9
     print(json.dumps({
@@ -587,13 +626,14 @@ def batch_leg(args):
                    "launch": "one persistent cluster kernel per batch, CUDA graph replay",
                    "autotuned": info, "tune_s": tune_s, "l2": "instances' vectors mostly L2-resident"},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "traffic": measured_traffic("batch_2d_256/C%d/chunk%d/clusters%d/rt%d/top%d" % (
+                     "traffic": measured_traffic("batch_2d_256/C%d/chunk%d/clusters%d/rt%d/top%d%s" % (
                          info["cluster"], info["chunk"], info["clusters"], info["rtiles"],
-                         info["tiled_instances"])),
+                         info["tiled_instances"], "/resident" if info["resident"] else "")),
                      "bytes_per_launch": byts, "peak_kind": peak_kind,
                      "note": "algorithmic bytes of all instances per batch launch; the working "
                              "set of the active instances is L2-resident, so frac can exceed 1"},
         "per_instance_calls": {"ms": ms_single, "speedup_of_batch": ms_single / ms},
+        "resident_form": resident,
         "solves_per_s": 256 / (ms / 1e3),
         "per_matvec": per_matvec(units / (ms / 1e3)),
         "gpu_launches": launches, "clocks": clk.summary()}))

@@ -286,11 +286,13 @@ kpm_status kpm_batch_run(kpm_batch b, double* mu, void* stream);
 
 /* Autotuner: times `reps` replays of every launchable untiled configuration
  * (cluster size C in {1, 2, 4, 8, 16}, traversal chunk in {2, 4, 16} passes,
- * 100 % or 50 % of the co-resident clusters), then, at the best of them and
- * at half its cluster size, R-tiling (2 or 4 tiles dividing the chunks per
- * row) of all, half, an eighth or a thirty-second of the instances, largest
- * work first; keeps the fastest for this batch and appends it to the tuning
- * cache. */
+ * 100 % or 50 % of the co-resident clusters), then the resident form
+ * (kpm_batch_set_resident) at every cluster size where it fits, and, if the
+ * global-memory form is still the fastest, R-tiling (2 or 4 tiles dividing
+ * the chunks per row) of all, half, an eighth or a thirty-second of the
+ * instances, largest work first, at the best configuration and at half its
+ * cluster size; keeps the fastest for this batch and appends it to the
+ * tuning cache. */
 kpm_status kpm_batch_tune(kpm_batch b, int reps, void* stream);
 
 /* Fixes the configuration (cluster size a power of two <= 16, chunk >= 1,
@@ -311,6 +313,24 @@ kpm_status kpm_batch_info(kpm_batch b, int* cluster, int* chunk, int* clusters_l
  * otherwise); 1 = no tiling.  An instance's moments depend only on C, its
  * tile count and the instance. */
 kpm_status kpm_batch_set_rtiles(kpm_batch b, int rtiles, int top);
+
+/* Resident form (resident = 1): each cluster keeps the two vector blocks of
+ * the instance it runs in its CTAs' shared memory for the whole solve, CTA
+ * rank k holding the rows [k P, k P + P) with P = ceil(N / C), and reads the
+ * neighbour rows held by the other CTAs through distributed shared memory;
+ * the products (Eq. (rn)) and the moment identities are unchanged and no
+ * vector row goes to global memory.  For stencil operators whose largest
+ * instance fits (KPM_EINVAL otherwise); untiled (setting resident clears the
+ * R-tiling, and R-tiling is refused while it is set).  The cluster size and
+ * the share of co-resident clusters still come from kpm_batch_set_config;
+ * the traversal chunk does not apply.  An instance's moments depend only on
+ * C and the instance, as in the global-memory form. */
+kpm_status kpm_batch_set_resident(kpm_batch b, int resident);
+
+/* Whether the resident form is set, and the smallest cluster size at which
+ * the batch's largest instance fits in shared memory (0: none does, or the
+ * operator is not a stencil). */
+kpm_status kpm_batch_get_resident(kpm_batch b, int* resident, int* min_cluster);
 
 /* Current R-tiles, the number of instances tiled, and the largest R-tiles
  * this batch admits (min(4, G)). */

@@ -25,6 +25,7 @@ struct BatchConfig {
   int frac = 100;     // percent of the co-resident clusters launched
   int rtiles = 1;     // column tiles of a tiled instance (divides the chunks per row)
   int top = 0;        // the `top` instances of largest work are tiled (<= 0: all)
+  int res = 0;        // 1: vector rows resident in the clusters' shared memory
 };
 
 constexpr int MAX_RTILES = 4;
@@ -92,12 +93,37 @@ int max_clusters(kpm_batch_s* b, int C) {
                  : max_clusters_batch_f64(b->cplx, b->proto, C);
 }
 
+// Rows per CTA the resident form needs at cluster size C (the largest instance).
+int64_t res_rows_cap(const kpm_batch_s* b, int C) {
+  int64_t cap = 1;
+  for (const kpm_handle_s* h : b->handles) cap = std::max<int64_t>(cap, (h->n + C - 1) / C);
+  return cap;
+}
+
+// Co-resident clusters of the resident form at cluster size C (0: the
+// operator is not a stencil or the largest instance does not fit).
+int max_clusters_res(kpm_batch_s* b, int C) {
+  const StepArgs& a = b->inst_tasks[b->order[0]].a;
+  const int64_t cap = res_rows_cap(b, C);
+  return b->fp32 ? max_clusters_batch_res_f32(b->cplx, a, C, cap)
+                 : max_clusters_batch_res_f64(b->cplx, a, C, cap);
+}
+
+int cfg_clusters(kpm_batch_s* b, const BatchConfig& c) {
+  return c.res ? max_clusters_res(b, c.C) : max_clusters(b, c.C);
+}
+
 kpm_status build_graph(kpm_batch_s* b, const BatchConfig& c) {
   if (b->exec && b->exec_cfg.C == c.C && b->exec_cfg.chunk == c.chunk &&
-      b->exec_cfg.frac == c.frac && b->exec_cfg.rtiles == c.rtiles && b->exec_cfg.top == c.top)
+      b->exec_cfg.frac == c.frac && b->exec_cfg.rtiles == c.rtiles && b->exec_cfg.top == c.top &&
+      b->exec_cfg.res == c.res)
     return KPM_OK;
   if (c.rtiles < 1 || c.rtiles > MAX_RTILES || b->G % c.rtiles)
     return fail(KPM_EINVAL, "R-tiles must divide the chunks per row");
+  if (c.res && c.rtiles > 1)
+    return fail(KPM_EINVAL, "the resident form runs untiled instances (R-tiles 1)");
+  if (c.res && !b->handles[0]->stencil)
+    return fail(KPM_EINVAL, "the resident form takes stencil operators only");
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
@@ -122,8 +148,10 @@ kpm_status build_graph(kpm_batch_s* b, const BatchConfig& c) {
   // the kernel's shared memory is sized for the widest task
   b->proto = b->host_tasks.back().a;
   const int ntasks = (int)b->host_tasks.size();
-  const int nclu = max_clusters(b, c.C);
-  if (nclu <= 0) return fail(KPM_EINVAL, "cluster size " + std::to_string(c.C) + " cannot be launched");
+  const int nclu = cfg_clusters(b, c);
+  if (nclu <= 0)
+    return fail(KPM_EINVAL, "cluster size " + std::to_string(c.C) + " cannot be launched" +
+                                (c.res ? " with the vectors resident in shared memory" : ""));
   const int use = std::max(1, std::min(ntasks, nclu * c.frac / 100));
   b->grid = use * c.C;
   KPM_CUDA(cudaMemcpy(b->d_tasks, b->host_tasks.data(), b->host_tasks.size() * sizeof(BatchTask),
@@ -133,11 +161,18 @@ kpm_status build_graph(kpm_batch_s* b, const BatchConfig& c) {
   cudaError_t e = cudaMemsetAsync(b->d_queue, 0, (1 + (size_t)b->count) * sizeof(int), b->cap_stream);
   if (e == cudaSuccess)
     e = cudaEventRecordWithFlags(b->ev[0], b->cap_stream, cudaEventRecordExternal);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && c.res) {
+    const int64_t cap = res_rows_cap(b, c.C);
+    e = b->fp32 ? launch_batch_res_f32(b->cplx, b->proto, b->d_tasks, ntasks, b->d_queue, b->grid,
+                                       c.C, cap, b->cap_stream)
+                : launch_batch_res_f64(b->cplx, b->proto, b->d_tasks, ntasks, b->d_queue, b->grid,
+                                       c.C, cap, b->cap_stream);
+  } else if (e == cudaSuccess) {
     e = b->fp32 ? launch_batch_f32(b->cplx, b->proto, b->d_tasks, ntasks, b->d_queue, b->grid,
                                    c.C, b->cap_stream)
                 : launch_batch_f64(b->cplx, b->proto, b->d_tasks, ntasks, b->d_queue, b->grid,
                                    c.C, b->cap_stream);
+  }
   if (e == cudaSuccess)
     e = cudaEventRecordWithFlags(b->ev[1], b->cap_stream, cudaEventRecordExternal);
   cudaGraph_t graph = nullptr;
@@ -193,10 +228,11 @@ bool cache_lookup(const std::string& key, BatchConfig* c) {
     const size_t sep = s.rfind(" = ");
     if (sep == std::string::npos || s.substr(0, sep) != key) continue;
     BatchConfig t;
-    const int got =
-        sscanf(s.c_str() + sep + 3, "%d %d %d %d %d", &t.C, &t.chunk, &t.frac, &t.rtiles, &t.top);
+    const int got = sscanf(s.c_str() + sep + 3, "%d %d %d %d %d %d", &t.C, &t.chunk, &t.frac,
+                           &t.rtiles, &t.top, &t.res);
     if (got == 3) t.rtiles = 1;  // entries written before R-tiling was tuned
-    if (got == 4) t.top = 0;
+    if (got <= 4) t.top = 0;
+    if (got <= 5) t.res = 0;     // entries written before the resident form was tuned
     if (got >= 3) {
       *c = t;
       found = true;
@@ -212,7 +248,8 @@ void cache_store(const std::string& key, const BatchConfig& c) {
   if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
   FILE* f = fopen(path.c_str(), "a");
   if (!f) return;  // an unwritable cache only costs a re-tune
-  fprintf(f, "%s = %d %d %d %d %d\n", key.c_str(), c.C, c.chunk, c.frac, c.rtiles, c.top);
+  fprintf(f, "%s = %d %d %d %d %d %d\n", key.c_str(), c.C, c.chunk, c.frac, c.rtiles, c.top,
+          c.res);
   fclose(f);
 }
 
@@ -444,7 +481,7 @@ kpm_status kpm_batch_tune(kpm_batch b, int reps, void* stream) {
   BatchConfig best;
   double best_ms = 1e30;
   auto time_cfg = [&](const BatchConfig& c) -> kpm_status {
-    if (max_clusters(b, c.C) <= 0) return KPM_OK;
+    if (cfg_clusters(b, c) <= 0) return KPM_OK;
     if (build_graph(b, c) != KPM_OK) {
       cudaGetLastError();
       return KPM_OK;
@@ -476,11 +513,24 @@ kpm_status kpm_batch_tune(kpm_batch b, int reps, void* stream) {
         kpm_status s_ = time_cfg(c);
         if (s_ != KPM_OK) return s_;
       }
-  // then R-tiling of the largest instances (all, a half, an eighth, a
-  // thirty-second of them) at the best configuration and half its cluster;
-  // a tiling is kept only if it beats the untiled best by more than 2 %
-  // (the timing noise of a few replays)
-  if (best_ms < 1e30) {
+  // the resident form (stencil operators whose largest instance fits the
+  // shared memory of a cluster): every cluster size, all or half of the
+  // co-resident clusters (the traversal chunk does not apply)
+  if (b->handles[0]->stencil)
+    for (int C : Cs)
+      for (int fr : fracs) {
+        BatchConfig c;
+        c.C = C;
+        c.frac = fr;
+        c.res = 1;
+        kpm_status s_ = time_cfg(c);
+        if (s_ != KPM_OK) return s_;
+      }
+  // then, if the global-memory form won, R-tiling of the largest instances
+  // (all, a half, an eighth, a thirty-second of them) at the best
+  // configuration and half its cluster; a tiling is kept only if it beats
+  // the untiled best by more than 2 % (the timing noise of a few replays)
+  if (best_ms < 1e30 && !best.res) {
     const BatchConfig base = best;
     const double base_ms = best_ms;
     best_ms = base_ms * 0.98;
@@ -541,8 +591,39 @@ kpm_status kpm_batch_set_rtiles(kpm_batch b, int rtiles, int top) {
   if (rtiles < 1 || rtiles > MAX_RTILES || (rtiles & (rtiles - 1)) || b->G % rtiles)
     return fail(KPM_EINVAL, "R-tiles must be 1, 2 or 4 and divide the chunks per row (" +
                                 std::to_string(b->G) + ")");
+  if (rtiles > 1 && b->cfg.res)
+    return fail(KPM_EINVAL, "the resident form runs untiled instances (R-tiles 1)");
   b->cfg.rtiles = rtiles;
   b->cfg.top = top <= 0 || top >= b->count ? 0 : top;
+  return KPM_OK;
+}
+
+kpm_status kpm_batch_set_resident(kpm_batch b, int resident) {
+  if (!b) return fail(KPM_EINVAL, "batch is NULL");
+  if (resident != 0 && resident != 1) return fail(KPM_EINVAL, "resident must be 0 or 1");
+  if (resident && !b->handles[0]->stencil)
+    return fail(KPM_EINVAL, "the resident form takes stencil operators only");
+  b->cfg.res = resident;
+  if (resident) {
+    b->cfg.rtiles = 1;
+    b->cfg.top = 0;
+  }
+  return KPM_OK;
+}
+
+kpm_status kpm_batch_get_resident(kpm_batch b, int* resident, int* min_cluster) {
+  if (!b) return fail(KPM_EINVAL, "batch is NULL");
+  if (resident) *resident = b->cfg.res;
+  if (min_cluster) {
+    KPM_CUDA(cudaSetDevice(b->device));
+    *min_cluster = 0;
+    if (b->handles[0]->stencil)
+      for (int C = 1; C <= 16; C *= 2)
+        if (max_clusters_res(b, C) > 0) {
+          *min_cluster = C;
+          break;
+        }
+  }
   return KPM_OK;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "kpm_batch.cuh"
+#include "kpm_batch_res.cuh"
 #include "kpm_step_dispatch.cuh"
 
 namespace kpm {
@@ -19,6 +20,25 @@ template <class CH>
 int clusters_batch(const StepArgs& proto, int C) {
   return visit_op<CH>(proto.rowptr == nullptr && proto.col == nullptr, proto, [&]<class OP>() {
     return batch_max_clusters<CH, OP>(C, proto.Gt, proto.Rp);
+  });
+}
+
+// The cluster-resident form: stencil operators only.
+template <class CH>
+cudaError_t run_batch_res(const StepArgs& proto, BatchTask* tasks, int ntasks, int* queue, int grid,
+                          int C, int64_t rows_cap, cudaStream_t st) {
+  if (proto.rowptr != nullptr || proto.col != nullptr) return cudaErrorNotSupported;
+  return visit_op<CH>(true, proto, [&]<class OP>() {
+    return launch_batch_res_one<CH, OP>(tasks, ntasks, queue, grid, C, proto.G, proto.Rp,
+                                        rows_cap, st);
+  });
+}
+
+template <class CH>
+int clusters_batch_res(const StepArgs& proto, int C, int64_t rows_cap) {
+  if (proto.rowptr != nullptr || proto.col != nullptr) return 0;
+  return visit_op<CH>(true, proto, [&]<class OP>() {
+    return batch_res_max_clusters<CH, OP>(C, proto.G, proto.Rp, rows_cap);
   });
 }
 

@@ -132,6 +132,14 @@ cudaError_t launch_batch_f64(bool cplx, const StepArgs& proto, BatchTask* tasks,
                              int* queue, int grid, int C, cudaStream_t st);
 int max_clusters_batch_f32(bool cplx, const StepArgs& proto, int C);
 int max_clusters_batch_f64(bool cplx, const StepArgs& proto, int C);
+// Cluster-resident form (vector rows in the clusters' shared memory, at most
+// rows_cap rows per CTA; stencil operators only)
+cudaError_t launch_batch_res_f32(bool cplx, const StepArgs& proto, BatchTask* tasks, int ntasks,
+                                 int* queue, int grid, int C, int64_t rows_cap, cudaStream_t st);
+cudaError_t launch_batch_res_f64(bool cplx, const StepArgs& proto, BatchTask* tasks, int ntasks,
+                                 int* queue, int grid, int C, int64_t rows_cap, cudaStream_t st);
+int max_clusters_batch_res_f32(bool cplx, const StepArgs& proto, int C, int64_t rows_cap);
+int max_clusters_batch_res_f64(bool cplx, const StepArgs& proto, int C, int64_t rows_cap);
 }  // namespace kpm
 
 // The handle (opaque to callers).

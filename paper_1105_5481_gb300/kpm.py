@@ -100,6 +100,8 @@ def lib() -> C.CDLL:
         L.kpm_batch_set_config.argtypes = [h, C.c_int, C.c_int, C.c_int]
         L.kpm_batch_info.argtypes = [h, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_double)]
+        L.kpm_batch_set_resident.argtypes = [h, C.c_int]
+        L.kpm_batch_get_resident.argtypes = [h, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.kpm_batch_destroy.argtypes = [h]
         L.kpm_batch_destroy.restype = None
         L.kpm_server_create.argtypes = [C.c_size_t, C.c_int, C.c_int, C.POINTER(h)]
@@ -120,7 +122,8 @@ def lib() -> C.CDLL:
                      "kpm_moments", "kpm_dos", "kpm_info", "kpm_step_timing",
                      "kpm_moments_csr_noalloc", "kpm_batch_create", "kpm_batch_run", "kpm_batch_tune",
                      "kpm_batch_set_config", "kpm_batch_info", "kpm_batch_set_rtiles",
-                     "kpm_batch_get_rtiles", "kpm_server_create",
+                     "kpm_batch_get_rtiles", "kpm_batch_set_resident", "kpm_batch_get_resident",
+                     "kpm_server_create",
                      "kpm_server_submit", "kpm_server_wait", "kpm_server_poll", "kpm_server_cancel",
                      "kpm_server_stats"):
             getattr(L, name).restype = C.c_int
@@ -493,6 +496,18 @@ def kpm_batch_get_rtiles(bt: Batch):
     rt, tp, mx = C.c_int(), C.c_int(), C.c_int()
     _check(lib().kpm_batch_get_rtiles(bt.raw, C.byref(rt), C.byref(tp), C.byref(mx)))
     return rt.value, tp.value, mx.value
+
+
+def kpm_batch_set_resident(bt: Batch, resident=True):
+    """Keep every instance's vector blocks in its cluster's shared memory."""
+    _check(lib().kpm_batch_set_resident(bt.raw, int(bool(resident))))
+
+
+def kpm_batch_get_resident(bt: Batch):
+    """(resident form set, smallest cluster size at which the batch fits; 0: none)."""
+    on, cmin = C.c_int(), C.c_int()
+    _check(lib().kpm_batch_get_resident(bt.raw, C.byref(on), C.byref(cmin)))
+    return bool(on.value), cmin.value
 
 
 def kpm_batch_info(bt: Batch):

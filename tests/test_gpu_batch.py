@@ -1,6 +1,7 @@
 """The batched persistent launch: every instance against the oracle, the same
 instance alone and in a mix (bitwise, for a fixed cluster size), all cluster
-sizes, R-tiling (an instance's columns split into independent tasks), and the
+sizes, R-tiling (an instance's columns split into independent tasks), the
+resident form (vector rows kept in the clusters' shared memory), and the
 autotuner with its on-disk cache."""
 import numpy as np
 import pytest
@@ -155,13 +156,124 @@ def test_autotuner_writes_and_reuses_its_cache(K, tmp_path, monkeypatch):
         info = K.kpm_batch_tune(bt, reps=1)
         mu = K.kpm_batch_run(bt)
         tiles, tiled, _ = K.kpm_batch_get_rtiles(bt)
+        resident = K.kpm_batch_get_resident(bt)[0]
+    assert not (resident and tiles > 1)
     text = cache.read_text()
     assert "batch|" in text and f"= {info['cluster']} {info['chunk']}" in text
     fields = text.strip().splitlines()[-1].split(" = ")[1].split()
     assert int(fields[3]) == tiles and (tiles == 1 or int(fields[4]) in (0, tiled))
+    assert int(fields[5]) == int(resident)
     with make_batch(K, insts, "fp32") as bt2:
         info2 = K.kpm_batch_info(bt2)
         mu2 = K.kpm_batch_run(bt2)
         assert K.kpm_batch_get_rtiles(bt2)[:2] == (tiles, tiled)
+        assert K.kpm_batch_get_resident(bt2)[0] == resident
     assert (info2["cluster"], info2["chunk"]) == (info["cluster"], info["chunk"])
     assert np.array_equal(mu, mu2)
+
+
+# ---------------------------------------------------------------- resident form
+# Each cluster keeps its instance's two vector blocks in shared memory (CTA k
+# owns rows [kP, kP + P), P = ceil(N / C)) and reads the other CTAs' rows
+# through distributed shared memory.
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_resident_instances_match_oracle(K, prec):
+    insts = instances()
+    with make_batch(K, insts, prec) as bt:
+        K.kpm_batch_set_resident(bt, True)
+        on, cmin = K.kpm_batch_get_resident(bt)
+        # largest instance 48 x 48, R = 16: 2 x 295 KB of FP64 rows fit 4 CTAs
+        assert on and 1 <= cmin <= 4
+        K.kpm_batch_set_config(bt, 4, 4, 100)
+        parts = bt.split(K.kpm_batch_run(bt))
+        again = bt.split(K.kpm_batch_run(bt))
+    for x, mu, mu2 in zip(insts, parts, again):
+        mu_o, _ = O.moments_doubling(x["H"], x["a"], x["b"], I.rademacher_block(x["seed"], x["H"].n, 16),
+                                     x["M"])
+        assert np.abs(mu - mu_o).max() <= TOL[prec]
+        assert np.array_equal(mu, mu2)
+
+
+@pytest.mark.parametrize("C", [1, 2, 4, 8, 16])
+def test_resident_every_cluster_size_alone_and_in_the_mix(K, C):
+    # C = 16 leaves the last CTAs of the 5 x 5 instance without rows
+    insts = instances(8)
+    with make_batch(K, insts, "fp32") as bt:
+        K.kpm_batch_set_resident(bt, True)
+        assert K.kpm_batch_get_resident(bt)[1] == 1  # 40 x 40, R = 16 FP32: 2 x 100 KB
+        K.kpm_batch_set_config(bt, C, 4, 50)
+        parts = bt.split(K.kpm_batch_run(bt))
+        assert K.kpm_batch_info(bt)["cluster"] == C
+    for x, mu in zip(insts, parts):
+        mu_o, _ = O.moments_doubling(x["H"], x["a"], x["b"], I.rademacher_block(x["seed"], x["H"].n, 16),
+                                     x["M"])
+        assert np.abs(mu - mu_o).max() <= 1e-5
+    for k in (0, 5):
+        with make_batch(K, [insts[k]], "fp32") as b1:
+            K.kpm_batch_set_resident(b1, True)
+            K.kpm_batch_set_config(b1, C, 4, 100)
+            assert np.array_equal(K.kpm_batch_run(b1), parts[k])
+
+
+@pytest.mark.parametrize("prec,R,tol", [("fp32", 16, 1e-5), ("fp64", 8, 1e-10)])
+def test_resident_complex_hoppings_open_edge_3d(K, prec, R, tol):
+    # spin-derived complex hoppings, on-site disorder, one open direction;
+    # random-phase vectors (R = 16 complex FP32: 4 chunks per row)
+    L, periodic = (6, 5, 4), (True, False, True)
+    N = 120
+    hop = I.spin_hoppings(L, *I.spins(7, N))
+    on = I.onsite_disorder(8, N, 1.0)
+    H = O.lattice_hamiltonian(L, periodic=periodic, onsite=on, hop=hop)
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    with K.kpm_create_stencil(3, L, periodic=periodic, onsite=on, hop=hop, complex_=True) as h:
+        with K.kpm_batch_create([h, h], [40, 62], R, [a, a], [b, b], [5, 6], precision=prec) as bt:
+            K.kpm_batch_set_resident(bt, True)
+            K.kpm_batch_set_config(bt, 4, 4, 100)
+            parts = bt.split(K.kpm_batch_run(bt))
+    for M, seed, mu in zip((40, 62), (5, 6), parts):
+        mu_o, _ = O.moments_doubling(H, a, b, I.phase_block(seed, N, R), M)
+        assert np.abs(mu - mu_o).max() <= tol
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_resident_chain_across_ctas(K, periodic):
+    # a 1D chain of 50 sites on 2 CTAs: the bonds 24-25 (and 49-0 when
+    # periodic) join rows held by different CTAs
+    N = 50
+    on = I.onsite_disorder(9, N, 2.0)
+    H = O.lattice_hamiltonian((N,), periodic=(periodic,), onsite=on)
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    with K.kpm_create_stencil(1, (N,), periodic=(periodic,), onsite=on) as h:
+        with K.kpm_batch_create([h], [64], 8, [a], [b], [11], precision="fp64") as bt:
+            K.kpm_batch_set_resident(bt, True)
+            K.kpm_batch_set_config(bt, 2, 4, 100)
+            mu = K.kpm_batch_run(bt)
+    mu_o, _ = O.moments_doubling(H, a, b, I.rademacher_block(11, N, 8), 64)
+    assert np.abs(mu - mu_o).max() <= 1e-10
+
+
+def test_resident_refusals(K):
+    # too large for any cluster: 128 x 128, R = 16 FP64 is 2 x 2 MB of rows
+    L = (128, 128)
+    with K.kpm_create_stencil(2, L) as h:
+        with K.kpm_batch_create([h], [8], 16, [4.1], [0.0], [1], precision="fp64") as bt:
+            K.kpm_batch_set_resident(bt, True)
+            assert K.kpm_batch_get_resident(bt) == (True, 0)
+            with pytest.raises(K.KPMError) as e:
+                K.kpm_batch_run(bt)
+            assert e.value.status == K.KPM_EINVAL
+            with pytest.raises(K.KPMError) as e:
+                K.kpm_batch_set_rtiles(bt, 2)
+            assert e.value.status == K.KPM_EINVAL
+            K.kpm_batch_set_resident(bt, False)
+            assert np.abs(K.kpm_batch_run(bt)[0] - 1.0) <= 1e-12
+    # CSR operators have no resident form
+    Hs = O.lattice_hamiltonian((6, 6))
+    with K.kpm_create_csr(Hs.n, Hs.rowptr, Hs.col, Hs.val) as h:
+        with K.kpm_batch_create([h], [8], 8, [4.1], [0.0], [1], precision="fp64") as bt:
+            with pytest.raises(K.KPMError) as e:
+                K.kpm_batch_set_resident(bt, True)
+            assert e.value.status == K.KPM_EINVAL
+            assert K.kpm_batch_get_resident(bt) == (False, 0)
