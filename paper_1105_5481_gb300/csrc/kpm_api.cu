@@ -201,7 +201,12 @@ void plan_grid(const kpm_handle_s* h, bool fp32, StepArgs& a, int* block, int* g
     return;
   }
   const int G = a.Gt;            // chunks per row handled by one CTA (<= BLOCK)
-  const int blk = BLOCK;
+  // Lattices too small to give every SM a one-pass CTA of BLOCK threads take
+  // smaller CTAs (down to one warp, at least one row per pass), so that the
+  // step's arithmetic spreads over more SMs: GB300's FP64 pipe (2 FMA per SM
+  // and clock) otherwise makes the few busy SMs the limit of each step.
+  int blk = BLOCK;
+  while (blk / 2 >= std::max(32, G) && (h->n * G + blk - 1) / blk < h->num_sms) blk /= 2;
   const int spi = blk / G;
   int occ = fp32 ? occ_step_f32(h->stencil, h->cplx, a, blk)
                  : occ_step_f64(h->stencil, h->cplx, a, blk);
