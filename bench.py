@@ -51,6 +51,7 @@ STEP_SOURCES = ["paper_1105_5481_gb300/csrc/kpm_step.cuh",
                 "paper_1105_5481_gb300/csrc/kpm_args.h"]
 BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_batch_res.cuh",
+                                "paper_1105_5481_gb300/csrc/kpm_chunk16.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_batch_dispatch.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_batch_f32.cu"]
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture,
@@ -247,7 +248,7 @@ def csr_handle(K, w):
     return K.kpm_create_csr(rp.size - 1, rp, col, val, complex_=True)
 
 
-def profile_run(prec, workload, batch_chunk=2):
+def profile_run(prec, workload, batch_chunk=2, batch_cluster=4, batch_chunk_bytes=32):
     """Two solves of the workload with Gershgorin bounds (no Lanczos products, so
     the only fused-step launches are those of the two solves); prec "bounds":
     three spectral-bound estimates of the headline lattice (Gershgorin and the
@@ -276,7 +277,8 @@ def profile_run(prec, workload, batch_chunk=2):
         ab = [K.kpm_bounds(h, 0, WORKLOAD["pad_eps"])[2:] for h in hs]
         with K.kpm_batch_create(hs, [x["M"] for x in insts], 16, [p[0] for p in ab],
                                 [p[1] for p in ab], [x["seed"] for x in insts], prec) as bt:
-            K.kpm_batch_set_config(bt, 4, batch_chunk, 100)
+            K.kpm_batch_set_chunk_bytes(bt, batch_chunk_bytes)
+            K.kpm_batch_set_config(bt, batch_cluster, batch_chunk, 100)
             for _ in range(2):
                 mu = K.kpm_batch_run(bt)
         print(json.dumps({"profile": prec, "workload": workload, "mu0": float(mu[0])}))
@@ -562,6 +564,7 @@ def batch_leg(args):
     info = K.kpm_batch_tune(bt, reps=1)
     info["rtiles"], info["tiled_instances"], _ = K.kpm_batch_get_rtiles(bt)
     info["resident"] = K.kpm_batch_get_resident(bt)[0]
+    info["chunk_bytes"], info["threads_per_row"] = K.kpm_batch_get_chunk_bytes(bt)
     tune_s = time.perf_counter() - t0
     mu_host = K.kpm_batch_run(bt)  # host output: divergence check
     assert np.all(np.abs(mu_host) <= 1 + 1e-5)
@@ -628,7 +631,8 @@ def batch_leg(args):
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                      "traffic": measured_traffic("batch_2d_256/C%d/chunk%d/clusters%d/rt%d/top%d%s" % (
                          info["cluster"], info["chunk"], info["clusters"], info["rtiles"],
-                         info["tiled_instances"], "/resident" if info["resident"] else "")),
+                         info["tiled_instances"], ("/resident" if info["resident"] else "") +
+                         ("/chunk16B" if info["chunk_bytes"] == 16 else ""))),
                      "bytes_per_launch": byts, "peak_kind": peak_kind,
                      "note": "algorithmic bytes of all instances per batch launch; the working "
                              "set of the active instances is L2-resident, so frac can exceed 1"},
@@ -749,7 +753,11 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-chunk", type=int, default=2,
-                    help="--profile with the batch workload: passes per chunk (clusters of 4)")
+                    help="--profile with the batch workload: passes per chunk")
+    ap.add_argument("--batch-cluster", type=int, default=4,
+                    help="--profile with the batch workload: CTAs per cluster")
+    ap.add_argument("--batch-chunk-bytes", type=int, default=32, choices=[16, 32],
+                    help="--profile with the batch workload: bytes of a row per thread")
     ap.add_argument("--workload", default="cubic_spin_L64",
                     choices=["cubic_spin_L64", "csr_spin_dilute_L160", "batch_2d_256",
                              "serve_poisson", "square_L32_fp64", "dense_wigner_D4096"],
@@ -762,7 +770,8 @@ def main():
     if args.impl == "reference":
         return reference_arm(args)
     if args.profile:
-        return profile_run(args.profile, args.workload, args.batch_chunk)
+        return profile_run(args.profile, args.workload, args.batch_chunk, args.batch_cluster,
+                           args.batch_chunk_bytes)
     if args.workload == "square_L32_fp64":
         return square_leg(args)
     if args.workload == "csr_spin_dilute_L160":

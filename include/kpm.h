@@ -286,7 +286,9 @@ kpm_status kpm_batch_run(kpm_batch b, double* mu, void* stream);
 
 /* Autotuner: times `reps` replays of every launchable untiled configuration
  * (cluster size C in {1, 2, 4, 8, 16}, traversal chunk in {2, 4, 16} passes,
- * 100 % or 50 % of the co-resident clusters), then the resident form
+ * 100 % or 50 % of the co-resident clusters), then twice the threads per row
+ * (kpm_batch_set_chunk_bytes 16, real FP32 stencils) at every cluster size
+ * and traversal chunk, then the resident form
  * (kpm_batch_set_resident) at every cluster size where it fits, and, if the
  * global-memory form is still the fastest, R-tiling (2 or 4 tiles dividing
  * the chunks per row) of all, half, an eighth or a thirty-second of the
@@ -313,6 +315,19 @@ kpm_status kpm_batch_info(kpm_batch b, int* cluster, int* chunk, int* clusters_l
  * otherwise); 1 = no tiling.  An instance's moments depend only on C, its
  * tile count and the instance. */
 kpm_status kpm_batch_set_rtiles(kpm_batch b, int rtiles, int top);
+
+/* Threads per row: each thread moves one chunk of `bytes` bytes of a row per
+ * product, so a row of Rp columns takes Rp*4/bytes threads (real FP32).
+ * bytes = 32 (the default: 8 real or 4 complex FP32 columns per thread) or
+ * 16 (4 real columns: twice the threads per row, half the registers of
+ * vector data per thread); 16 needs a real FP32 batch of stencil operators
+ * in the global-memory form (KPM_EINVAL otherwise).  FP64 batches always
+ * move 16-byte chunks (2 real or 1 complex column).  The row layout is the
+ * same for both widths. */
+kpm_status kpm_batch_set_chunk_bytes(kpm_batch b, int bytes);
+
+/* Current chunk width in bytes and threads per row (chunks per row). */
+kpm_status kpm_batch_get_chunk_bytes(kpm_batch b, int* bytes, int* threads_per_row);
 
 /* Resident form (resident = 1): each cluster keeps the two vector blocks of
  * the instance it runs in its CTAs' shared memory for the whole solve, CTA

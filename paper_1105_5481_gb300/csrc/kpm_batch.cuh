@@ -54,9 +54,22 @@ struct BatchTask {
   int* tiles_done;    // per-instance count of finished tiles (zeroed per launch)
 };
 
+// Resident CTAs per SM requested from the register allocator, per chunk
+// policy (the 16-byte chunk's smaller vector registers allow three).
+template <class CH>
+struct BatchMinBlocks {
+  static constexpr int value = KPM_BATCH_MIN_BLOCKS;
+};
+template <bool NC>
+struct ChunkF32h;
+template <bool NC>
+struct BatchMinBlocks<ChunkF32h<NC>> {
+  static constexpr int value = 3;
+};
+
 template <class CH, class OP>
-__global__ void __launch_bounds__(256, KPM_BATCH_MIN_BLOCKS) batch_kernel(BatchTask* tasks, int ntasks,
-                                                       int* queue) {
+__global__ void __launch_bounds__(256, BatchMinBlocks<CH>::value)
+    batch_kernel(BatchTask* tasks, int ntasks, int* queue) {
   using T = typename CH::T;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();

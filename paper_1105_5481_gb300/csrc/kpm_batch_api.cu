@@ -26,6 +26,7 @@ struct BatchConfig {
   int rtiles = 1;     // column tiles of a tiled instance (divides the chunks per row)
   int top = 0;        // the `top` instances of largest work are tiled (<= 0: all)
   int res = 0;        // 1: vector rows resident in the clusters' shared memory
+  int tpr = 1;        // threads per row relative to the 32-byte chunk (2: 16-byte chunks)
 };
 
 constexpr int MAX_RTILES = 4;
@@ -88,9 +89,24 @@ void plan_instance(StepArgs& a, const kpm_handle_s* h, int chunk) {
   a.chunk = chunk;
 }
 
-int max_clusters(kpm_batch_s* b, int C) {
-  return b->fp32 ? max_clusters_batch_f32(b->cplx, b->proto, C)
-                 : max_clusters_batch_f64(b->cplx, b->proto, C);
+// Whether 16-byte chunks (twice the threads per row) apply: real FP32 stencils.
+bool half_chunks_ok(const kpm_batch_s* b) {
+  return b->fp32 && !b->cplx && b->handles[0]->stencil;
+}
+
+// Launch prototype of configuration c: chunks per row and per task.
+StepArgs cfg_proto(const kpm_batch_s* b, const BatchConfig& c) {
+  StepArgs a = b->inst_tasks[b->order[0]].a;
+  a.G = b->G * c.tpr;
+  a.Gt = a.G / std::max(1, c.rtiles);
+  return a;
+}
+
+int max_clusters(kpm_batch_s* b, const BatchConfig& c) {
+  const StepArgs a = cfg_proto(b, c);
+  if (c.tpr == 2) return max_clusters_batch_f32h(a, c.C);
+  return b->fp32 ? max_clusters_batch_f32(b->cplx, a, c.C)
+                 : max_clusters_batch_f64(b->cplx, a, c.C);
 }
 
 // Rows per CTA the resident form needs at cluster size C (the largest instance).
@@ -110,15 +126,19 @@ int max_clusters_res(kpm_batch_s* b, int C) {
 }
 
 int cfg_clusters(kpm_batch_s* b, const BatchConfig& c) {
-  return c.res ? max_clusters_res(b, c.C) : max_clusters(b, c.C);
+  return c.res ? max_clusters_res(b, c.C) : max_clusters(b, c);
 }
 
 kpm_status build_graph(kpm_batch_s* b, const BatchConfig& c) {
   if (b->exec && b->exec_cfg.C == c.C && b->exec_cfg.chunk == c.chunk &&
       b->exec_cfg.frac == c.frac && b->exec_cfg.rtiles == c.rtiles && b->exec_cfg.top == c.top &&
-      b->exec_cfg.res == c.res)
+      b->exec_cfg.res == c.res && b->exec_cfg.tpr == c.tpr)
     return KPM_OK;
-  if (c.rtiles < 1 || c.rtiles > MAX_RTILES || b->G % c.rtiles)
+  if (c.tpr != 1 && (c.tpr != 2 || !half_chunks_ok(b) || c.res))
+    return fail(KPM_EINVAL,
+                "twice the threads per row needs a real FP32 stencil batch in the global-memory form");
+  const int Geff = b->G * c.tpr;
+  if (c.rtiles < 1 || c.rtiles > MAX_RTILES || Geff % c.rtiles)
     return fail(KPM_EINVAL, "R-tiles must divide the chunks per row");
   if (c.res && c.rtiles > 1)
     return fail(KPM_EINVAL, "the resident form runs untiled instances (R-tiles 1)");
@@ -137,7 +157,8 @@ kpm_status build_graph(kpm_batch_s* b, const BatchConfig& c) {
     const int T = k < ntiled ? c.rtiles : 1;
     for (int j = 0; j < T; ++j) {
       BatchTask t = b->inst_tasks[i];
-      t.a.Gt = b->G / T;
+      t.a.G = Geff;
+      t.a.Gt = Geff / T;
       plan_instance(t.a, b->handles[i], c.chunk);
       t.ycol = j;
       t.ntiles = T;
@@ -167,6 +188,8 @@ kpm_status build_graph(kpm_batch_s* b, const BatchConfig& c) {
                                        c.C, cap, b->cap_stream)
                 : launch_batch_res_f64(b->cplx, b->proto, b->d_tasks, ntasks, b->d_queue, b->grid,
                                        c.C, cap, b->cap_stream);
+  } else if (e == cudaSuccess && c.tpr == 2) {
+    e = launch_batch_f32h(b->proto, b->d_tasks, ntasks, b->d_queue, b->grid, c.C, b->cap_stream);
   } else if (e == cudaSuccess) {
     e = b->fp32 ? launch_batch_f32(b->cplx, b->proto, b->d_tasks, ntasks, b->d_queue, b->grid,
                                    c.C, b->cap_stream)
@@ -228,11 +251,12 @@ bool cache_lookup(const std::string& key, BatchConfig* c) {
     const size_t sep = s.rfind(" = ");
     if (sep == std::string::npos || s.substr(0, sep) != key) continue;
     BatchConfig t;
-    const int got = sscanf(s.c_str() + sep + 3, "%d %d %d %d %d %d", &t.C, &t.chunk, &t.frac,
-                           &t.rtiles, &t.top, &t.res);
+    const int got = sscanf(s.c_str() + sep + 3, "%d %d %d %d %d %d %d", &t.C, &t.chunk, &t.frac,
+                           &t.rtiles, &t.top, &t.res, &t.tpr);
     if (got == 3) t.rtiles = 1;  // entries written before R-tiling was tuned
     if (got <= 4) t.top = 0;
     if (got <= 5) t.res = 0;     // entries written before the resident form was tuned
+    if (got <= 6) t.tpr = 1;     // entries written before threads per row were tuned
     if (got >= 3) {
       *c = t;
       found = true;
@@ -248,8 +272,8 @@ void cache_store(const std::string& key, const BatchConfig& c) {
   if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
   FILE* f = fopen(path.c_str(), "a");
   if (!f) return;  // an unwritable cache only costs a re-tune
-  fprintf(f, "%s = %d %d %d %d %d %d\n", key.c_str(), c.C, c.chunk, c.frac, c.rtiles, c.top,
-          c.res);
+  fprintf(f, "%s = %d %d %d %d %d %d %d\n", key.c_str(), c.C, c.chunk, c.frac, c.rtiles, c.top,
+          c.res, c.tpr);
   fclose(f);
 }
 
@@ -513,6 +537,18 @@ kpm_status kpm_batch_tune(kpm_batch b, int reps, void* stream) {
         kpm_status s_ = time_cfg(c);
         if (s_ != KPM_OK) return s_;
       }
+  // twice the threads per row (16-byte chunks; real FP32 stencils): every
+  // cluster size and chunk, all co-resident clusters
+  if (half_chunks_ok(b))
+    for (int C : Cs)
+      for (int ch : chunks) {
+        BatchConfig c;
+        c.C = C;
+        c.chunk = ch;
+        c.tpr = 2;
+        kpm_status s_ = time_cfg(c);
+        if (s_ != KPM_OK) return s_;
+      }
   // the resident form (stencil operators whose largest instance fits the
   // shared memory of a cluster): every cluster size, all or half of the
   // co-resident clusters (the traversal chunk does not apply)
@@ -536,7 +572,7 @@ kpm_status kpm_batch_tune(kpm_batch b, int reps, void* stream) {
     best_ms = base_ms * 0.98;
     for (int C : {base.C, base.C / 2}) {
       if (C < 1) continue;
-      for (int rt = 2; rt <= MAX_RTILES && b->G % rt == 0; rt *= 2)
+      for (int rt = 2; rt <= MAX_RTILES && (b->G * base.tpr) % rt == 0; rt *= 2)
         for (int div : {1, 2, 8, 32}) {
           const int top = std::max(1, b->count / div);
           if (div > 1 && top == b->count) continue;
@@ -588,13 +624,34 @@ kpm_status kpm_batch_set_config(kpm_batch b, int cluster, int chunk, int percent
 
 kpm_status kpm_batch_set_rtiles(kpm_batch b, int rtiles, int top) {
   if (!b) return fail(KPM_EINVAL, "batch is NULL");
-  if (rtiles < 1 || rtiles > MAX_RTILES || (rtiles & (rtiles - 1)) || b->G % rtiles)
+  if (rtiles < 1 || rtiles > MAX_RTILES || (rtiles & (rtiles - 1)) || (b->G * b->cfg.tpr) % rtiles)
     return fail(KPM_EINVAL, "R-tiles must be 1, 2 or 4 and divide the chunks per row (" +
-                                std::to_string(b->G) + ")");
+                                std::to_string(b->G * b->cfg.tpr) + ")");
   if (rtiles > 1 && b->cfg.res)
     return fail(KPM_EINVAL, "the resident form runs untiled instances (R-tiles 1)");
   b->cfg.rtiles = rtiles;
   b->cfg.top = top <= 0 || top >= b->count ? 0 : top;
+  return KPM_OK;
+}
+
+kpm_status kpm_batch_set_chunk_bytes(kpm_batch b, int bytes) {
+  if (!b) return fail(KPM_EINVAL, "batch is NULL");
+  if (bytes != 32 && bytes != 16) return fail(KPM_EINVAL, "chunk bytes must be 16 or 32");
+  const int tpr = bytes == 16 ? 2 : 1;
+  if (tpr == 2 && !half_chunks_ok(b))
+    return fail(KPM_EINVAL, "16-byte chunks take real FP32 vectors and stencil operators");
+  if (tpr == 2 && b->cfg.res)
+    return fail(KPM_EINVAL, "the resident form runs 32-byte chunks");
+  if ((b->G * tpr) % b->cfg.rtiles)
+    return fail(KPM_EINVAL, "the current R-tiles do not divide the chunks per row");
+  b->cfg.tpr = tpr;
+  return KPM_OK;
+}
+
+kpm_status kpm_batch_get_chunk_bytes(kpm_batch b, int* bytes, int* threads_per_row) {
+  if (!b) return fail(KPM_EINVAL, "batch is NULL");
+  if (bytes) *bytes = b->cfg.tpr == 2 ? 16 : (b->fp32 ? 32 : 16);
+  if (threads_per_row) *threads_per_row = b->G * b->cfg.tpr;
   return KPM_OK;
 }
 
@@ -603,6 +660,8 @@ kpm_status kpm_batch_set_resident(kpm_batch b, int resident) {
   if (resident != 0 && resident != 1) return fail(KPM_EINVAL, "resident must be 0 or 1");
   if (resident && !b->handles[0]->stencil)
     return fail(KPM_EINVAL, "the resident form takes stencil operators only");
+  if (resident && b->cfg.tpr != 1)
+    return fail(KPM_EINVAL, "the resident form runs 32-byte chunks");
   b->cfg.res = resident;
   if (resident) {
     b->cfg.rtiles = 1;
@@ -631,7 +690,7 @@ kpm_status kpm_batch_get_rtiles(kpm_batch b, int* rtiles, int* top, int* max_rti
   if (!b) return fail(KPM_EINVAL, "batch is NULL");
   if (rtiles) *rtiles = b->cfg.rtiles;
   if (top) *top = b->cfg.rtiles > 1 ? (b->cfg.top <= 0 ? b->count : b->cfg.top) : 0;
-  if (max_rtiles) *max_rtiles = std::min(MAX_RTILES, b->G);
+  if (max_rtiles) *max_rtiles = std::min(MAX_RTILES, b->G * b->cfg.tpr);
   return KPM_OK;
 }
 

@@ -132,6 +132,10 @@ cudaError_t launch_batch_f64(bool cplx, const StepArgs& proto, BatchTask* tasks,
                              int* queue, int grid, int C, cudaStream_t st);
 int max_clusters_batch_f32(bool cplx, const StepArgs& proto, int C);
 int max_clusters_batch_f64(bool cplx, const StepArgs& proto, int C);
+// 16-byte chunks of a real FP32 block (twice the threads per row; stencil operators)
+cudaError_t launch_batch_f32h(const StepArgs& proto, BatchTask* tasks, int ntasks, int* queue,
+                              int grid, int C, cudaStream_t st);
+int max_clusters_batch_f32h(const StepArgs& proto, int C);
 // Cluster-resident form (vector rows in the clusters' shared memory, at most
 // rows_cap rows per CTA; stencil operators only)
 cudaError_t launch_batch_res_f32(bool cplx, const StepArgs& proto, BatchTask* tasks, int ntasks,

@@ -100,6 +100,8 @@ def lib() -> C.CDLL:
         L.kpm_batch_set_config.argtypes = [h, C.c_int, C.c_int, C.c_int]
         L.kpm_batch_info.argtypes = [h, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_double)]
+        L.kpm_batch_set_chunk_bytes.argtypes = [h, C.c_int]
+        L.kpm_batch_get_chunk_bytes.argtypes = [h, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.kpm_batch_set_resident.argtypes = [h, C.c_int]
         L.kpm_batch_get_resident.argtypes = [h, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.kpm_batch_destroy.argtypes = [h]
@@ -123,6 +125,7 @@ def lib() -> C.CDLL:
                      "kpm_moments_csr_noalloc", "kpm_batch_create", "kpm_batch_run", "kpm_batch_tune",
                      "kpm_batch_set_config", "kpm_batch_info", "kpm_batch_set_rtiles",
                      "kpm_batch_get_rtiles", "kpm_batch_set_resident", "kpm_batch_get_resident",
+                     "kpm_batch_set_chunk_bytes", "kpm_batch_get_chunk_bytes",
                      "kpm_server_create",
                      "kpm_server_submit", "kpm_server_wait", "kpm_server_poll", "kpm_server_cancel",
                      "kpm_server_stats"):
@@ -496,6 +499,18 @@ def kpm_batch_get_rtiles(bt: Batch):
     rt, tp, mx = C.c_int(), C.c_int(), C.c_int()
     _check(lib().kpm_batch_get_rtiles(bt.raw, C.byref(rt), C.byref(tp), C.byref(mx)))
     return rt.value, tp.value, mx.value
+
+
+def kpm_batch_set_chunk_bytes(bt: Batch, nbytes):
+    """Bytes of a row each thread moves per product (32 or 16: twice the threads per row)."""
+    _check(lib().kpm_batch_set_chunk_bytes(bt.raw, int(nbytes)))
+
+
+def kpm_batch_get_chunk_bytes(bt: Batch):
+    """(chunk bytes, threads per row)."""
+    nb, tpr = C.c_int(), C.c_int()
+    _check(lib().kpm_batch_get_chunk_bytes(bt.raw, C.byref(nb), C.byref(tpr)))
+    return nb.value, tpr.value
 
 
 def kpm_batch_set_resident(bt: Batch, resident=True):

@@ -157,17 +157,20 @@ def test_autotuner_writes_and_reuses_its_cache(K, tmp_path, monkeypatch):
         mu = K.kpm_batch_run(bt)
         tiles, tiled, _ = K.kpm_batch_get_rtiles(bt)
         resident = K.kpm_batch_get_resident(bt)[0]
+        chunk_bytes = K.kpm_batch_get_chunk_bytes(bt)[0]
     assert not (resident and tiles > 1)
     text = cache.read_text()
     assert "batch|" in text and f"= {info['cluster']} {info['chunk']}" in text
     fields = text.strip().splitlines()[-1].split(" = ")[1].split()
     assert int(fields[3]) == tiles and (tiles == 1 or int(fields[4]) in (0, tiled))
     assert int(fields[5]) == int(resident)
+    assert int(fields[6]) == {32: 1, 16: 2}[chunk_bytes]
     with make_batch(K, insts, "fp32") as bt2:
         info2 = K.kpm_batch_info(bt2)
         mu2 = K.kpm_batch_run(bt2)
         assert K.kpm_batch_get_rtiles(bt2)[:2] == (tiles, tiled)
         assert K.kpm_batch_get_resident(bt2)[0] == resident
+        assert K.kpm_batch_get_chunk_bytes(bt2)[0] == chunk_bytes
     assert (info2["cluster"], info2["chunk"]) == (info["cluster"], info["chunk"])
     assert np.array_equal(mu, mu2)
 
@@ -277,3 +280,84 @@ def test_resident_refusals(K):
                 K.kpm_batch_set_resident(bt, True)
             assert e.value.status == K.KPM_EINVAL
             assert K.kpm_batch_get_resident(bt) == (False, 0)
+
+
+# ---------------------------------------------------------------- threads per row
+# 16-byte chunks: each thread moves 4 real FP32 columns of a row, so a row
+# takes twice the threads of the default 32-byte chunk (same row layout).
+
+
+@pytest.mark.parametrize("R", [16, 13, 32])
+@pytest.mark.parametrize("C", [1, 4])
+def test_half_chunks_match_oracle(K, R, C):
+    insts = instances(8)
+    Rp = {16: 16, 13: 16, 32: 32}[R]   # padded to a power of two of 8-column chunks
+    with make_batch(K, insts, "fp32", R) as bt:
+        assert K.kpm_batch_get_chunk_bytes(bt) == (32, Rp // 8)
+        K.kpm_batch_set_chunk_bytes(bt, 16)
+        assert K.kpm_batch_get_chunk_bytes(bt) == (16, Rp // 4)
+        K.kpm_batch_set_config(bt, C, 4, 100)
+        parts = bt.split(K.kpm_batch_run(bt))
+        again = bt.split(K.kpm_batch_run(bt))
+    for x, mu, mu2 in zip(insts, parts, again):
+        mu_o, _ = O.moments_doubling(x["H"], x["a"], x["b"], I.rademacher_block(x["seed"], x["H"].n, R),
+                                     x["M"])
+        assert np.abs(mu - mu_o).max() <= 1e-5
+        assert np.array_equal(mu, mu2)
+
+
+def test_half_chunks_with_rtiles_and_other_lattices(K):
+    # R = 16: four 16-byte chunks per row, so four column tiles fit
+    insts = instances(6)
+    with make_batch(K, insts, "fp32") as bt:
+        K.kpm_batch_set_chunk_bytes(bt, 16)
+        assert K.kpm_batch_get_rtiles(bt)[2] == 4
+        K.kpm_batch_set_rtiles(bt, 4)
+        K.kpm_batch_set_config(bt, 2, 2, 100)
+        parts = bt.split(K.kpm_batch_run(bt))
+        with pytest.raises(K.KPMError) as e:
+            K.kpm_batch_set_chunk_bytes(bt, 32)  # 4 tiles do not divide 2 chunks per row
+        assert e.value.status == K.KPM_EINVAL
+    for x, mu in zip(insts, parts):
+        mu_o, _ = O.moments_doubling(x["H"], x["a"], x["b"], I.rademacher_block(x["seed"], x["H"].n, 16),
+                                     x["M"])
+        assert np.abs(mu - mu_o).max() <= 1e-5
+    # a 3D box with an open direction and a 1D chain
+    for dims, L, periodic in ((3, (7, 6, 5), (True, True, False)), (1, (61,), (True,))):
+        N = int(np.prod(L))
+        on = I.onsite_disorder(12 + dims, N, 1.5)
+        H = O.lattice_hamiltonian(L, periodic=periodic, onsite=on)
+        a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+        with K.kpm_create_stencil(dims, L, periodic=periodic, onsite=on) as h:
+            with K.kpm_batch_create([h, h], [30, 52], 16, [a, a], [b, b], [3, 4], precision="fp32") as bt:
+                K.kpm_batch_set_chunk_bytes(bt, 16)
+                K.kpm_batch_set_config(bt, 4, 4, 100)
+                got = bt.split(K.kpm_batch_run(bt))
+        for M, seed, mu in zip((30, 52), (3, 4), got):
+            mu_o, _ = O.moments_doubling(H, a, b, I.rademacher_block(seed, N, 16), M)
+            assert np.abs(mu - mu_o).max() <= 1e-5
+
+
+def test_half_chunks_refusals(K):
+    insts = instances(3)
+    with make_batch(K, insts, "fp64", 8) as bt:      # FP64 rows always move 16-byte chunks
+        assert K.kpm_batch_get_chunk_bytes(bt) == (16, 4)
+        with pytest.raises(K.KPMError):
+            K.kpm_batch_set_chunk_bytes(bt, 16)
+    with make_batch(K, insts, "fp32") as bt:
+        for bad in (8, 64):
+            with pytest.raises(K.KPMError):
+                K.kpm_batch_set_chunk_bytes(bt, bad)
+        K.kpm_batch_set_resident(bt, True)
+        with pytest.raises(K.KPMError):
+            K.kpm_batch_set_chunk_bytes(bt, 16)
+        K.kpm_batch_set_resident(bt, False)
+        K.kpm_batch_set_chunk_bytes(bt, 16)
+        with pytest.raises(K.KPMError):
+            K.kpm_batch_set_resident(bt, True)
+    L = (12, 10)
+    hop = I.spin_hoppings(L, *I.spins(3, 120))
+    with K.kpm_create_stencil(2, L, hop=hop, complex_=True) as h:   # complex rows: 32-byte chunks
+        with K.kpm_batch_create([h], [8], 16, [9.0], [0.0], [1], precision="fp32") as bt:
+            with pytest.raises(K.KPMError):
+                K.kpm_batch_set_chunk_bytes(bt, 16)
