@@ -62,7 +62,7 @@ BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
 # reported only while the hash matches.
 MEASURED_TRAFFIC = {"cubic_spin_L64": (347.67e6, "step", "3b00c719cc0d365a"),
                     "csr_spin_dilute_L160": (3438.84e6, "step", "3b00c719cc0d365a"),
-                    "batch_2d_256/C4/chunk4/clusters74/rt1/top0": (68.17e9, "batch", "4782c8361760af5b")}
+                    "batch_2d_256/C4/chunk4/clusters74/rt1/top0": (60.49e9, "batch", "c1c7224a50899e0e")}
 
 
 def per_matvec(value):
@@ -248,7 +248,8 @@ def csr_handle(K, w):
     return K.kpm_create_csr(rp.size - 1, rp, col, val, complex_=True)
 
 
-def profile_run(prec, workload, batch_chunk=2, batch_cluster=4, batch_chunk_bytes=32):
+def profile_run(prec, workload, batch_chunk=2, batch_cluster=4, batch_chunk_bytes=32,
+                batch_rtiles=1, batch_top=0):
     """Two solves of the workload with Gershgorin bounds (no Lanczos products, so
     the only fused-step launches are those of the two solves); prec "bounds":
     three spectral-bound estimates of the headline lattice (Gershgorin and the
@@ -279,6 +280,7 @@ def profile_run(prec, workload, batch_chunk=2, batch_cluster=4, batch_chunk_byte
                                 [p[1] for p in ab], [x["seed"] for x in insts], prec) as bt:
             K.kpm_batch_set_chunk_bytes(bt, batch_chunk_bytes)
             K.kpm_batch_set_config(bt, batch_cluster, batch_chunk, 100)
+            K.kpm_batch_set_rtiles(bt, batch_rtiles, batch_top)
             for _ in range(2):
                 mu = K.kpm_batch_run(bt)
         print(json.dumps({"profile": prec, "workload": workload, "mu0": float(mu[0])}))
@@ -758,6 +760,10 @@ def main():
                     help="--profile with the batch workload: CTAs per cluster")
     ap.add_argument("--batch-chunk-bytes", type=int, default=32, choices=[16, 32],
                     help="--profile with the batch workload: bytes of a row per thread")
+    ap.add_argument("--batch-rtiles", type=int, default=1,
+                    help="--profile with the batch workload: column tiles of the largest instances")
+    ap.add_argument("--batch-top", type=int, default=0,
+                    help="--profile with the batch workload: instances tiled (0: all)")
     ap.add_argument("--workload", default="cubic_spin_L64",
                     choices=["cubic_spin_L64", "csr_spin_dilute_L160", "batch_2d_256",
                              "serve_poisson", "square_L32_fp64", "dense_wigner_D4096"],
@@ -771,7 +777,7 @@ def main():
         return reference_arm(args)
     if args.profile:
         return profile_run(args.profile, args.workload, args.batch_chunk, args.batch_cluster,
-                           args.batch_chunk_bytes)
+                           args.batch_chunk_bytes, args.batch_rtiles, args.batch_top)
     if args.workload == "square_L32_fp64":
         return square_leg(args)
     if args.workload == "csr_spin_dilute_L160":
