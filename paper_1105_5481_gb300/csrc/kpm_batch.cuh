@@ -9,7 +9,8 @@
 // hardware cluster barrier (release/acquire at cluster scope, which orders the
 // vector rows written by one CTA before the next step's reads by the others).
 // Each CTA's moment partial goes to CTA rank 0 through distributed shared
-// memory; rank 0 adds the C partials in rank order.  Every access to another
+// memory (reduced while the cluster barrier is pending); rank 0 adds the C
+// partials in rank order, one product later.  Every access to another
 // CTA's shared memory is followed by a cluster barrier before any CTA can
 // leave the kernel.  An instance's result thus
 // depends only on C and the instance, never on the other instances in the
@@ -32,6 +33,16 @@
 namespace kpm {
 
 namespace cg = cooperative_groups;
+
+// The two halves of a cluster barrier (all threads of every CTA of the
+// cluster execute both, in this order): arrive with release semantics at
+// cluster scope, then wait with acquire semantics.
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
 
 struct BatchTask {
   StepArgs a;         // operator, geometry, traversal (x, y, w, partial set per step)
@@ -113,10 +124,21 @@ __global__ void __launch_bounds__(256, BatchMinBlocks<CH>::value)
     __syncthreads();
     const int Rp = s_args[0].Rp;
     const int nsteps = bt.M / 2;
-    // shared memory: CTA reduction scratch, then partials [2 parities][C][2 Rp] (rank 0)
+    // shared memory: CTA reduction scratch, then partials [3 slots][C][2 Rp] (rank 0)
     double* red = smem;
     double* part = smem + step_smem_bytes(s_args[0].Gt, blockDim.x, CH::VEC) / sizeof(double);
     double* part0 = cluster.map_shared_rank(part, 0);
+    // rank 0: the C partials of product `st`, added in rank order
+    auto sum_partials = [&](int st) {
+      const double* pp = part + (size_t)(st % 3) * C * 2 * Rp;
+      const int c0 = s_tile[0], Rt = s_tile[1];
+      for (int o = t; o < 2 * Rt; o += blockDim.x) {
+        const int q = (o / Rt) * Rp + c0 + o % Rt;  // (A or B, column)
+        double sum = 0.0;
+        for (int r = 0; r < C; ++r) sum += pp[(size_t)r * 2 * Rp + q];
+        bt.sums[(size_t)st * 2 * Rp + q] = sum;
+      }
+    };
 
     for (int step = bt.step_begin; step < bt.step_end; ++step) {
       const StepArgs& a = s_args[step & 1];
@@ -132,18 +154,19 @@ __global__ void __launch_bounds__(256, BatchMinBlocks<CH>::value)
       typename CH::Acc s;
       CH::acc_zero(s);
       step_rows<CH, MODE_DYN, OP, false, true>(a, op, rank, C, 0, s, step == 0);
-      cta_reduce<CH>(a, s, 0, red, part0 + ((size_t)(step & 1) * C + rank) * 2 * Rp + s_tile[0]);
-      cluster.sync();
-      if (rank == 0) {
-        const double* pp = part + (size_t)(step & 1) * C * 2 * Rp;
-        const int c0 = s_tile[0], Rt = s_tile[1];
-        for (int o = t; o < 2 * Rt; o += blockDim.x) {
-          const int q = (o / Rt) * Rp + c0 + o % Rt;  // (A or B, column)
-          double sum = 0.0;
-          for (int r = 0; r < C; ++r) sum += pp[(size_t)r * 2 * Rp + q];
-          bt.sums[(size_t)step * 2 * Rp + q] = sum;
-        }
-      }
+      // Split cluster barrier: the arrive publishes this CTA's rows of v_{n+1};
+      // the CTA reduction of its moment partial runs while the other CTAs
+      // finish, and its result (slot step % 3 at rank 0) is published by the
+      // next product's arrive.  Rank 0 sums a product's partials one product
+      // later; three slots keep a slot from being rewritten before it is read.
+      cluster_arrive_release();
+      cta_reduce<CH>(a, s, 0, red, part0 + ((size_t)(step % 3) * C + rank) * 2 * Rp + s_tile[0]);
+      cluster_wait_acquire();
+      if (rank == 0 && step > bt.step_begin) sum_partials(step - 1);
+    }
+    if (bt.step_begin < bt.step_end) {
+      cluster.sync();  // the partials of the last product of this launch
+      if (rank == 0) sum_partials(bt.step_end - 1);
     }
     if (bt.step_end == nsteps && bt.step_begin < bt.step_end && rank == 0) {
       __syncthreads();  // rank 0's own sums writes above
@@ -184,10 +207,10 @@ __global__ void __launch_bounds__(256, BatchMinBlocks<CH>::value)
   }
 }
 
-// reduction scratch, then partials [2 parities][C][2 Rp]
+// reduction scratch, then partials [3 slots][C][2 Rp]
 template <class CH, class OP>
 inline size_t batch_smem_bytes(int Gt, int block, int C, int Rp) {
-  return step_smem_bytes(Gt, block, CH::VEC) + (size_t)2 * C * 2 * Rp * sizeof(double);
+  return step_smem_bytes(Gt, block, CH::VEC) + (size_t)3 * C * 2 * Rp * sizeof(double);
 }
 
 template <class CH, class OP>
