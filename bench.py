@@ -62,7 +62,22 @@ BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
 # reported only while the hash matches.
 MEASURED_TRAFFIC = {"cubic_spin_L64": (347.67e6, "step", "3b00c719cc0d365a"),
                     "csr_spin_dilute_L160": (3438.84e6, "step", "3b00c719cc0d365a"),
-                    "batch_2d_256/C4/chunk4/clusters74/rt1/top0": (60.49e9, "batch", "c1c7224a50899e0e")}
+                    "batch_2d_256/C4/chunk4/clusters74/rt1/top0": (68.05e9, "batch", "721b534bb2268f1c"),
+                    "batch_2d_256/C4/chunk2/clusters74/rt2/top8": (59.14e9, "batch", "721b534bb2268f1c")}
+
+
+def accuracy_vs_fp64(K, mu32, mu64, a, b, n_nodes):
+    """Error of an FP32-vector result against the FP64 path on the same inputs and random
+    vectors (the FP64 path is parity-tested against the FP64 oracle): the largest moment
+    difference and the L1 distance of the Jackson DOS, integral of |rho32 - rho64| dE by
+    the Gauss-Chebyshev rule on the DOS nodes."""
+    mu32, mu64 = np.asarray(mu32, dtype=np.float64), np.asarray(mu64, dtype=np.float64)
+    _, r32 = K.kpm_dos(mu32, a, b, n_nodes)
+    _, r64 = K.kpm_dos(mu64, a, b, n_nodes)
+    x = np.cos(np.pi * (np.arange(n_nodes) + 0.5) / n_nodes)
+    wq = np.pi / n_nodes * np.sqrt(1 - x * x)
+    return {"max_abs_dmu": float(np.abs(mu32 - mu64).max()),
+            "dos_l1": float(np.sum(np.abs(r32 - r64) * wq * a))}
 
 
 def per_matvec(value):
@@ -417,6 +432,12 @@ def csr_leg(args):
     ms = e0.elapsed_time(e1) / steps
     launches = K.kpm_kernel_launches() - l0
     chain_ms, nsteps = K.kpm_step_timing(h)
+    # accuracy against the FP64 path on the first 512 moments (a prefix of the same
+    # recursion: an FP64 solve of all 4096 would take ~12 s)
+    m_pref = 512
+    mu64 = K.kpm_moments(h, m_pref, R, a, b, seed=1, precision="fp64", stream=stream)
+    accuracy = accuracy_vs_fp64(K, mu_chk[:m_pref], mu64, a, b, w["K"])
+    accuracy["moments_compared"] = m_pref
     bytes_step = 3 * N * R * 8 + nnz * (8 + 4) + 8 * (N + 1)
     hbm, peak_kind = peaks()
     ach = bytes_step / (chain_ms / nsteps / 1e3) / 1e9
@@ -434,7 +455,7 @@ def csr_leg(args):
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                      "traffic": measured_traffic("csr_spin_dilute_L160"), "bytes_per_launch": bytes_step,
                      "launch_ms": chain_ms / nsteps, "peak_kind": peak_kind},
-        "batch_of_one_moments": batch_of_one,
+        "accuracy_vs_fp64": accuracy,
         "gpu_launches": launches, "clocks": clk.summary()}))
     h.close()
     return 0
@@ -601,6 +622,14 @@ def batch_leg(args):
     e1.record(stream)
     stream.synchronize()
     ms_single = e0.elapsed_time(e1)
+    # accuracy: every 32nd instance against its FP64 solve on the same random vectors
+    acc_b = []
+    for k, (mu_i, h_i, m_i, p_i, sd) in enumerate(zip(bt.split(mu_host), hs, Ms, ab, seeds)):
+        if k % 32 == 0:
+            mu64 = K.kpm_moments(h_i, m_i, R, p_i[0], p_i[1], seed=sd, precision="fp64")
+            acc_b.append(accuracy_vs_fp64(K, mu_i, mu64, p_i[0], p_i[1], 1024))
+    accuracy = {"max_abs_dmu": max(x["max_abs_dmu"] for x in acc_b),
+                "dos_l1": max(x["dos_l1"] for x in acc_b), "instances_compared": len(acc_b)}
     # the resident form (each instance's vectors in its cluster's shared memory)
     # at the smallest cluster size where the largest instance fits
     resident = None
@@ -640,6 +669,7 @@ def batch_leg(args):
                              "set of the active instances is L2-resident, so frac can exceed 1"},
         "per_instance_calls": {"ms": ms_single, "speedup_of_batch": ms_single / ms},
         "resident_form": resident,
+        "accuracy_vs_fp64": accuracy,
         "solves_per_s": 256 / (ms / 1e3),
         "per_matvec": per_matvec(units / (ms / 1e3)),
         "gpu_launches": launches, "clocks": clk.summary()}))
@@ -860,6 +890,9 @@ def main():
 
     ms32, launches32, step_ms32, clk32 = timed("fp32", args.steps, args.warmup)
     ms64, launches64, step_ms64, clk64 = timed("fp64", args.fp64_steps, min(args.warmup, 3))
+    # the FP32-vector result against the FP64 path on the same random vectors
+    mu64_chk = K.kpm_moments(h, M, R, a, b, seed=seed0, precision="fp64", stream=stream)
+    accuracy = accuracy_vs_fp64(K, mu_chk, mu64_chk, a, b, Kn)
 
     combined = None
     if dist is not None:
@@ -935,6 +968,7 @@ def main():
                          "bytes_per_launch": bytes32, "launch_ms": step_ms32,
                          "peak_kind": f"{peak_kind} (copy bandwidth)"},
             "per_matvec": per_matvec(value),
+            "accuracy_vs_fp64": accuracy,
             "fp64_path": {"value": world * units / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
                           "per_matvec": per_matvec(world * units / (ms64 / 1e3)),
                           "steps": args.fp64_steps, "dtype": "f64",
