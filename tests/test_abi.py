@@ -72,6 +72,22 @@ def test_invalid_arguments_are_rejected_before_the_device(K):
     assert L.kpm_create_dense(6, Zb.view(np.float64).ctypes.data, K.KPM_COMPLEX, C.byref(h)) == K.KPM_EINVAL
 
 
+def test_batch_entry_points_reject_a_null_batch(K):
+    # every batch call validates its handle before it touches a device
+    L = K.lib()
+    i1, i2 = C.c_int(), C.c_int()
+    assert L.kpm_batch_set_resident(None, 1) == K.KPM_EINVAL
+    assert L.kpm_batch_get_resident(None, C.byref(i1), C.byref(i2)) == K.KPM_EINVAL
+    assert L.kpm_batch_set_chunk_bytes(None, 16) == K.KPM_EINVAL
+    assert L.kpm_batch_get_chunk_bytes(None, C.byref(i1), C.byref(i2)) == K.KPM_EINVAL
+    assert L.kpm_batch_set_rtiles(None, 2, 0) == K.KPM_EINVAL
+    assert L.kpm_batch_set_config(None, 4, 4, 100) == K.KPM_EINVAL
+    assert L.kpm_batch_run(None, None, None) == K.KPM_EINVAL
+    assert "NULL" in K.kpm_last_error()
+    out = C.c_void_p()
+    assert L.kpm_batch_create(0, None, None, C.byref(out)) == K.KPM_EINVAL
+
+
 def _oracle_csr(L, periodic, onsite, hop, mask, t=1.0):
     H = O.lattice_hamiltonian(L, periodic=periodic, onsite=onsite, hop=hop, mask=mask, t=t)
     return H.rowptr, H.col, H.val
