@@ -170,6 +170,20 @@ typedef struct {
 kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu_per_vec,
                        void* stream);
 
+/* Checkpoint and resume (the paper has no counterpart; a library service):
+ * continues the realisation of the most recent kpm_moments call on `h` to M
+ * moments (M even, larger than that call's M).  A call with S == 1 leaves
+ * v_{n-1}, v_n and the per-step moment sums of its realisation in the
+ * handle; this entry point runs products n = M_old/2 .. M/2 - 1 from there
+ * with the same launches as one uninterrupted call, so mu[0..M) (and
+ * mu_per_vec[r*M + n], the R vectors of that call) equal those of a single
+ * kpm_moments call with this M and the same parameters bit for bit.  It may
+ * be repeated (256 -> 512 -> 1024).  Outputs as kpm_moments (host or device;
+ * host outputs synchronise and report KPM_EDIVERGE).  KPM_ENOTREADY if there
+ * is no such state (no previous call, S > 1, or the previous kpm_moments
+ * call on this handle failed); KPM_EINVAL if M is odd or not larger. */
+kpm_status kpm_moments_extend(kpm_handle h, int M, double* mu, double* mu_per_vec, void* stream);
+
 /* Kernel-damped Chebyshev series on K Chebyshev nodes (Eq. (fKPM)):
  *   x_k = cos(pi (k + 1/2) / K),  E[k] = a x_k + b,
  *   rho[k] = [g_0 mu_0 + 2 sum_{n=1}^{M-1} g_n mu_n cos(pi n (k+1/2)/K)] / (pi a sqrt(1 - x_k^2))

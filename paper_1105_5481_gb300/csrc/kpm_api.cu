@@ -775,6 +775,7 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
     return fail(KPM_EINVAL, "dense handles compute in FP64 (the paper's formulation)");
   if (!mu && !mu_per_vec) return fail(KPM_EINVAL, "no output requested");
   if ((int64_t)S * R * (int64_t)M > ((int64_t)1 << 40)) return fail(KPM_EINVAL, "S*R*M too large");
+  h->work.resumable = false;  // set again below once this call's steps are enqueued
   KPM_CUDA(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const bool fp32 = p->precision == KPM_FP32_VEC_FP64_MOM;
@@ -973,6 +974,16 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
   }
   w.direct_done = true;
   w.timed = true;
+  if (S == 1) {
+    // v_{M/2-1} and v_{M/2} stay in v[] with the per-step sums: kpm_moments_extend
+    // can continue this realisation
+    w.resumable = true;
+    w.res_steps = steps;
+    w.res_R = R;
+    w.res_a = p->a;
+    w.res_b = p->b;
+    w.res_seed = (unsigned long long)p->seed;
+  }
   KPM_CUDA(launch_finalize(w.sums, S, steps, R, Rp, h->n, M, w.per_vec, w.mu, h->d_prm, st));
   bool host_out = false;
   if (mu) {
@@ -985,6 +996,102 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
     const bool dev = is_device_ptr(mu_per_vec);
     host_out |= !dev;
     KPM_CUDA(cudaMemcpyAsync(mu_per_vec, w.per_vec, (size_t)S * R * M * sizeof(double),
+                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  if (host_out) {
+    int flags = 0;
+    KPM_CUDA(cudaMemcpyAsync(&flags, &h->d_prm->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KPM_CUDA(cudaStreamSynchronize(st));
+    if (flags & 1)
+      return fail(KPM_EDIVERGE,
+                  "a moment left [-1, 1]: the bounds (a, b) do not enclose the spectrum");
+  }
+  return KPM_OK;
+}
+
+kpm_status kpm_moments_extend(kpm_handle h, int M, double* mu, double* mu_per_vec, void* stream) {
+  if (!h) return fail(KPM_EINVAL, "handle is NULL");
+  auto& w = h->work;
+  if (!w.resumable)
+    return fail(KPM_ENOTREADY,
+                "no resumable state: extend follows a kpm_moments call with S = 1 on this handle");
+  const int old_steps = w.res_steps;
+  if (M < 2 || (M & 1)) return fail(KPM_EINVAL, "M must be even and >= 2");
+  if (M / 2 <= old_steps) return fail(KPM_EINVAL, "M must exceed the moments already computed");
+  if (!mu && !mu_per_vec) return fail(KPM_EINVAL, "no output requested");
+  KPM_CUDA(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int steps = M / 2, Rp = w.Rp, R = w.res_R, grid = w.nCTA;
+  const bool fp32 = w.prec == KPM_FP32_VEC_FP64_MOM;
+  // per-step sums for the longer chain, keeping those of the steps already done
+  const size_t sums_bytes = (size_t)steps * 2 * Rp * sizeof(double);
+  if (w.sums_bytes < sums_bytes) {
+    double* ns = nullptr;
+    kpm_status sa = dalloc((char**)&ns, sums_bytes);
+    if (sa != KPM_OK) return sa;
+    KPM_CUDA(cudaMemcpyAsync(ns, w.sums, (size_t)old_steps * 2 * Rp * sizeof(double),
+                             cudaMemcpyDeviceToDevice, st));
+    KPM_CUDA(cudaStreamSynchronize(st));
+    dfree(w.sums);
+    w.sums = ns;
+    w.sums_bytes = sums_bytes;
+  }
+  const size_t out_bytes = ((size_t)R * M + M) * sizeof(double);
+  if (w.out_bytes < out_bytes) {
+    KPM_CUDA(cudaStreamSynchronize(st));
+    dfree(w.per_vec);
+    w.per_vec = nullptr;
+    w.mu = nullptr;
+    w.out_bytes = 0;
+    kpm_status sa = dalloc((char**)&w.per_vec, out_bytes);
+    if (sa != KPM_OK) return sa;
+    w.out_bytes = out_bytes;
+  }
+  w.mu = w.per_vec + (size_t)R * M;
+  // the call's parameters for realisation 0 at the new M (the scaled operator
+  // of the resumed call is still in place)
+  RunParams prm{};
+  prm.a = w.res_a;
+  prm.b = w.res_b;
+  prm.seed = w.res_seed;
+  prm.s = 0;
+  prm.R = R;
+  prm.S = 1;
+  prm.M = M;
+  prm.flags = 0;
+  KPM_CUDA(cudaMemcpyAsync(h->d_prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st));
+  // the same step launches as the uninterrupted chain: product n reads v_n
+  // from v[n & 1] and writes v_{n+1} over v_{n-1}; the ring is reduced at the
+  // same step boundaries, so the sums equal those of a single call with this M
+  StepArgs a = w.proto;
+  const LaunchCfg cfg{w.block, grid};
+  for (int n = old_steps; n < steps; ++n) {
+    a.x = w.v[n & 1];
+    a.y = w.v[(n + 1) & 1];
+    a.w = w.v[(n + 1) & 1];
+    a.partial = w.ring + (size_t)(n % RING) * grid * 2 * Rp;
+    a.reverse = (n & 1) ^ 1;
+    KPM_CUDA(launch_op(h, fp32, MODE_STEP, a, cfg, st));
+    if ((n + 1) % RING == 0 || n == steps - 1) {
+      const int first = std::max(old_steps, n / RING * RING);
+      KPM_CUDA(launch_reduce_ring(w.ring, RING, first, n + 1 - first, grid, Rp, h->d_prm, steps,
+                                  w.sums, st));
+    }
+  }
+  KPM_CUDA(launch_finalize(w.sums, 1, steps, R, Rp, h->n, M, w.per_vec, w.mu, h->d_prm, st));
+  w.res_steps = steps;
+  w.ready = false;  // the captured graph and buffers belong to the old M: the next call rebuilds
+  bool host_out = false;
+  if (mu) {
+    const bool dev = is_device_ptr(mu);
+    host_out |= !dev;
+    KPM_CUDA(cudaMemcpyAsync(mu, w.mu, M * sizeof(double),
+                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  if (mu_per_vec) {
+    const bool dev = is_device_ptr(mu_per_vec);
+    host_out |= !dev;
+    KPM_CUDA(cudaMemcpyAsync(mu_per_vec, w.per_vec, (size_t)R * M * sizeof(double),
                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   }
   if (host_out) {

@@ -193,6 +193,12 @@ struct kpm_handle_s {
     bool ready = false;        // buffers and launch plan match the current shape
     bool direct_done = false;  // one call of this shape ran without a graph
     kpm::StepArgs proto{};                    // launch arguments common to all steps
+    // resumable state of the last kpm_moments call (S == 1): v_{n-1}, v_n in
+    // v[], the per-step sums of its steps, and its parameters
+    bool resumable = false;
+    int res_steps = 0, res_R = 0;
+    double res_a = 0.0, res_b = 0.0;
+    unsigned long long res_seed = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};  // recorded around the step chain in the graph
     bool timed = false;
   } work;

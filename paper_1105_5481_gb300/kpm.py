@@ -74,6 +74,7 @@ def lib() -> C.CDLL:
                                          C.c_void_p, C.c_void_p, C.c_void_p]
         L.kpm_bounds.argtypes = [h, C.c_int, C.c_double, C.c_uint64] + [C.POINTER(C.c_double)] * 4 + [C.c_void_p]
         L.kpm_moments.argtypes = [h, C.POINTER(kpm_params), C.c_void_p, C.c_void_p, C.c_void_p]
+        L.kpm_moments_extend.argtypes = [h, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
         L.kpm_dos.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                               C.c_void_p, C.c_void_p, C.c_void_p]
         L.kpm_dos_kernel.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
@@ -121,7 +122,7 @@ def lib() -> C.CDLL:
         L.kpm_kernel_launches.restype = C.c_uint64
         for name in ("kpm_create_stencil", "kpm_create_csr", "kpm_create_dense", "kpm_stencil_to_csr",
                      "kpm_bounds",
-                     "kpm_moments", "kpm_dos", "kpm_info", "kpm_step_timing",
+                     "kpm_moments", "kpm_moments_extend", "kpm_dos", "kpm_info", "kpm_step_timing",
                      "kpm_moments_csr_noalloc", "kpm_batch_create", "kpm_batch_run", "kpm_batch_tune",
                      "kpm_batch_set_config", "kpm_batch_info", "kpm_batch_set_rtiles",
                      "kpm_batch_get_rtiles", "kpm_batch_set_resident", "kpm_batch_get_resident",
@@ -308,6 +309,17 @@ def kpm_moments(h: Handle, M, R, a, b, seed=0, S=1, precision="fp64", user_v0=No
     if st == KPM_EDIVERGE and not check:
         return (mu, pv, st) if per_vec or out_per_vec is not None else (mu, st)
     _check(st)
+    return (mu, pv) if per_vec or out_per_vec is not None else mu
+
+
+def kpm_moments_extend(h: Handle, M, R=None, per_vec=False, out=None, out_per_vec=None, stream=None):
+    """Continue the last single-realisation kpm_moments call on ``h`` to M moments.
+    Returns mu (and mu_per_vec[R, M] if per_vec; R is that call's R)."""
+    mu = out if out is not None else np.zeros(int(M))
+    pv = out_per_vec
+    if pv is None and per_vec:
+        pv = np.zeros((int(R), int(M)))
+    _check(lib().kpm_moments_extend(h.raw, int(M), _ptr(mu), _ptr(pv), _stream(stream)))
     return (mu, pv) if per_vec or out_per_vec is not None else mu
 
 

@@ -245,3 +245,54 @@ def test_widest_vector_block_matches_oracle(K, prec, cplx, R):
         assert e.value.status == K.KPM_EINVAL
     assert np.abs(per - per_o).max() <= TOL[prec]
     assert np.abs(mu - mu_o).max() <= TOL[prec]
+
+
+# ---------------------------------------------------------------- checkpoint / resume
+# kpm_moments_extend continues the last single-realisation call on a handle;
+# the moments equal those of one uninterrupted call bit for bit, because the
+# same launches run in the same order from the kept v_{n-1}, v_n and sums.
+
+
+@pytest.mark.parametrize("name,prec,csr,chain",
+                         [("square_L32", "fp64", False, (256, 512)),
+                          ("cube_spin_L8", "fp32", False, (128, 256, 1024)),
+                          ("ragged_open_mask", "fp64", True, (40, 42, 300))])
+def test_extend_equals_one_call(K, name, prec, csr, chain):
+    kw, cplx = make_case(name)
+    H = oracle_H(kw)
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    R, M = 8, chain[-1]
+    with handle(K, kw, cplx, csr) as h:
+        direct, pv_direct = K.kpm_moments(h, M, R, a, b, seed=7, precision=prec, per_vec=True)
+        K.kpm_moments(h, chain[0], R, a, b, seed=7, precision=prec)
+        for m in chain[1:]:
+            mu, pv = K.kpm_moments_extend(h, m, R=R, per_vec=True)
+        again = K.kpm_moments(h, M, R, a, b, seed=7, precision=prec)  # the handle rebuilds cleanly
+    assert np.array_equal(mu, direct)
+    assert np.array_equal(pv, pv_direct)
+    assert np.array_equal(again, direct)
+    v0 = (I.phase_block if cplx else I.rademacher_block)(7, H.n, R)
+    mu_o, _ = O.moments_doubling(H, a, b, v0, M)
+    assert np.abs(mu - mu_o).max() <= TOL[prec]
+
+
+def test_extend_refusals(K):
+    kw, cplx = make_case("chain_open")
+    H = oracle_H(kw)
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    with handle(K, kw, cplx) as h:
+        with pytest.raises(K.KPMError) as e:
+            K.kpm_moments_extend(h, 64)                     # no call to resume yet
+        assert e.value.status == K.KPM_ENOTREADY
+        K.kpm_moments(h, 64, 4, a, b, seed=1, S=2)           # two realisations: not resumable
+        with pytest.raises(K.KPMError) as e:
+            K.kpm_moments_extend(h, 128)
+        assert e.value.status == K.KPM_ENOTREADY
+        K.kpm_moments(h, 64, 4, a, b, seed=1)
+        for bad in (64, 62, 97):                             # not larger, or odd
+            with pytest.raises(K.KPMError) as e:
+                K.kpm_moments_extend(h, bad)
+            assert e.value.status == K.KPM_EINVAL
+        mu = K.kpm_moments_extend(h, 256)                    # grows the per-step sums
+    mu_o, _ = O.moments_doubling(H, a, b, I.rademacher_block(1, H.n, 4), 256)
+    assert np.abs(mu - mu_o).max() <= 1e-10
