@@ -179,10 +179,11 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
  * mu_per_vec[r*M + n], the R vectors of that call) equal those of a single
  * kpm_moments call with this M and the same parameters bit for bit.  It may
  * be repeated (256 -> 512 -> 1024).  Outputs as kpm_moments (host or device;
- * host outputs synchronise and report KPM_EDIVERGE).  KPM_ENOTREADY if there
- * is no such state (no previous call, S > 1, or the previous kpm_moments
- * call on this handle returned before enqueueing its products, e.g. on
- * invalid arguments); KPM_EINVAL if M is odd or not larger. */
+ * host outputs synchronise and report KPM_EDIVERGE).  A kpm_moments call
+ * rejected by its argument checks touches nothing and leaves the state as it
+ * was; any other kpm_moments call replaces it.  KPM_ENOTREADY if there is no
+ * such state (no previous call, the last call had S > 1, or its launches
+ * failed); KPM_EINVAL if M is odd or not larger. */
 kpm_status kpm_moments_extend(kpm_handle h, int M, double* mu, double* mu_per_vec, void* stream);
 
 /* Kernel-damped Chebyshev series on K Chebyshev nodes (Eq. (fKPM)):
