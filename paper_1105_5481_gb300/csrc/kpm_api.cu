@@ -775,9 +775,6 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
     return fail(KPM_EINVAL, "dense handles compute in FP64 (the paper's formulation)");
   if (!mu && !mu_per_vec) return fail(KPM_EINVAL, "no output requested");
   if ((int64_t)S * R * (int64_t)M > ((int64_t)1 << 40)) return fail(KPM_EINVAL, "S*R*M too large");
-  h->work.resumable = false;  // set again below once this call's steps are enqueued
-  KPM_CUDA(cudaSetDevice(h->device));
-  cudaStream_t st = (cudaStream_t)stream;
   const bool fp32 = p->precision == KPM_FP32_VEC_FP64_MOM;
   int Rp, G;
   padded_width(R, fp32, h->cplx, &Rp, &G);
@@ -789,6 +786,11 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
   } else if (G > 1024) {
     return fail(KPM_EINVAL, "R too large for one block of vectors");
   }
+  // the arguments are valid: this call replaces any resumable state (set
+  // again below once its products are enqueued)
+  h->work.resumable = false;
+  KPM_CUDA(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
   const int slot = fp32 ? 1 : 0;
   const bool user_v0 = p->user_v0 != nullptr;
   const int steps = M / 2;
