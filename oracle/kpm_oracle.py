@@ -26,7 +26,7 @@ Rev. Mod. Phys. 78, 275 (2006)):
   gershgorin             Eq. (tilde) bounds from the Gershgorin theorem         [pinned]
   lanczos_bounds         k-step Lanczos with full reorthogonalisation, Ritz
                          value +- residual |beta_k s_k|, clamped to Gershgorin  [pinned]
-  rescale                Eq. (tilde): a = (Emax-Emin)/(2-eps), b = (Emax+Emin)/2
+  rescale                Eq. (tilde): a = (Emax-Emin)/(2-eps), b = (Emax+Emin)/2  [pinned]
   lorentz_kernel         review Eq. 74: g_n = sinh(lambda (1 - n/M)) / sinh(lambda)  [pinned]
   green                  local Green's function by the review's expansion
                          G(x+i0) = -i/sqrt(1-x^2) [g_0 mu_0 + 2 sum g_n mu_n e^{-in arccos x}] [pinned]
