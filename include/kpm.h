@@ -182,8 +182,10 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
  * host outputs synchronise and report KPM_EDIVERGE).  A kpm_moments call
  * rejected by its argument checks touches nothing and leaves the state as it
  * was; any other kpm_moments call replaces it.  KPM_ENOTREADY if there is no
- * such state (no previous call, the last call had S > 1, or its launches
- * failed); KPM_EINVAL if M is odd or not larger. */
+ * such state: no previous call, the last call had S > 1, or the last
+ * kpm_moments or kpm_moments_extend call that passed its argument checks
+ * failed part way (an allocation or a launch), which drops the state;
+ * KPM_EINVAL if M is odd or not larger (the state is then kept). */
 kpm_status kpm_moments_extend(kpm_handle h, int M, double* mu, double* mu_per_vec, void* stream);
 
 /* Kernel-damped Chebyshev series on K Chebyshev nodes (Eq. (fKPM)):
@@ -437,21 +439,39 @@ void kpm_server_destroy(kpm_server s);
  * FP64 Chebyshev moments mu[0..M) of a CSR matrix that is already in device
  * memory (d_rowptr[n+1] int64, d_col[nnz] int32, d_val[nnz] FP64 or [nnz][2]
  * complex FP64, same layout and meaning as kpm_create_csr) with the same
- * kernels and the same random vectors as kpm_moments with S = 1 and
- * precision KPM_FP64, and allocates nothing: all of its scratch (two N x R
- * vector blocks, the scaled matrix values, partial and moment sums) lives in
- * one file-scope device array of KPM_NOALLOC_SCRATCH_BYTES bytes that every
- * GPU loading the library holds until the process exits.
+ * random vectors and the same doubling identities as kpm_moments with S = 1
+ * and precision KPM_FP64, and allocates nothing: all of its scratch (a
+ * checked copy of the structure, two N x R vector blocks, the scaled matrix
+ * values, partial and moment sums, the per-vector moments the mean is
+ * taken from) lives in one file-scope device array of
+ * KPM_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds
+ * until the process exits.  Its fused step is the library's generic CSR
+ * kernel (rows walked through the row pointers); kpm_moments takes a padded
+ * ELL copy for short rows, so the two agree to rounding (1e-10), not bit for
+ * bit.
+ *   Preconditions: the three arrays hold at least n+1, nnz and nnz (x2
+ *       complex) elements, and H is Hermitian.  The structure is checked on
+ *       the device before use: rowptr[0] == 0, rowptr non-decreasing,
+ *       rowptr[n] == nnz, every col in [0, n).  The products read only a copy
+ *       of it whose indices are made safe, so a broken rule never sends a
+ *       load out of bounds; it makes a host-output call return KPM_EINVAL
+ *       before any product is launched, and a device-output call write NaN
+ *       to every mu[n].
  *   mu: M doubles, device (asynchronous on `stream`) or host (synchronises and
  *       reports KPM_EDIVERGE like kpm_moments).
  * Returns KPM_EINVAL, naming the bytes it would need, when the problem does
- * not fit in the scratch (roughly 16 N R + 16 nnz bytes for real FP64; R up
- * to 512 real or 256 complex).  The first call on a device looks up the
- * scratch's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the
- * scratch and each leaves its contents behind: calls whose work can overlap
- * on the GPU (other streams, other host threads) race and must be serialised
- * by the caller. */
+ * not fit in the scratch: about 16 N Rp + 8 N + 12 nnz + 8 M (Rp + R) bytes
+ * for the real field, plus 128 Rp bytes per CTA of the step for the moment
+ * partials (Rp = R rounded up to a power of two, at least 2; complex: twice
+ * the vector and value terms, Rp = R rounded up to a power of two), R at
+ * most 512 real or 256 complex.  The
+ * first call on a device looks up the scratch's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process; make that first call before any stream capture, and do not
+ * call the entry point after a cudaDeviceReset of that device (the kept
+ * address would be stale).  All calls share the scratch and each leaves its
+ * contents behind: calls whose work can overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller. */
 kpm_status kpm_moments_csr_noalloc(int64_t n, int64_t nnz, const int64_t* d_rowptr,
                                    const int32_t* d_col, const double* d_val, kpm_field field,
                                    int M, int R, uint64_t seed, double a, double b, double* mu,
@@ -471,6 +491,14 @@ const char* kpm_last_error(void);
 /* Number of CUDA kernels the library has enqueued in this process (kernels in
  * a replayed graph count once per replay). */
 uint64_t kpm_kernel_launches(void);
+
+/* Testing aid (the paper has no counterpart): host-side fault injection for
+ * the library's own device allocations.  The next `after` allocations of the
+ * library's handles and calls succeed and the one after them fails with
+ * KPM_ENOMEM, as a real out-of-memory would; the injector then disarms.
+ * after = -1 disarms it at once.  Process-wide; no device work is involved.
+ * Returns KPM_EINVAL for after < -1. */
+kpm_status kpm_testing_fail_allocations(int64_t after);
 
 #ifdef __cplusplus
 }

@@ -101,10 +101,24 @@ void pfree(void* p, cudaStream_t st) {
 
 // Synchronous-use allocation: ordered on the legacy stream and completed
 // before return, so any stream may use the memory afterwards.
+// Host-side fault injection for tests (kpm_testing_fail_allocations): the
+// number of dalloc calls that still succeed before one fails; -1 = off.
+std::atomic<long long> g_fail_alloc_after{-1};
+
+bool injected_alloc_failure() {
+  long long k = g_fail_alloc_after.load();
+  while (k >= 0) {
+    if (g_fail_alloc_after.compare_exchange_weak(k, k - 1)) return k == 0;
+  }
+  return false;
+}
+
 template <typename T>
 kpm_status dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) return KPM_OK;
+  if (injected_alloc_failure())
+    return fail(KPM_ENOMEM, "device allocation (failure injected by kpm_testing_fail_allocations)");
   cudaError_t e = palloc((void**)p, count * sizeof(T), 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e != cudaSuccess) {
@@ -437,6 +451,12 @@ extern "C" {
 const char* kpm_last_error(void) { return t_err.c_str(); }
 
 uint64_t kpm_kernel_launches(void) { return g_launches.load(); }
+
+kpm_status kpm_testing_fail_allocations(int64_t after) {
+  if (after < -1) return fail(KPM_EINVAL, "after must be >= -1");
+  g_fail_alloc_after.store((long long)after);
+  return KPM_OK;
+}
 
 kpm_status kpm_create_stencil(const kpm_stencil_desc* d, kpm_field field, kpm_handle* out) {
   if (!out) return fail(KPM_EINVAL, "out is NULL");
@@ -854,6 +874,10 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
       cudaGraphExecDestroy(w.exec);
       w.exec = nullptr;
     }
+    // buffers are about to be replaced: until the plan below is complete no
+    // later call may take the old one (an allocation failing half way leaves
+    // the handle to rebuild on its next call)
+    w.ready = false;
     const size_t vbytes = (size_t)h->n * Rp * elem_bytes(fp32, h->cplx);
     if (w.vbytes < vbytes) {
       dfree(w.v[0]);
@@ -1021,6 +1045,12 @@ kpm_status kpm_moments_extend(kpm_handle h, int M, double* mu, double* mu_per_ve
   if (M < 2 || (M & 1)) return fail(KPM_EINVAL, "M must be even and >= 2");
   if (M / 2 <= old_steps) return fail(KPM_EINVAL, "M must exceed the moments already computed");
   if (!mu && !mu_per_vec) return fail(KPM_EINVAL, "no output requested");
+  // From here on buffers change: the captured graph and launch plan of the
+  // resumed call no longer match (the next kpm_moments rebuilds), and the
+  // state is resumable again only once every product below is enqueued, so a
+  // failure part way (an allocation, a launch) leaves nothing to resume from.
+  w.ready = false;
+  w.resumable = false;
   KPM_CUDA(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int steps = M / 2, Rp = w.Rp, R = w.res_R, grid = w.nCTA;
@@ -1082,7 +1112,7 @@ kpm_status kpm_moments_extend(kpm_handle h, int M, double* mu, double* mu_per_ve
   }
   KPM_CUDA(launch_finalize(w.sums, 1, steps, R, Rp, h->n, M, w.per_vec, w.mu, h->d_prm, st));
   w.res_steps = steps;
-  w.ready = false;  // the captured graph and buffers belong to the old M: the next call rebuilds
+  w.resumable = true;
   bool host_out = false;
   if (mu) {
     const bool dev = is_device_ptr(mu);

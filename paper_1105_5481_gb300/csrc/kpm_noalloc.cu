@@ -8,8 +8,17 @@
 // code that runs while a memory pool is frozen or nearly exhausted, processes
 // that budget all of their device memory at start-up, and hosts (plugins,
 // real-time loops) where a cudaMalloc/cudaFree would synchronise the device or
-// take a lock they cannot afford.  The kernels it launches are the same ones
-// kpm_moments uses; only the source of their scratch memory differs.
+// take a lock they cannot afford.  It runs the library's generic CSR form of
+// the fused step (rows walked through the row pointers), not the padded-ELL
+// form that kpm_moments picks for short rows, so its moments agree with
+// kpm_moments to rounding (1e-10), not bit for bit.
+//
+// The caller's structure arrays are device memory the library cannot inspect
+// from the host, so a check kernel reads them first: it copies the row
+// pointers clamped to [0, nnz] and the column indices (out-of-range ones
+// replaced by 0) into the scratch, and flags any violation of the CSR rules.
+// The steps read only those copies, so a malformed structure cannot send a
+// load outside the caller's arrays or the vector blocks.
 #include <math.h>
 
 #include <algorithm>
@@ -49,6 +58,40 @@ kpm_status scratch_address(int dev, unsigned char** out) {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// RunParams::flags bit set when the caller's CSR structure breaks a rule
+constexpr int BAD_CSR = 2;
+
+// Copies the structure into the scratch with every index made safe, and
+// flags: rowptr[0] != 0, rowptr[n] != nnz, a decreasing or out-of-range row
+// pointer, a column index outside [0, n).
+__global__ void noalloc_csr_check_kernel(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
+                                         const int32_t* __restrict__ col, int64_t* __restrict__ rp_out,
+                                         int32_t* __restrict__ col_out, RunParams* prm) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  for (int64_t i = t0; i <= n; i += stride) {
+    const int64_t r = rowptr[i];
+    bad |= (i == 0 && r != 0) || (i == n && r != nnz) || r < 0 || r > nnz;
+    if (i > 0) bad |= rowptr[i - 1] > r;
+    rp_out[i] = r < 0 ? 0 : (r > nnz ? nnz : r);
+  }
+  for (int64_t k = t0; k < nnz; k += stride) {
+    const int32_t c = col[k];
+    const bool ok = c >= 0 && (int64_t)c < n;
+    bad |= !ok;
+    col_out[k] = ok ? c : 0;
+  }
+  if (bad) atomicOr(&prm->flags, BAD_CSR);
+}
+
+// Device outputs of a call whose structure was flagged become NaN.
+__global__ void noalloc_poison_kernel(const RunParams* prm, double* mu, int M) {
+  if (!(prm->flags & BAD_CSR)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x)
+    mu[i] = __longlong_as_double(0x7ff8000000000000LL);
+}
 
 bool on_device(const void* p) {
   cudaPointerAttributes at;
@@ -108,6 +151,8 @@ extern "C" kpm_status kpm_moments_csr_noalloc(int64_t n, int64_t nnz, const int6
   const size_t o_prm = off; off = align256(off + sizeof(RunParams));
   const size_t o_sc = off; off = align256(off + sizeof(ScalarBlock));
   const size_t o_vals = off; off = align256(off + (size_t)std::max<int64_t>(nnz, 1) * c * 8);
+  const size_t o_rp = off; off = align256(off + (size_t)(n + 1) * 8);
+  const size_t o_col = off; off = align256(off + (size_t)std::max<int64_t>(nnz, 1) * 4);
   const size_t o_v0 = off; off = align256(off + (size_t)n * Rp * c * 8);
   const size_t o_v1 = off; off = align256(off + (size_t)n * Rp * c * 8);
   const size_t o_ring = off; off = align256(off + (size_t)NA_RING * grid * 2 * Rp * 8);
@@ -126,6 +171,8 @@ extern "C" kpm_status kpm_moments_csr_noalloc(int64_t n, int64_t nnz, const int6
   auto* prm = (RunParams*)(base + o_prm);
   auto* sc = (ScalarBlock*)(base + o_sc);
   auto* vals = (double*)(base + o_vals);
+  auto* rp_safe = (int64_t*)(base + o_rp);
+  auto* col_safe = (int32_t*)(base + o_col);
   auto* v0 = (double*)(base + o_v0);
   auto* v1 = (double*)(base + o_v1);
   auto* ring = (double*)(base + o_ring);
@@ -145,12 +192,29 @@ extern "C" kpm_status kpm_moments_csr_noalloc(int64_t n, int64_t nnz, const int6
   hp.S = 1;
   hp.M = M;
   KPM_CUDA(cudaMemcpyAsync(prm, &hp, sizeof(hp), cudaMemcpyHostToDevice, st));
+  {
+    const int64_t work = std::max<int64_t>(n + 1, nnz);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 4 * (int64_t)sms));
+    noalloc_csr_check_kernel<<<blocks, 256, 0, st>>>(n, nnz, d_rowptr, d_col, rp_safe, col_safe, prm);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    KPM_CUDA(cudaGetLastError());
+  }
+  if (!dev_out) {
+    // host output: the call synchronises anyway, so a malformed structure is
+    // reported before any product is launched
+    int flags = 0;
+    KPM_CUDA(cudaMemcpyAsync(&flags, &prm->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KPM_CUDA(cudaStreamSynchronize(st));
+    if (flags & BAD_CSR)
+      return fail(KPM_EINVAL, "malformed CSR structure: rowptr[0] must be 0, rowptr non-decreasing "
+                  "with rowptr[n] = nnz, and every column index in [0, n)");
+  }
   KPM_CUDA(launch_prescale_csr(false, cplx, nnz, d_val, prm, false, vals, sc, st));
   KPM_CUDA(launch_rng_init(false, cplx, n, Rp, prm, v0, st));
   StepArgs sa = a0;
   sa.sc = sc;
-  sa.rowptr = d_rowptr;
-  sa.col = d_col;
+  sa.rowptr = rp_safe;
+  sa.col = col_safe;
   sa.vals = vals;
   const LaunchCfg cfg{NA_BLOCK, (int)grid};
   void* v[2] = {v0, v1};
@@ -174,7 +238,11 @@ extern "C" kpm_status kpm_moments_csr_noalloc(int64_t n, int64_t nnz, const int6
                                   Rp, prm, steps, sums, st));
   }
   KPM_CUDA(launch_finalize(sums, 1, steps, R, Rp, n, M, per_vec, mu_dev, prm, st));
-  if (!dev_out) {
+  if (dev_out) {
+    noalloc_poison_kernel<<<1, 256, 0, st>>>(prm, mu_dev, M);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    KPM_CUDA(cudaGetLastError());
+  } else {
     int flags = 0;
     KPM_CUDA(cudaMemcpyAsync(mu, mu_dev, (size_t)M * 8, cudaMemcpyDeviceToHost, st));
     KPM_CUDA(cudaMemcpyAsync(&flags, &prm->flags, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -120,6 +120,7 @@ def lib() -> C.CDLL:
         L.kpm_destroy.restype = None
         L.kpm_last_error.restype = C.c_char_p
         L.kpm_kernel_launches.restype = C.c_uint64
+        L.kpm_testing_fail_allocations.argtypes = [C.c_int64]
         for name in ("kpm_create_stencil", "kpm_create_csr", "kpm_create_dense", "kpm_stencil_to_csr",
                      "kpm_bounds",
                      "kpm_moments", "kpm_moments_extend", "kpm_dos", "kpm_info", "kpm_step_timing",
@@ -129,7 +130,7 @@ def lib() -> C.CDLL:
                      "kpm_batch_set_chunk_bytes", "kpm_batch_get_chunk_bytes",
                      "kpm_server_create",
                      "kpm_server_submit", "kpm_server_wait", "kpm_server_poll", "kpm_server_cancel",
-                     "kpm_server_stats"):
+                     "kpm_server_stats", "kpm_testing_fail_allocations"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -637,3 +638,9 @@ def kpm_last_error() -> str:
 
 def kpm_kernel_launches() -> int:
     return int(lib().kpm_kernel_launches())
+
+
+def kpm_testing_fail_allocations(after: int):
+    """Testing aid: the next `after` device allocations of the library succeed and
+    the one after fails with KPM_ENOMEM (-1 disarms)."""
+    _check(lib().kpm_testing_fail_allocations(int(after)))

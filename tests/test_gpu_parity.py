@@ -296,3 +296,36 @@ def test_extend_refusals(K):
         mu = K.kpm_moments_extend(h, 256)                    # grows the per-step sums
     mu_o, _ = O.moments_doubling(H, a, b, I.rademacher_block(1, H.n, 4), 256)
     assert np.abs(mu - mu_o).max() <= 1e-10
+
+
+@pytest.mark.parametrize("fail_after", [0, 1])
+def test_extend_failing_part_way_leaves_nothing_to_resume(K, fail_after):
+    # An extend that runs out of device memory after it has started replacing
+    # buffers (fail_after = 1: the per-step sums grow, then the per-vector
+    # moments cannot) must leave no state behind: a second extend has nothing
+    # to resume, and the next kpm_moments rebuilds its plan instead of
+    # replaying a graph that points at freed memory.
+    kw, cplx = make_case("square_L32")
+    H = oracle_H(kw)
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    R = 8
+    with handle(K, kw, cplx) as h:
+        first = K.kpm_moments(h, 64, R, a, b, seed=3)
+        K.kpm_moments(h, 64, R, a, b, seed=3)               # second call: captured graph
+        K.kpm_testing_fail_allocations(fail_after)
+        try:
+            with pytest.raises(K.KPMError) as e:
+                K.kpm_moments_extend(h, 128)
+            assert e.value.status == K.KPM_ENOMEM
+        finally:
+            K.kpm_testing_fail_allocations(-1)
+        with pytest.raises(K.KPMError) as e:
+            K.kpm_moments_extend(h, 128)
+        assert e.value.status == K.KPM_ENOTREADY
+        again = K.kpm_moments(h, 64, R, a, b, seed=3)
+        longer = K.kpm_moments(h, 128, R, a, b, seed=3)
+        resumed = K.kpm_moments_extend(h, 256)             # resumable again after a full call
+    assert np.array_equal(again, first)
+    mu_o, _ = O.moments_doubling(H, a, b, I.rademacher_block(3, H.n, R), 256)
+    assert np.abs(longer - mu_o[:128]).max() <= TOL["fp64"]
+    assert np.abs(resumed - mu_o).max() <= TOL["fp64"]
