@@ -147,8 +147,8 @@ typedef struct {
   int R;                  /* random vectors per realisation, >= 1 */
   int S;                  /* realisations, >= 1 (0 is read as 1) */
   uint64_t seed;          /* random vectors: entry (s, r, i) from (seed, stream 0,
-                             counter (s*R + r)*N + i): Rademacher +-1 (real field)
-                             or exp(2 pi i u) (complex field) */
+                             counter ((s0 + s)*R + r)*N + i): Rademacher +-1 (real
+                             field) or exp(2 pi i u) (complex field) */
   int precision;          /* kpm_precision */
   double a, b;            /* H~ = (H - b)/a, a > 0; never chosen implicitly */
   const void* user_v0;    /* NULL, or an N x R start block (row-major, R
@@ -156,6 +156,13 @@ typedef struct {
                              or device; requires S == 1.  The estimator uses the
                              paper's 1/(N R) normalisation, so the full basis is
                              sqrt(N) times the identity. */
+  int s0;                 /* first realisation: realisation s of this call draws
+                             its vectors as realisation s0 + s of the seed's
+                             sequence (counter ((s0 + s)*R + r)*N + i), so
+                             processes that run s0 = 0, 1, ... of one seed split
+                             one run of S realisations (Sec. II-A-4) between
+                             them.  >= 0, s0 + S <= 2^30; 0 for one process.
+                             Batches and the server take s0 = 0. */
 } kpm_params;
 
 /* Chebyshev moments mu[0..M) (Eqs. (rn), (munr), doubling form), averaged over
@@ -169,6 +176,41 @@ typedef struct {
  * chunk count up to a power of two; dense handles have no such limit). */
 kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu_per_vec,
                        void* stream);
+
+/* Local moments (the local density of states; the paper lists local
+ * quantities among the KPM's uses, Sec. I, and the cited KPM review defines
+ * them): mu_loc[j*M + n] = <i_j| T_n(H~) |i_j> for the nsites sites
+ * i_j = sites[j], from the recursion of Eq. (rn) started on the unit vectors
+ * sqrt(N) e_{i_j} (one vector column per site, so that the estimator's 1/N
+ * normalisation of Eq. (munr) gives the local moment).  The start block is
+ * written on the device from the site indices; nothing N-sized crosses the
+ * bus.  sites is a host array of nsites indices in [0, N) (repeats allowed);
+ * M, a, b and precision as kpm_params; mu_loc host or device (host output
+ * synchronises and reports KPM_EDIVERGE like kpm_moments).  The sum over all
+ * N sites of the local moments is N times the moments of kpm_moments' exact
+ * trace.  The call replaces the handle's resumable state like kpm_moments.
+ * Returns KPM_EINVAL for an index outside [0, N), nsites < 1, a device
+ * pointer for sites, or what kpm_moments rejects with R = nsites. */
+kpm_status kpm_ldos_moments(kpm_handle h, const int64_t* sites, int nsites, int M, double a,
+                            double b, int precision, double* mu_loc, void* stream);
+
+/* Momentum-resolved moments (the spectral function A(k, E); the paper names
+ * spectral functions among the KPM's uses, Sec. I):
+ *   mu_k[j*M + n] = <k_j| T_n(H~) |k_j>,  |k> = N^{-1/2} sum_x e^{i k.x} |x>,
+ * for nk wave vectors k_j = (k[3j], k[3j+1], k[3j+2]) in radians per lattice
+ * spacing (components beyond the lattice's dims are ignored; x are the
+ * integer site coordinates of kpm_stencil_desc).  The Jackson-damped series
+ * of these moments (kpm_dos) is A(k_j, E); on a clean periodic lattice with
+ * k on the reciprocal grid (k_d = 2 pi m_d / L_d) the plane wave is an
+ * eigenvector and mu_n = T_n(E~(k)) exactly.  The plane waves are written on
+ * the device.  Complex field: one vector column per wave vector.  Real
+ * field: the columns cos(k.x) and sin(k.x), whose moments add up to those of
+ * the plane wave because H~ is real symmetric (a device kernel adds the
+ * pairs).  Stencil handles only (CSR and dense handles carry no lattice
+ * coordinates: KPM_EINVAL); k a host array; mu_k host or device; M, a, b,
+ * precision and errors as kpm_moments; replaces the resumable state. */
+kpm_status kpm_spectral_moments(kpm_handle h, const double* k, int nk, int M, double a, double b,
+                                int precision, double* mu_k, void* stream);
 
 /* Checkpoint and resume (the paper has no counterpart; a library service):
  * continues the realisation of the most recent kpm_moments call on `h` to M

@@ -34,6 +34,11 @@ Rev. Mod. Phys. 78, 275 (2006)):
                          site) by the Gauss-Chebyshev rule on the DOS nodes       [pinned]
   ldos_exact             local moments <i|T_n(H~)|i> = sum_k |U_ik|^2 T_n(E~_k)
                          (the KPM review's local DOS, a unit start vector)      [pinned]
+  plane_waves            e^{i k.x} on the lattice sites (site i = x0 + L0 (x1 + L1 x2)),
+                         the start vectors of momentum-resolved moments          [pinned]
+  spectral_exact         <k|T_n(H~)|k> = sum_m |<k|u_m>|^2 T_n(E~_m) for the
+                         normalised plane wave |k> (the review's spectral
+                         function A(k, E) expanded in Chebyshev moments)         [pinned]
   dos_many, stats        the DOS of each vector's moments (Eq. (fKPM)), and the
                          mean and standard error over the independent vectors
                          of the moments and of the DOS (the spread behind the
@@ -54,7 +59,7 @@ __all__ = [
     "CSR", "lattice_hamiltonian", "dense", "from_dense", "gershgorin", "lanczos_bounds", "rescale",
     "moments_direct", "moments_doubling", "exact_moments", "jackson_kernel", "dos",
     "lorentz_kernel", "damping", "dos_many", "stats", "dos_error_integral", "ldos_exact",
-    "green", "thermo",
+    "green", "thermo", "plane_waves", "spectral_exact",
 ]
 
 
@@ -386,6 +391,34 @@ def ldos_exact(H: CSR, a: float, b: float, sites, M: int) -> np.ndarray:
     T = np.cos(np.arange(M)[:, None] * np.arccos(x)[None, :])  # [M, N]
     W = np.abs(U[np.asarray(sites, dtype=np.int64), :]) ** 2      # [sites, N]
     return W @ T.T
+
+
+def plane_waves(L, k) -> np.ndarray:
+    """Columns e^{i k_j . x} (not normalised: |column|^2 = N) for the wave vectors
+    k[j] (radians per lattice spacing, one component per lattice dimension), x the
+    integer coordinates of site i = x0 + L0 (x1 + L1 x2).  Returns [N, nk] complex."""
+    L = tuple(int(v) for v in L)
+    k = np.atleast_2d(np.asarray(k, dtype=np.float64))[:, :len(L)]
+    N = int(np.prod(L))
+    i = np.arange(N)
+    coords = []
+    for Ld in L:                      # x_d = (i // (L0 ... L_{d-1})) mod L_d
+        coords.append(i % Ld)
+        i = i // Ld
+    X = np.stack(coords, axis=1).astype(np.float64)  # [N, dims]
+    return np.exp(1j * (X @ k.T))
+
+
+def spectral_exact(H: CSR, a: float, b: float, L, k, M: int) -> np.ndarray:
+    """Momentum-resolved moments <k|T_n(H~)|k> = sum_m |<k|u_m>|^2 cos(n arccos E~_m)
+    for the normalised plane waves |k> = N^{-1/2} sum_x e^{i k.x}|x>, from a dense
+    eigendecomposition (small N only).  Returns [nk, M]."""
+    lam, U = np.linalg.eigh(dense(H))
+    x = np.clip((lam - b) / a, -1.0, 1.0)
+    T = np.cos(np.arange(M)[:, None] * np.arccos(x)[None, :])  # [M, N]
+    P = plane_waves(L, k) / math.sqrt(H.n)                        # [N, nk]
+    W = np.abs(U.conj().T @ P) ** 2                                # [N eigen, nk]
+    return W.T @ T.T
 
 
 def jackson_kernel(M: int) -> np.ndarray:

@@ -150,6 +150,7 @@ void free_work(kpm_handle_s* h) {
   dfree(w.sums);
   dfree(w.per_vec);  // w.mu points into per_vec
   dfree(w.v0stage);
+  dfree(w.sb_dev);
   if (w.ev[0]) cudaEventDestroy(w.ev[0]);
   if (w.ev[1]) cudaEventDestroy(w.ev[1]);
   w = kpm_handle_s::Work{};
@@ -779,8 +780,15 @@ kpm_status kpm_bounds(kpm_handle h, int lanczos_steps, double pad_eps, uint64_t 
   return KPM_OK;
 }
 
-kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu_per_vec,
-                       void* stream) {
+}  // extern "C"
+
+namespace kpm {
+// The moment computation behind kpm_moments, kpm_ldos_moments and
+// kpm_spectral_moments.  sb.kind != START_RANDOM replaces the random block by
+// a start block built on the device (see StartBlock); with internal = true
+// both outputs may be NULL (the caller reads w.per_vec itself).
+kpm_status moments_impl(kpm_handle h, const kpm_params* p, double* mu, double* mu_per_vec,
+                        void* stream, const StartBlock& sb, bool internal) {
   if (!h) return fail(KPM_EINVAL, "handle is NULL");
   if (!p) return fail(KPM_EINVAL, "params is NULL");
   const int M = p->M, R = p->R, S = p->S > 0 ? p->S : 1;
@@ -791,10 +799,14 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
   if (p->precision != KPM_FP64 && p->precision != KPM_FP32_VEC_FP64_MOM)
     return fail(KPM_EINVAL, "bad precision");
   if (p->user_v0 && S != 1) return fail(KPM_EINVAL, "user_v0 requires S == 1");
+  if (p->s0 < 0 || (int64_t)p->s0 + S > ((int64_t)1 << 30))
+    return fail(KPM_EINVAL, "s0 must be >= 0 with s0 + S <= 2^30");
   if (h->dense && p->precision != KPM_FP64)
     return fail(KPM_EINVAL, "dense handles compute in FP64 (the paper's formulation)");
-  if (!mu && !mu_per_vec) return fail(KPM_EINVAL, "no output requested");
+  if (!mu && !mu_per_vec && !internal) return fail(KPM_EINVAL, "no output requested");
   if ((int64_t)S * R * (int64_t)M > ((int64_t)1 << 40)) return fail(KPM_EINVAL, "S*R*M too large");
+  if (sb.kind != START_RANDOM && (S != 1 || p->user_v0))
+    return fail(KPM_EINVAL, "a device-built start block takes S = 1 and no user_v0");
   const bool fp32 = p->precision == KPM_FP32_VEC_FP64_MOM;
   int Rp, G;
   padded_width(R, fp32, h->cplx, &Rp, &G);
@@ -812,7 +824,7 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
   KPM_CUDA(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int slot = fp32 ? 1 : 0;
-  const bool user_v0 = p->user_v0 != nullptr;
+  const bool user_v0 = p->user_v0 != nullptr || sb.kind != START_RANDOM;
   const int steps = M / 2;
   auto& w = h->work;
   kpm_status s_ = ensure_scaled(h, slot, fp32);
@@ -946,13 +958,34 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
   prm.b = p->b;
   prm.seed = (unsigned long long)p->seed;
   prm.s = 0;
+  prm.s0 = p->s0;
   prm.R = R;
   prm.S = S;
   prm.M = M;
   prm.flags = 0;
   KPM_CUDA(cudaMemcpyAsync(h->d_prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st));
   KPM_CUDA(prescale(h, slot, fp32, false, st));
-  if (user_v0) {
+  if (sb.kind != START_RANDOM) {
+    // the start block's parameters (site indices or wave vectors) go to the
+    // device; the block itself is written there by one kernel
+    const size_t pb = (size_t)sb.count * (sb.kind == START_PLANE_WAVES ? 3 : 1) * 8;
+    if (w.sb_bytes < pb) {
+      KPM_CUDA(cudaStreamSynchronize(st));
+      dfree(w.sb_dev);
+      w.sb_dev = nullptr;
+      w.sb_bytes = 0;
+      {
+        kpm_status sa = dalloc((char**)&w.sb_dev, pb);
+        if (sa != KPM_OK) return sa;
+      }
+      w.sb_bytes = pb;
+    }
+    KPM_CUDA(cudaMemcpyAsync(w.sb_dev, sb.kind == START_PLANE_WAVES ? (const void*)sb.k
+                                                                    : (const void*)sb.sites,
+                             pb, cudaMemcpyHostToDevice, st));
+    KPM_CUDA(launch_start_block(fp32, h->cplx, sb.kind, h->n, R, Rp, w.sb_dev, h->geom,
+                                w.v[0], st));
+  } else if (user_v0) {
     const size_t vb = (size_t)h->n * R * (h->cplx ? 2 : 1) * sizeof(double);
     const double* src = (const double*)p->user_v0;
     if (!is_device_ptr(p->user_v0)) {
@@ -1009,6 +1042,7 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
     w.res_a = p->a;
     w.res_b = p->b;
     w.res_seed = (unsigned long long)p->seed;
+    w.res_s0 = p->s0;
   }
   KPM_CUDA(launch_finalize(w.sums, S, steps, R, Rp, h->n, M, w.per_vec, w.mu, h->d_prm, st));
   bool host_out = false;
@@ -1031,6 +1065,94 @@ kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu
     if (flags & 1)
       return fail(KPM_EDIVERGE,
                   "a moment left [-1, 1]: the bounds (a, b) do not enclose the spectrum");
+  }
+  return KPM_OK;
+}
+}  // namespace kpm
+
+extern "C" {
+
+kpm_status kpm_moments(kpm_handle h, const kpm_params* p, double* mu, double* mu_per_vec,
+                       void* stream) {
+  return moments_impl(h, p, mu, mu_per_vec, stream, StartBlock{}, false);
+}
+
+kpm_status kpm_ldos_moments(kpm_handle h, const int64_t* sites, int nsites, int M, double a,
+                            double b, int precision, double* mu_loc, void* stream) {
+  if (!h) return fail(KPM_EINVAL, "handle is NULL");
+  if (!sites || nsites < 1) return fail(KPM_EINVAL, "need nsites >= 1 site indices");
+  if (!mu_loc) return fail(KPM_EINVAL, "mu_loc is NULL");
+  if (is_device_ptr(sites)) return fail(KPM_EINVAL, "sites must be a host array");
+  for (int j = 0; j < nsites; ++j)
+    if (sites[j] < 0 || sites[j] >= h->n) return fail(KPM_EINVAL, "site index outside [0, N)");
+  kpm_params p{};
+  p.M = M;
+  p.R = nsites;
+  p.S = 1;
+  p.precision = precision;
+  p.a = a;
+  p.b = b;
+  StartBlock sb;
+  sb.kind = START_UNIT_SITES;
+  sb.sites = sites;
+  sb.count = nsites;
+  return moments_impl(h, &p, nullptr, mu_loc, stream, sb, false);
+}
+
+kpm_status kpm_spectral_moments(kpm_handle h, const double* k, int nk, int M, double a, double b,
+                                int precision, double* mu_k, void* stream) {
+  if (!h) return fail(KPM_EINVAL, "handle is NULL");
+  if (!h->stencil) return fail(KPM_EINVAL, "plane waves need a lattice: a stencil handle");
+  if (!k || nk < 1) return fail(KPM_EINVAL, "need nk >= 1 wave vectors");
+  if (!mu_k) return fail(KPM_EINVAL, "mu_k is NULL");
+  if (is_device_ptr(k)) return fail(KPM_EINVAL, "k must be a host array");
+  for (int j = 0; j < 3 * nk; ++j)
+    if (!isfinite(k[j])) return fail(KPM_EINVAL, "non-finite wave vector component");
+  // complex field: one column e^{i k.x} per wave vector; real field: the
+  // columns cos(k.x) and sin(k.x), whose moments add up to those of the plane
+  // wave because H~ is real symmetric
+  const int per = h->cplx ? 1 : 2;
+  if ((int64_t)nk * per > (1 << 20)) return fail(KPM_EINVAL, "too many wave vectors");
+  kpm_params p{};
+  p.M = M;
+  p.R = nk * per;
+  p.S = 1;
+  p.precision = precision;
+  p.a = a;
+  p.b = b;
+  StartBlock sb;
+  sb.kind = START_PLANE_WAVES;
+  sb.k = k;
+  sb.count = nk;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (per == 1) return moments_impl(h, &p, nullptr, mu_k, stream, sb, false);
+  kpm_status r = moments_impl(h, &p, nullptr, nullptr, stream, sb, true);
+  if (r != KPM_OK) return r;
+  auto& w = h->work;
+  const bool dev = is_device_ptr(mu_k);
+  double* out = mu_k;
+  if (!dev) {
+    // host output: the pair sums are staged in the handle's staging buffer
+    const size_t ob = (size_t)nk * M * sizeof(double);
+    if (w.v0stage_bytes < ob) {
+      KPM_CUDA(cudaStreamSynchronize(st));
+      dfree(w.v0stage);
+      w.v0stage = nullptr;
+      w.v0stage_bytes = 0;
+      kpm_status sa = dalloc((char**)&w.v0stage, ob);
+      if (sa != KPM_OK) return sa;
+      w.v0stage_bytes = ob;
+    }
+    out = w.v0stage;
+  }
+  KPM_CUDA(launch_pair_sum(w.per_vec, nk, M, out, st));
+  if (!dev) {
+    int flags = 0;
+    KPM_CUDA(cudaMemcpyAsync(mu_k, out, (size_t)nk * M * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KPM_CUDA(cudaMemcpyAsync(&flags, &h->d_prm->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KPM_CUDA(cudaStreamSynchronize(st));
+    if (flags & 1)
+      return fail(KPM_EDIVERGE, "a moment left [-1, 1]: the bounds (a, b) do not enclose the spectrum");
   }
   return KPM_OK;
 }
@@ -1087,6 +1209,7 @@ kpm_status kpm_moments_extend(kpm_handle h, int M, double* mu, double* mu_per_ve
   prm.b = w.res_b;
   prm.seed = w.res_seed;
   prm.s = 0;
+  prm.s0 = w.res_s0;
   prm.R = R;
   prm.S = 1;
   prm.M = M;

@@ -34,7 +34,7 @@ struct RunParams {
   int S;
   int M;
   int flags;                // bit0: diverged
-  int pad;
+  int s0;                   // realisation index of s = 0 in the random-vector counters
 };
 
 // ----------------------------------------------------------------- kernel launchers

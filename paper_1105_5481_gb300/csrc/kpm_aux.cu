@@ -89,7 +89,7 @@ template <typename T, bool CPLX>
 __global__ void rng_init_kernel(int64_t n, int Rp, const RunParams* __restrict__ prm, T* v0) {
   const int R = prm->R;
   const unsigned long long seed = prm->seed;
-  const unsigned long long s = (unsigned long long)prm->s;
+  const unsigned long long s = (unsigned long long)(prm->s + prm->s0);
   const int64_t total = n * Rp;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x)
@@ -111,6 +111,61 @@ __global__ void load_v0_kernel(int64_t n, int R, int Rp, const double* __restric
     } else {
       v0[e] = r < R ? (T)src[i * R + r] : T(0);
     }
+  }
+}
+
+// Start blocks built on the device.  Unit sites (local moments): column r is
+// sqrt(N) e_{sites[r]}, so that the estimator's 1/N normalisation of
+// Eq. (munr) gives <i|T_n(H~)|i>.  Plane waves (momentum-resolved moments):
+// column r (complex field) is e^{i k_r . x}, x the lattice coordinates of the
+// site; on the real field columns 2j and 2j+1 are cos(k_j . x) and
+// sin(k_j . x).  Either way |column|^2 = N (a pair's two columns together).
+template <typename T, bool CPLX>
+__global__ void start_block_kernel(int kind, int64_t n, int R, int Rp, const void* __restrict__ params,
+                                   StencilGeom g, T* v0) {
+  const int64_t total = n * Rp;
+  const double root_n = sqrt((double)n);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / Rp;
+    const int r = (int)(e % Rp);
+    double re = 0.0, im = 0.0;
+    if (r < R) {
+      if (kind == 1) {
+        if (reinterpret_cast<const int64_t*>(params)[r] == i) re = root_n;
+      } else {
+        const int j = CPLX ? r : r / 2;
+        const double* k = reinterpret_cast<const double*>(params) + 3 * (size_t)j;
+        double phase = 0.0;
+        for (int d = 0; d < g.dims; ++d) phase += k[d] * (double)((i / g.stride[d]) % g.L[d]);
+        double sv, cv;
+        sincos(phase, &sv, &cv);
+        if (CPLX) {
+          re = cv;
+          im = sv;
+        } else {
+          re = (r & 1) ? sv : cv;
+        }
+      }
+    }
+    if (CPLX) {
+      int64_t ore, oim;
+      cplx_offsets<T>(i, r, Rp, ore, oim);
+      v0[ore] = (T)re;
+      v0[oim] = (T)im;
+    } else {
+      v0[e] = (T)re;
+    }
+  }
+}
+
+__global__ void pair_sum_kernel(const double* __restrict__ pv, int npairs, int M,
+                                double* __restrict__ out) {
+  const int64_t total = (int64_t)npairs * M;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / M, m = e % M;
+    out[e] = pv[(2 * j) * M + m] + pv[(2 * j + 1) * M + m];
   }
 }
 
@@ -936,6 +991,24 @@ cudaError_t launch_load_v0(bool fp32, bool cplx, int64_t n, int R, int Rp, const
     if (cplx) load_v0_kernel<double, true><<<g, 256, 0, st>>>(n, R, Rp, src, (double*)v0);
     else load_v0_kernel<double, false><<<g, 256, 0, st>>>(n, R, Rp, src, (double*)v0);
   }
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_start_block(bool fp32, bool cplx, int kind, int64_t n, int R, int Rp,
+                               const void* params, const StencilGeom& g, void* v0, cudaStream_t st) {
+  const unsigned gr = blocks_for(n * Rp, 256);
+  if (fp32) {
+    if (cplx) start_block_kernel<float, true><<<gr, 256, 0, st>>>(kind, n, R, Rp, params, g, (float*)v0);
+    else start_block_kernel<float, false><<<gr, 256, 0, st>>>(kind, n, R, Rp, params, g, (float*)v0);
+  } else {
+    if (cplx) start_block_kernel<double, true><<<gr, 256, 0, st>>>(kind, n, R, Rp, params, g, (double*)v0);
+    else start_block_kernel<double, false><<<gr, 256, 0, st>>>(kind, n, R, Rp, params, g, (double*)v0);
+  }
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_pair_sum(const double* pv, int npairs, int M, double* out, cudaStream_t st) {
+  pair_sum_kernel<<<blocks_for((int64_t)npairs * M, 256), 256, 0, st>>>(pv, npairs, M, out);
   return counted(cudaGetLastError());
 }
 

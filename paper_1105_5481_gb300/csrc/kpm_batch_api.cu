@@ -304,7 +304,8 @@ kpm_status kpm_batch_create(int count, const kpm_handle* handles, const kpm_para
       return fail(KPM_EINVAL, "all instances of a batch must share precision and R");
     if (p.M < 2 || (p.M & 1)) return fail(KPM_EINVAL, "M must be even and >= 2");
     if (!(p.a > 0.0) || !isfinite(p.a) || !isfinite(p.b)) return fail(KPM_EINVAL, "bad a or b");
-    if (p.user_v0 || (p.S > 1)) return fail(KPM_EINVAL, "batched instances take S = 1 and no user_v0");
+    if (p.user_v0 || (p.S > 1) || p.s0 != 0)
+      return fail(KPM_EINVAL, "batched instances take S = 1, s0 = 0 and no user_v0");
   }
   auto* b = new kpm_batch_s();
   b->device = h0->device;

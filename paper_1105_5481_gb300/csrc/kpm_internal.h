@@ -56,6 +56,19 @@ cudaError_t launch_rng_init(bool fp32, bool cplx, int64_t n, int Rp, const RunPa
                             cudaStream_t st);
 cudaError_t launch_load_v0(bool fp32, bool cplx, int64_t n, int R, int Rp, const double* src,
                            void* v0, cudaStream_t st);
+// Start blocks built on the device (local and momentum-resolved moments).
+enum StartKind { START_RANDOM = 0, START_UNIT_SITES = 1, START_PLANE_WAVES = 2 };
+struct StartBlock {
+  int kind = START_RANDOM;
+  const int64_t* sites = nullptr;  // host, START_UNIT_SITES: column j = sqrt(N) e_{sites[j]}
+  const double* k = nullptr;       // host, START_PLANE_WAVES: k[3j..3j+2], column(s) of e^{i k.x}
+  int count = 0;
+};
+// params: int64 site indices (unit sites) or FP64 [count][3] wave vectors
+cudaError_t launch_start_block(bool fp32, bool cplx, int kind, int64_t n, int R, int Rp,
+                               const void* params, const StencilGeom& g, void* v0, cudaStream_t st);
+// out[j*M + n] = pv[(2j)*M + n] + pv[(2j+1)*M + n], j < npairs
+cudaError_t launch_pair_sum(const double* pv, int npairs, int M, double* out, cudaStream_t st);
 cudaError_t launch_reduce_ring(const double* ring, int ring_slots, int first_step, int count,
                                int nCTA, int Rp, const RunParams* prm, int steps_per_real,
                                double* sums, cudaStream_t st);
@@ -113,6 +126,8 @@ size_t elem_bytes(bool fp32, bool cplx);
 
 struct kpm_handle_s;
 namespace kpm {
+kpm_status moments_impl(kpm_handle_s* h, const kpm_params* p, double* mu, double* mu_per_vec,
+                        void* stream, const StartBlock& sb, bool internal);
 // Fills the operator part of a step's arguments from a handle and scaled
 // operator arrays (stencil: hs, ds; CSR/ELL: vals in hs).
 void operator_args(StepArgs& a, const kpm_handle_s* h, void* hs, void* ds, const ScalarBlock* sc,
@@ -188,6 +203,8 @@ struct kpm_handle_s {
     size_t out_bytes = 0;
     double* v0stage = nullptr;
     size_t v0stage_bytes = 0;
+    void* sb_dev = nullptr;   // parameters of a device-built start block
+    size_t sb_bytes = 0;
     cudaGraphExec_t exec = nullptr;
     uint64_t kernels_per_replay = 0;
     bool ready = false;        // buffers and launch plan match the current shape
@@ -196,7 +213,7 @@ struct kpm_handle_s {
     // resumable state of the last kpm_moments call (S == 1): v_{n-1}, v_n in
     // v[], the per-step sums of its steps, and its parameters
     bool resumable = false;
-    int res_steps = 0, res_R = 0;
+    int res_steps = 0, res_R = 0, res_s0 = 0;
     double res_a = 0.0, res_b = 0.0;
     unsigned long long res_seed = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};  // recorded around the step chain in the graph

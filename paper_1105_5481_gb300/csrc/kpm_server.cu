@@ -599,7 +599,8 @@ kpm_status kpm_server_submit(kpm_server s, kpm_handle h, const kpm_params* p, in
   if (!s || !h || !p || !req_id) return fail(KPM_EINVAL, "NULL argument");
   if (p->M < 2 || (p->M & 1)) return fail(KPM_EINVAL, "M must be even and >= 2");
   if (p->R < 1) return fail(KPM_EINVAL, "R must be >= 1");
-  if (p->S > 1 || p->user_v0) return fail(KPM_EINVAL, "served requests take S = 1 and no user_v0");
+  if (p->S > 1 || p->user_v0 || p->s0 != 0)
+    return fail(KPM_EINVAL, "served requests take S = 1, s0 = 0 and no user_v0");
   if (p->precision != KPM_FP64 && p->precision != KPM_FP32_VEC_FP64_MOM)
     return fail(KPM_EINVAL, "bad precision");
   if (!(p->a > 0.0) || !isfinite(p->a) || !isfinite(p->b)) return fail(KPM_EINVAL, "bad a or b");

@@ -45,7 +45,7 @@ class kpm_stencil_desc(C.Structure):
 class kpm_params(C.Structure):
     _fields_ = [("M", C.c_int), ("R", C.c_int), ("S", C.c_int), ("seed", C.c_uint64),
                 ("precision", C.c_int), ("a", C.c_double), ("b", C.c_double),
-                ("user_v0", C.c_void_p)]
+                ("user_v0", C.c_void_p), ("s0", C.c_int)]
 
 
 class kpm_server_stats_t(C.Structure):
@@ -75,6 +75,10 @@ def lib() -> C.CDLL:
         L.kpm_bounds.argtypes = [h, C.c_int, C.c_double, C.c_uint64] + [C.POINTER(C.c_double)] * 4 + [C.c_void_p]
         L.kpm_moments.argtypes = [h, C.POINTER(kpm_params), C.c_void_p, C.c_void_p, C.c_void_p]
         L.kpm_moments_extend.argtypes = [h, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.kpm_ldos_moments.argtypes = [h, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double,
+                                       C.c_int, C.c_void_p, C.c_void_p]
+        L.kpm_spectral_moments.argtypes = [h, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double,
+                                           C.c_int, C.c_void_p, C.c_void_p]
         L.kpm_dos.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                               C.c_void_p, C.c_void_p, C.c_void_p]
         L.kpm_dos_kernel.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
@@ -123,7 +127,8 @@ def lib() -> C.CDLL:
         L.kpm_testing_fail_allocations.argtypes = [C.c_int64]
         for name in ("kpm_create_stencil", "kpm_create_csr", "kpm_create_dense", "kpm_stencil_to_csr",
                      "kpm_bounds",
-                     "kpm_moments", "kpm_moments_extend", "kpm_dos", "kpm_info", "kpm_step_timing",
+                     "kpm_moments", "kpm_moments_extend", "kpm_ldos_moments", "kpm_spectral_moments",
+                     "kpm_dos", "kpm_info", "kpm_step_timing",
                      "kpm_moments_csr_noalloc", "kpm_batch_create", "kpm_batch_run", "kpm_batch_tune",
                      "kpm_batch_set_config", "kpm_batch_info", "kpm_batch_set_rtiles",
                      "kpm_batch_get_rtiles", "kpm_batch_set_resident", "kpm_batch_get_resident",
@@ -285,8 +290,9 @@ def kpm_bounds(h: Handle, lanczos_steps=30, pad_eps=0.01, seed=0, stream=None):
 
 
 def kpm_moments(h: Handle, M, R, a, b, seed=0, S=1, precision="fp64", user_v0=None, per_vec=False,
-                out=None, out_per_vec=None, stream=None, check=True):
+                out=None, out_per_vec=None, stream=None, check=True, s0=0):
     """Chebyshev moments.  Returns mu (and mu_per_vec[S*R, M] if per_vec).
+    s0: realisation index of this call's first realisation in the seed's sequence.
 
     ``out``/``out_per_vec`` may be preallocated float64 arrays or CUDA tensors
     (then the call does not synchronise).  With check=False a KPM_EDIVERGE
@@ -295,6 +301,7 @@ def kpm_moments(h: Handle, M, R, a, b, seed=0, S=1, precision="fp64", user_v0=No
     p.M, p.R, p.S, p.seed = int(M), int(R), int(S), int(seed) & 0xFFFFFFFFFFFFFFFF
     p.precision = PRECISIONS[precision]
     p.a, p.b = float(a), float(b)
+    p.s0 = int(s0)
     v0 = None
     if user_v0 is not None:
         if hasattr(user_v0, "data_ptr"):
@@ -324,17 +331,27 @@ def kpm_moments_extend(h: Handle, M, R=None, per_vec=False, out=None, out_per_ve
     return (mu, pv) if per_vec or out_per_vec is not None else mu
 
 
-def kpm_ldos_moments(h: Handle, sites, M, a, b, precision="fp64", stream=None):
-    """Local Chebyshev moments <i|T_n(H~)|i> of the given sites: kpm_moments with the
-    start block of unit vectors sqrt(N) e_i (the estimator's 1/N normalisation).
-    Returns [len(sites), M]."""
-    sites = np.asarray(sites, dtype=np.int64)
-    n = int(kpm_info(h)["n"])
-    v0 = np.zeros((n, sites.size), dtype=np.complex128 if h.complex else np.float64)
-    v0[sites, np.arange(sites.size)] = np.sqrt(n)
-    _, pv = kpm_moments(h, M, sites.size, a, b, precision=precision, user_v0=v0, per_vec=True,
-                        stream=stream)
-    return pv
+def kpm_ldos_moments(h: Handle, sites, M, a, b, precision="fp64", out=None, stream=None):
+    """Local Chebyshev moments <i|T_n(H~)|i> of the given sites (start vectors
+    built on the device).  Returns [len(sites), M] (numpy unless ``out``, a CUDA
+    tensor of len(sites)*M doubles, is given)."""
+    sites = np.ascontiguousarray(np.atleast_1d(sites), dtype=np.int64)
+    mu = np.zeros((sites.size, int(M))) if out is None else out
+    _check(lib().kpm_ldos_moments(h.raw, _ptr(sites), sites.size, int(M), float(a), float(b),
+                                  PRECISIONS[precision], _ptr(mu), _stream(stream)))
+    return mu
+
+
+def kpm_spectral_moments(h: Handle, k, M, a, b, precision="fp64", out=None, stream=None):
+    """Momentum-resolved moments <k|T_n(H~)|k> of normalised plane waves for the
+    wave vectors k ([nk, 3] or [3], radians per lattice spacing).  Returns
+    [nk, M] (numpy unless ``out``, a CUDA tensor of nk*M doubles, is given)."""
+    k = np.asarray(k, dtype=np.float64)
+    k = np.ascontiguousarray(np.pad(k.reshape(-1, k.shape[-1]), ((0, 0), (0, 3 - k.shape[-1]))))
+    mu = np.zeros((k.shape[0], int(M))) if out is None else out
+    _check(lib().kpm_spectral_moments(h.raw, _ptr(k), k.shape[0], int(M), float(a), float(b),
+                                      PRECISIONS[precision], _ptr(mu), _stream(stream)))
+    return mu
 
 
 def kpm_dos(mu, a, b, K, kernel="jackson", E=None, rho=None, stream=None, lam=None):

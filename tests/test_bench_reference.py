@@ -16,4 +16,5 @@ def test_reference_arm_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
-    assert d["metric"] == "Chebyshev nnz*R*moments/s" and d["config"]["workload"] == "cubic_spin_L64"
+    assert d["metric"] == "Chebyshev nnz*R*moments/s" and d["config"]["workload"] == "csr_spin_dilute_L160"
+    assert d["config"]["M"] == 16 and d["config"]["M_workload"] == 4096   # the M actually timed

@@ -42,6 +42,10 @@ MUTATIONS = {
     "gershgorin_no_abs": ("np.abs(H.val[~on])", "H.val[~on].real"),
     "lanczos_no_residual": ("emax = theta[-1] + bk * abs(S[m - 1, -1])", "emax = theta[-1]"),
     "wrap_missing": ("xn = xn % L[d]", "xn = xn"),
+    "plane_wave_coordinates_swapped": ("coords.append(i % Ld)\n        i = i // Ld",
+                                       "coords.insert(0, i % Ld)\n        i = i // Ld"),
+    "spectral_unnormalised": ("P = plane_waves(L, k) / math.sqrt(H.n)", "P = plane_waves(L, k)"),
+    "spectral_amplitude_not_squared": ("W = np.abs(U.conj().T @ P) ** 2", "W = np.abs(U.conj().T @ P)"),
 }
 
 
@@ -132,6 +136,15 @@ def checks(O):
         mu0[0] = 1.0
         hot = O.thermo(mu0, 2.0, 0.0, 256, [0.0], 0.3, "none")[0]
         check("thermo", abs(hot[0] - 0.5) < 1e-12 and abs(hot[2] - math.log(2)) < 1e-12)
+        # momentum-resolved moments: on a clean periodic lattice a grid plane wave
+        # is an eigenvector with E(k) = -2 t sum_d cos k_d
+        Ls = (5, 3, 4)
+        Hc = O.lattice_hamiltonian(Ls, t=0.9)
+        ac, bc = O.rescale(*O.gershgorin(Hc), eps=0.01)
+        ks = 2 * math.pi * np.array([[1, 0, 0], [2, 1, 3], [0, 2, 1]]) / np.array(Ls)
+        xs = (-1.8 * np.cos(ks).sum(axis=1) - bc) / ac
+        want = np.cos(np.arange(12)[None, :] * np.arccos(xs)[:, None])
+        check("spectral", np.allclose(O.spectral_exact(Hc, ac, bc, Ls, ks, 12), want, atol=1e-10))
     except Exception as e:  # a mutant that crashes is caught too
         fails.append("exception:" + type(e).__name__)
     return fails
