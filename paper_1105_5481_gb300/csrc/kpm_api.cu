@@ -5,6 +5,8 @@
 // of kpm_step_*.cu and kpm_aux.cu.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -165,6 +167,7 @@ StepArgs base_args(const kpm_handle_s* h, int slot, int Rp, int G) {
   a.Gt = std::min(G, BLOCK);
   a.sc = h->d_sc + slot;
   a.geom = h->geom;
+  a.err = &h->d_prm->flags;
   if (h->stencil) {
     a.hs = h->has_hop ? h->d_hs[slot] : nullptr;
     a.ds = h->has_onsite ? h->d_ds[slot] : nullptr;
@@ -201,6 +204,18 @@ cudaError_t launch_op(const kpm_handle_s* h, bool fp32, StepMode mode, const Ste
 // of STEP_CHUNK passes in a grid-stride loop.
 #ifndef KPM_STEP_CHUNK
 #define KPM_STEP_CHUNK 4   // passes per chunk; 0 = one whole lattice line
+#endif
+
+// Default of the TMA-fed ELL step: shared-memory stages, passes per tile,
+// CTAs per SM (0 stages: the plain ELL step).
+#ifndef ELL_TMA_STAGES
+#define ELL_TMA_STAGES 2
+#endif
+#ifndef ELL_TMA_PASSES
+#define ELL_TMA_PASSES 2
+#endif
+#ifndef ELL_TMA_MINB
+#define ELL_TMA_MINB 2
 #endif
 
 void plan_grid(const kpm_handle_s* h, bool fp32, StepArgs& a, int* block, int* grid) {
@@ -248,6 +263,32 @@ void plan_grid(const kpm_handle_s* h, bool fp32, StepArgs& a, int* block, int* g
   int64_t g = std::min<int64_t>(slots, nchunks);
   *block = blk;
   *grid = (int)std::max<int64_t>(g, 1);
+  a.tma_stages = a.tma_passes = a.tma_minb = 0;
+  if (!h->stencil && blk == BLOCK && ell_tma_supported(a, fp32)) {
+    // the TMA-fed step (kpm_step_tma.cu): stages, passes per tile and CTAs per
+    // SM from KPM_ELL_TMA="stages,passes,ctas" ("0" turns it off)
+    int S = ELL_TMA_STAGES, P = ELL_TMA_PASSES, B = ELL_TMA_MINB;
+    if (const char* env = getenv("KPM_ELL_TMA")) {
+      int s_ = 0, p_ = P, b_ = B;
+      if (sscanf(env, "%d,%d,%d", &s_, &p_, &b_) >= 1) {
+        S = s_;
+        P = p_;
+        B = b_;
+      }
+    }
+    if (S > 0 && P > 0) {
+      a.tma_stages = S;
+      a.tma_passes = P;
+      a.tma_minb = B;
+      const int occ_t = std::max(0, std::min(occ_ell_tma_f32(h->cplx, a), 8));
+      const int64_t tiles = (h->n + (int64_t)(BLOCK / a.G) * P - 1) / ((int64_t)(BLOCK / a.G) * P);
+      if (occ_t > 0) {
+        *grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->num_sms * occ_t, tiles));
+      } else {
+        a.tma_stages = a.tma_passes = a.tma_minb = 0;  // does not fit: the plain step
+      }
+    }
+  }
 }
 
 kpm_status ensure_scaled(kpm_handle_s* h, int slot, bool fp32) {
@@ -269,7 +310,8 @@ kpm_status ensure_scaled(kpm_handle_s* h, int slot, bool fp32) {
   } else if (!h->d_vals[slot] && h->nnz > 0) {
     char* p = nullptr;
     const size_t entries = h->ell_w > 0 ? (size_t)h->n * h->ell_w : (size_t)h->nnz;
-    kpm_status st = dalloc(&p, entries * c * s);
+    // + 16 bytes: the TMA-fed ELL step copies the last tile in whole 16-byte units
+    kpm_status st = dalloc(&p, entries * c * s + 16);
     if (st != KPM_OK) return st;
     h->d_vals[slot] = p;
   }
@@ -585,7 +627,8 @@ kpm_status kpm_create_csr(int64_t n, const int64_t* rowptr, const int32_t* col, 
       }
       for (; k < W; ++k) ec[(size_t)i * W + k] = (int32_t)i;  // value stays 0
     }
-    if ((st = dalloc(&h->d_ell_col, ec.size())) != KPM_OK ||
+    // + 4 entries: the TMA-fed ELL step copies the last tile in whole 16-byte units
+    if ((st = dalloc(&h->d_ell_col, ec.size() + 4)) != KPM_OK ||
         (st = dalloc(&h->d_ell_val, ev.size())) != KPM_OK) {
       destroy_handle(h);
       return st;
@@ -1062,6 +1105,8 @@ kpm_status moments_impl(kpm_handle h, const kpm_params* p, double* mu, double* m
     int flags = 0;
     KPM_CUDA(cudaMemcpyAsync(&flags, &h->d_prm->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     KPM_CUDA(cudaStreamSynchronize(st));
+    if (flags & 4)
+      return fail(KPM_ETIMEOUT, "a bounded wait inside the fused step gave up (results invalid)");
     if (flags & 1)
       return fail(KPM_EDIVERGE,
                   "a moment left [-1, 1]: the bounds (a, b) do not enclose the spectrum");
@@ -1151,6 +1196,8 @@ kpm_status kpm_spectral_moments(kpm_handle h, const double* k, int nk, int M, do
     KPM_CUDA(cudaMemcpyAsync(mu_k, out, (size_t)nk * M * sizeof(double), cudaMemcpyDeviceToHost, st));
     KPM_CUDA(cudaMemcpyAsync(&flags, &h->d_prm->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     KPM_CUDA(cudaStreamSynchronize(st));
+    if (flags & 4)
+      return fail(KPM_ETIMEOUT, "a bounded wait inside the fused step gave up (results invalid)");
     if (flags & 1)
       return fail(KPM_EDIVERGE, "a moment left [-1, 1]: the bounds (a, b) do not enclose the spectrum");
   }
@@ -1253,6 +1300,8 @@ kpm_status kpm_moments_extend(kpm_handle h, int M, double* mu, double* mu_per_ve
     int flags = 0;
     KPM_CUDA(cudaMemcpyAsync(&flags, &h->d_prm->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     KPM_CUDA(cudaStreamSynchronize(st));
+    if (flags & 4)
+      return fail(KPM_ETIMEOUT, "a bounded wait inside the fused step gave up (results invalid)");
     if (flags & 1)
       return fail(KPM_EDIVERGE,
                   "a moment left [-1, 1]: the bounds (a, b) do not enclose the spectrum");

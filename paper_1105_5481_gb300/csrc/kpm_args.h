@@ -81,6 +81,13 @@ struct StepArgs {
   // are re-read by the next one).  The batched kernel keeps one direction:
   // there a CTA's own rows of the previous step are still in its L1.
   int reverse;
+  // TMA-fed padded-ELL step (FP32 vectors, MODE_STEP): shared-memory stages,
+  // passes per tile, minimum CTAs per SM of the variant; tma_stages = 0: the
+  // plain step
+  int tma_stages;
+  int tma_passes;
+  int tma_minb;
+  int* err;               // bit 2 set by a bounded wait that ran out (may be NULL)
 };
 
 struct LaunchCfg {

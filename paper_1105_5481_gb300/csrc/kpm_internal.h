@@ -32,6 +32,11 @@ cudaError_t launch_step_f32(bool stencil, bool cplx, StepMode mode, const StepAr
                             const LaunchCfg& cfg, cudaStream_t st);
 cudaError_t launch_step_f64(bool stencil, bool cplx, StepMode mode, const StepArgs& a,
                             const LaunchCfg& cfg, cudaStream_t st);
+// TMA-fed padded-ELL step (kpm_step_tma.cu): whether `a` admits it, its
+// launch (cfg.grid CTAs of its own size) and its CTAs per SM
+bool ell_tma_supported(const StepArgs& a, bool fp32);
+cudaError_t launch_ell_tma_f32(bool cplx, const StepArgs& a, const LaunchCfg& cfg, cudaStream_t st);
+int occ_ell_tma_f32(bool cplx, const StepArgs& a);
 // occupancy-derived CTAs per SM of the step variant selected by `a`
 int occ_step_f32(bool stencil, bool cplx, const StepArgs& a, int block);
 int occ_step_f64(bool stencil, bool cplx, const StepArgs& a, int block);

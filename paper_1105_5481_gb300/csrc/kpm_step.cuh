@@ -80,6 +80,11 @@ struct ChunkF64 {
   __device__ __forceinline__ void st(double* p) const {
     *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
   }
+  // from shared memory (16-byte aligned)
+  __device__ __forceinline__ void ld_shared(const double* p) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  }
   __device__ __forceinline__ void zero() { v[0] = v[1] = 0.0; }
   __device__ __forceinline__ void set_neg(const ChunkF64& w) { v[0] = -w.v[0]; v[1] = -w.v[1]; }
   __device__ __forceinline__ void half() { v[0] *= 0.5; v[1] *= 0.5; }
@@ -206,6 +211,13 @@ struct ChunkF32 {
                    : "l"(a)
                    : "memory");
     }
+  }
+  // from shared memory (16-byte aligned)
+  __device__ __forceinline__ void ld_shared(const float* a) {
+    const float4 u = *reinterpret_cast<const float4*>(a);
+    const float4 w = *reinterpret_cast<const float4*>(a + 4);
+    p[0] = make_float2(u.x, u.y); p[1] = make_float2(u.z, u.w);
+    p[2] = make_float2(w.x, w.y); p[3] = make_float2(w.z, w.w);
   }
   __device__ __forceinline__ void st(float* a) const {
     asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(a), "f"(p[0].x),

@@ -104,24 +104,35 @@ def _grid_k(L, ms):
     return 2 * math.pi * np.asarray(ms, dtype=np.float64) / np.asarray(L, dtype=np.float64)
 
 
-@pytest.mark.parametrize("complex_,prec", [(False, "fp64"), (False, "fp32"), (True, "fp64"),
+# FP32 vectors on a single eigenstate: the scaled operator's coefficients are
+# rounded to FP32 (relative error u = 2^-24), which moves the state's rescaled
+# energy x = cos(theta) by up to about 2u; mu_n = cos(n theta) then moves by up
+# to n |d theta| = 2 n u / sin(theta).  Many states (the DOS moments of random
+# vectors) average this out, one sharp state does not, so the FP32 path is held
+# to 4 n u / sin(theta) + 1e-6 per moment here and the FP64 path to 1e-10.
+@pytest.mark.parametrize("complex_,prec", [(False, "fp64"), (True, "fp64"), (False, "fp32"),
                                            (True, "fp32")])
 def test_spectral_clean_lattice_closed_form(K, complex_, prec):
     # clean periodic lattice: the plane wave e^{i k.x} with k on the reciprocal
     # grid is an eigenvector, E(k) = -2 |t| sum_d cos(k_d + arg t) (H_ij = -t on
     # forward bonds), so mu_n = cos(n arccos E~(k)); a complex t makes E(k)
     # differ from E(-k), which pins the sign of the phase
-    L = (8, 6, 5)
+    L, M = (8, 6, 5), 200
     t = complex(math.cos(0.4), math.sin(0.4)) if complex_ else 1.0
     H = O.lattice_hamiltonian(L, t=t)
     a, b = O.rescale(*O.gershgorin(H), eps=0.01)
     k = _grid_k(L, [[0, 0, 0], [1, 0, 0], [7, 0, 0], [3, 2, 1], [5, 4, 4], [4, 3, 0]])
     arg = math.atan2(t.imag, t.real) if complex_ else 0.0
     E = -2 * abs(t) * np.cos(k + arg).sum(axis=1)
-    expect = np.cos(np.arange(200)[None, :] * np.arccos((E - b) / a)[:, None])
+    theta = np.arccos((E - b) / a)
+    expect = np.cos(np.arange(M)[None, :] * theta[:, None])
     with K.kpm_create_stencil(3, L, t=t, complex_=complex_) as h:
-        got = K.kpm_spectral_moments(h, k, 200, a, b, precision=prec)
-    assert np.abs(got - expect).max() <= TOL[prec]
+        got = K.kpm_spectral_moments(h, k, M, a, b, precision=prec)
+    if prec == "fp64":
+        tol = TOL["fp64"]
+    else:
+        tol = 4 * np.arange(M)[None, :] * 2.0**-24 / np.sin(theta)[:, None] + 1e-6
+    assert np.all(np.abs(got - expect) <= tol)
 
 
 @pytest.mark.parametrize("complex_,prec", [(False, "fp64"), (True, "fp64"), (True, "fp32")])
