@@ -61,6 +61,7 @@ STEP_SOURCES = ["paper_1105_5481_gb300/csrc/kpm_step.cuh",
                 "paper_1105_5481_gb300/csrc/kpm_step_dispatch.cuh",
                 "paper_1105_5481_gb300/csrc/kpm_step_f32.cu",
                 "paper_1105_5481_gb300/csrc/kpm_args.h"]
+TMA_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_step_tma.cu"]
 BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_batch_res.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_chunk16.cuh",
@@ -71,7 +72,7 @@ BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
 # them), keyed by workload and launch configuration, with the hash of the
 # kernel sources it was taken on; reported only while the hash matches.
 MEASURED_TRAFFIC = {"cubic_spin_L64": (347.67e6, "step", "3b00c719cc0d365a"),
-                    "csr_spin_dilute_L160": (3438.84e6, "step", "3b00c719cc0d365a"),
+                    "csr_spin_dilute_L160": (3394.69e6, "tma", "cfacec4b7335f84e"),
                     "batch_2d_256/C4/chunk4/clusters74/rt1/top0": (68.05e9, "batch", "721b534bb2268f1c"),
                     "batch_2d_256/C4/chunk2/clusters74/rt2/top8": (59.14e9, "batch", "721b534bb2268f1c")}
 
@@ -84,7 +85,7 @@ def step_source_hash(kind="step"):
     import hashlib
 
     h = hashlib.sha256()
-    for f in (STEP_SOURCES if kind == "step" else BATCH_SOURCES):
+    for f in {"step": STEP_SOURCES, "tma": TMA_SOURCES, "batch": BATCH_SOURCES}[kind]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -516,7 +517,8 @@ def headline_leg(args):
                        "parallelism": f"replicas x{world}", "setup_s": setup_s},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                          "frac": ach / hbm, "traffic": measured_traffic(HEADLINE),
-                         "kernel": "cheb_step_kernel<float, complex, STEP, EllOp<6>>",
+                         "kernel": "ell_tma_step_kernel<float, complex, W=6> (TMA-fed, "
+                                   "2 stages x 64 rows, 2 CTAs/SM)",
                          "bytes_per_launch": bytes_step, "launch_ms": step_ms,
                          "peak_kind": f"{peak_kind} (copy bandwidth)"},
             "per_matvec": per_matvec(value),
@@ -1025,7 +1027,7 @@ def main():
                     help="--profile with the batch workload: instances tiled (0: all)")
     ap.add_argument("--workload", default=HEADLINE,
                     choices=[HEADLINE, "cubic_spin_L64", "batch_2d_256", "serve_poisson",
-                             "square_L32_fp64", "dense_wigner_D4096"],
+                             "square_L32_fp64", "dense_wigner_D4096", "csr_spin_dilute_L100"],
                     help="csr_spin_dilute_L160 (default: the headline line with the other "
                          "configurations as extra keys) or one configuration alone")
     ap.add_argument("--profile", default=None, choices=["fp32", "fp64", "bounds"],
@@ -1039,6 +1041,8 @@ def main():
                            args.batch_chunk_bytes, args.batch_rtiles, args.batch_top)
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         return relaunch_distributed(args)
+    if args.workload == "csr_spin_dilute_L100":
+        ap.error("csr_spin_dilute_L100 (a smaller lattice for profiler captures) is for --profile only")
     if args.workload != HEADLINE:
         return single_leg(args)
     return headline_leg(args)

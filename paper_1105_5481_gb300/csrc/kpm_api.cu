@@ -264,22 +264,26 @@ void plan_grid(const kpm_handle_s* h, bool fp32, StepArgs& a, int* block, int* g
   *block = blk;
   *grid = (int)std::max<int64_t>(g, 1);
   a.tma_stages = a.tma_passes = a.tma_minb = 0;
+  a.tma_prefetch = -1;
   if (!h->stencil && blk == BLOCK && ell_tma_supported(a, fp32)) {
     // the TMA-fed step (kpm_step_tma.cu): stages, passes per tile and CTAs per
-    // SM from KPM_ELL_TMA="stages,passes,ctas" ("0" turns it off)
-    int S = ELL_TMA_STAGES, P = ELL_TMA_PASSES, B = ELL_TMA_MINB;
+    // SM and L2 prefetch distance in tiles (negative: none) from
+    // KPM_ELL_TMA="stages,passes,ctas[,prefetch]" ("0" turns the form off)
+    int S = ELL_TMA_STAGES, P = ELL_TMA_PASSES, B = ELL_TMA_MINB, D = -1;
     if (const char* env = getenv("KPM_ELL_TMA")) {
-      int s_ = 0, p_ = P, b_ = B;
-      if (sscanf(env, "%d,%d,%d", &s_, &p_, &b_) >= 1) {
+      int s_ = 0, p_ = P, b_ = B, d_ = -1;
+      if (sscanf(env, "%d,%d,%d,%d", &s_, &p_, &b_, &d_) >= 1) {
         S = s_;
         P = p_;
         B = b_;
+        D = d_;
       }
     }
     if (S > 0 && P > 0) {
       a.tma_stages = S;
       a.tma_passes = P;
       a.tma_minb = B;
+      a.tma_prefetch = D;
       const int occ_t = std::max(0, std::min(occ_ell_tma_f32(h->cplx, a), 8));
       const int64_t tiles = (h->n + (int64_t)(BLOCK / a.G) * P - 1) / ((int64_t)(BLOCK / a.G) * P);
       if (occ_t > 0) {

@@ -87,6 +87,8 @@ struct StepArgs {
   int tma_stages;
   int tma_passes;
   int tma_minb;
+  int tma_prefetch;       // >= 0: L2 prefetch of the off-tile neighbour rows of the tile
+                          // that many tiles ahead; < 0: none
   int* err;               // bit 2 set by a bounded wait that ran out (may be NULL)
 };
 

@@ -80,7 +80,7 @@ def test_tma_step_matches_plain_step_and_oracle(K, name, R):
     mu_p, pv_p = _solve(K, kw, cplx, M, R, a, b, seed, "0")
     v0 = I.random_block(seed, H.n, R, cplx)
     _, per_o = O.moments_doubling(H, a, b, v0, M)
-    for tma in ("4,1,2", "2,2,2", "3,1,3", "8,1,2"):
+    for tma in ("4,1,2", "2,2,2", "3,1,3", "8,1,2", "2,2,3", "2,2,2,1", "4,1,2,0"):
         mu_t, pv_t = _solve(K, kw, cplx, M, R, a, b, seed, tma)
         assert np.abs(pv_t - pv_p).max() <= 1e-12, tma
         assert np.abs(pv_t - per_o).max() <= 1e-5, tma
