@@ -71,10 +71,10 @@ BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
 # capture (steady state of consecutive launches, caches not flushed between
 # them), keyed by workload and launch configuration, with the hash of the
 # kernel sources it was taken on; reported only while the hash matches.
-MEASURED_TRAFFIC = {"cubic_spin_L64": (347.67e6, "step", "3b00c719cc0d365a"),
+MEASURED_TRAFFIC = {"cubic_spin_L64": (347.94e6, "step", "1e44674953f97d10"),
                     "csr_spin_dilute_L160": (3394.69e6, "tma", "cfacec4b7335f84e"),
-                    "batch_2d_256/C4/chunk4/clusters74/rt1/top0": (68.05e9, "batch", "721b534bb2268f1c"),
-                    "batch_2d_256/C4/chunk2/clusters74/rt2/top8": (59.14e9, "batch", "721b534bb2268f1c")}
+                    "batch_2d_256/C4/chunk4/clusters74/rt1/top0": (68.85e9, "batch", "01bb4f00f5464de6"),
+                    "batch_2d_256/C4/chunk2/clusters74/rt2/top8": (60.56e9, "batch", "01bb4f00f5464de6")}
 
 # FP64 FMA issue rate of GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flop at the
 # sustained clock.  A dependent-chain probe measured 1.20 TFLOP/s (1.97 GHz).
