@@ -116,9 +116,15 @@ kpm_status kpm_create_csr(int64_t n, const int64_t* rowptr, const int32_t* col,
  * be Hermitian to rounding (|H_ij - conj(H_ji)| <= 1e-12 max|H|).  Dense
  * handles compute in FP64 (kpm_moments with KPM_FP64; KPM_FP32_VEC_FP64_MOM
  * returns KPM_EINVAL) and work with kpm_bounds, kpm_moments and the calls
- * built on them, not with the batch or the server.  kpm_info reports
- * nnz = n*n and is_stencil = 0.  Returns KPM_EINVAL for n outside
- * [1, 65536], a NULL H, a non-finite entry or a non-Hermitian H. */
+ * built on them, not with the batch or the server.  For real dense handles
+ * with n >= 512 the product runs on the bf16 tensor cores by the Ozaki
+ * splitting scheme (beta-bit integer slices of H~ and of the vector block,
+ * exact FP32 slice products, recombination in FP64; FP64-accurate results);
+ * complex and smaller handles use the FP64 pipe.  The environment variable
+ * KPM_DENSE_TENSOR=0 or =1, read when a call plans its launches, forces
+ * either form.  kpm_info reports nnz = n*n and is_stencil = 0.  Returns
+ * KPM_EINVAL for n outside [1, 65536], a NULL H, a non-finite entry or a
+ * non-Hermitian H. */
 kpm_status kpm_create_dense(int64_t n, const double* H, kpm_field field, kpm_handle* out);
 
 /* Converts a stencil description into CSR arrays on the host (library-side

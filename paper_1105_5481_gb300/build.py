@@ -71,7 +71,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     tmp = LIB + ".tmp"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
+    # cuBLAS: the plain bf16 GEMMs of the dense formulation's split products
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-L" + cudalib, "-lcublas",
+           "-Xlinker", "-rpath=" + cudalib]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))

@@ -143,9 +143,60 @@ kpm_status check_device(int* dev) {
   return KPM_OK;
 }
 
+void free_dense_tc(kpm_handle_s::Work& w) {
+  if (!w.dtc) return;
+  DenseTC& d = *w.dtc;
+  dense_tc_destroy_blas(d);
+  dfree(d.workspace);
+  dfree(d.A);
+  dfree(d.B);
+  dfree(d.C);
+  dfree(d.row_exp);
+  dfree(d.col_exp);
+  dfree(d.cmax);
+  delete w.dtc;
+  w.dtc = nullptr;
+}
+
+// The dense product of a real FP64 dense handle runs on the tensor cores
+// (kpm_dense_tc.cu) unless KPM_DENSE_TENSOR=0; by default from n = 512 on
+// (below that the FP64 kernel is as fast), always with KPM_DENSE_TENSOR=1.
+bool dense_tc_wanted(const kpm_handle_s* h, bool fp32) {
+  if (!h->dense || h->cplx || fp32) return false;
+  const char* env = getenv("KPM_DENSE_TENSOR");
+  if (env && env[0] == '0') return false;
+  if (env && env[0] == '1') return true;
+  return h->n >= 512;
+}
+
+// Buffers of the tensor-core form; false (and nothing kept) if they do not fit.
+bool setup_dense_tc(kpm_handle_s* h, int Rp) {
+  auto& w = h->work;
+  free_dense_tc(w);
+  auto* d = new DenseTC;
+  d->n = h->n;
+  d->Rp = Rp;
+  dense_tc_split(h->n, &d->beta, &d->k);
+  const size_t n = (size_t)h->n, k = (size_t)d->k;
+  const size_t cbytes = dense_tc_c_floats(h->n, Rp, d->k) * sizeof(float);
+  d->ws_bytes = 32u << 20;
+  bool ok = cbytes <= ((size_t)64 << 30) && dalloc((char**)&d->workspace, d->ws_bytes) == KPM_OK &&
+            dalloc(&d->A, k * n * n) == KPM_OK && dalloc(&d->B, k * n * Rp) == KPM_OK &&
+            dalloc((char**)&d->C, cbytes) == KPM_OK && dalloc(&d->row_exp, n) == KPM_OK &&
+            dalloc(&d->col_exp, (size_t)Rp) == KPM_OK && dalloc(&d->cmax, (size_t)Rp) == KPM_OK;
+  w.dtc = d;
+  if (ok) ok = dense_tc_create_blas(*d) == cudaSuccess;
+  if (!ok) {
+    free_dense_tc(w);
+    t_err.clear();
+  }
+  return ok;
+}
+
 void free_work(kpm_handle_s* h) {
   auto& w = h->work;
   if (w.exec) cudaGraphExecDestroy(w.exec);
+  free_dense_tc(w);
   dfree(w.v[0]);
   dfree(w.v[1]);
   dfree(w.ring);
@@ -193,7 +244,11 @@ cudaError_t launch_step(bool stencil, bool fp32, bool cplx, StepMode mode, const
 // One product of the handle's operator (stencil, CSR / ELL, or dense FP64).
 cudaError_t launch_op(const kpm_handle_s* h, bool fp32, StepMode mode, const StepArgs& a,
                       const LaunchCfg& cfg, cudaStream_t st) {
-  if (h->dense) return fp32 ? cudaErrorInvalidValue : launch_dense_step(h->cplx, mode, a, cfg, st);
+  if (h->dense) {
+    if (fp32) return cudaErrorInvalidValue;
+    if (h->work.dtc && mode != MODE_SPMV) return launch_dense_tc_step(*h->work.dtc, mode, a, cfg, st);
+    return launch_dense_step(h->cplx, mode, a, cfg, st);
+  }
   return launch_step(h->stencil, fp32, h->cplx, mode, a, cfg, st);
 }
 
@@ -966,6 +1021,8 @@ kpm_status moments_impl(kpm_handle h, const kpm_params* p, double* mu, double* m
     int block, grid;
     plan_grid(h, fp32, proto, &block, &grid);
     w.proto = proto;
+    if (dense_tc_wanted(h, fp32)) setup_dense_tc(h, Rp);
+    else free_dense_tc(w);
     dfree(w.ring);
     w.ring = nullptr;
     {
@@ -1012,6 +1069,7 @@ kpm_status moments_impl(kpm_handle h, const kpm_params* p, double* mu, double* m
   prm.flags = 0;
   KPM_CUDA(cudaMemcpyAsync(h->d_prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st));
   KPM_CUDA(prescale(h, slot, fp32, false, st));
+  if (w.dtc) KPM_CUDA(launch_dense_tc_slice_rows(*w.dtc, (const double*)h->d_vals[slot], st));
   if (sb.kind != START_RANDOM) {
     // the start block's parameters (site indices or wave vectors) go to the
     // device; the block itself is written there by one kernel

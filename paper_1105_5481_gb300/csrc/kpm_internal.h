@@ -41,6 +41,29 @@ int occ_ell_tma_f32(bool cplx, const StepArgs& a);
 int occ_step_f32(bool stencil, bool cplx, const StepArgs& a, int block);
 int occ_step_f64(bool stencil, bool cplx, const StepArgs& a, int block);
 
+// Dense products on the bf16 tensor cores by the Ozaki splitting scheme
+// (kpm_dense_tc.cu), real FP64 dense handles: slices of S (per call) and of
+// the current vector block (per step), the exact slice products, exponents.
+struct DenseTC {
+  int64_t n = 0;
+  int Rp = 0, beta = 0, k = 0;
+  void* blas = nullptr;             // cublasHandle_t
+  void* workspace = nullptr;        // the cuBLAS workspace (no allocation during capture)
+  size_t ws_bytes = 0;
+  uint16_t* A = nullptr;            // bf16 [k][n][n]
+  uint16_t* B = nullptr;            // bf16 [k][n][Rp]
+  float* C = nullptr;               // k(k+1)/2 blocks of n x Rp
+  int* row_exp = nullptr;           // [n]
+  int* col_exp = nullptr;           // [Rp]
+  unsigned long long* cmax = nullptr;  // [Rp]
+};
+void dense_tc_split(int64_t n, int* beta, int* k);
+size_t dense_tc_c_floats(int64_t n, int Rp, int k);
+cudaError_t launch_dense_tc_slice_rows(const DenseTC& d, const double* S, cudaStream_t st);
+cudaError_t launch_dense_tc_step(const DenseTC& d, StepMode mode, const StepArgs& a,
+                                 const LaunchCfg& cfg, cudaStream_t st);
+cudaError_t dense_tc_create_blas(DenseTC& d);
+void dense_tc_destroy_blas(DenseTC& d);
 // dense operators (kpm_dense.cu): FP64 only
 cudaError_t launch_dense_step(bool cplx, StepMode mode, const StepArgs& a, const LaunchCfg& cfg,
                               cudaStream_t st);
@@ -215,6 +238,8 @@ struct kpm_handle_s {
     bool ready = false;        // buffers and launch plan match the current shape
     bool direct_done = false;  // one call of this shape ran without a graph
     kpm::StepArgs proto{};                    // launch arguments common to all steps
+    // the dense product on the tensor cores (real FP64 dense handles)
+    kpm::DenseTC* dtc = nullptr;
     // resumable state of the last kpm_moments call (S == 1): v_{n-1}, v_n in
     // v[], the per-step sums of its steps, and its parameters
     bool resumable = false;
