@@ -151,8 +151,8 @@ void free_dense_tc(kpm_handle_s::Work& w) {
   dfree(d.A);
   dfree(d.B);
   dfree(d.C);
-  dfree(d.row_exp);
-  dfree(d.col_exp);
+  dfree(d.row_scale);
+  dfree(d.col_scale);
   dfree(d.cmax);
   delete w.dtc;
   w.dtc = nullptr;
@@ -182,8 +182,8 @@ bool setup_dense_tc(kpm_handle_s* h, int Rp) {
   d->ws_bytes = 32u << 20;
   bool ok = cbytes <= ((size_t)64 << 30) && dalloc((char**)&d->workspace, d->ws_bytes) == KPM_OK &&
             dalloc(&d->A, k * n * n) == KPM_OK && dalloc(&d->B, k * n * Rp) == KPM_OK &&
-            dalloc((char**)&d->C, cbytes) == KPM_OK && dalloc(&d->row_exp, n) == KPM_OK &&
-            dalloc(&d->col_exp, (size_t)Rp) == KPM_OK && dalloc(&d->cmax, (size_t)Rp) == KPM_OK;
+            dalloc((char**)&d->C, cbytes) == KPM_OK && dalloc(&d->row_scale, n) == KPM_OK &&
+            dalloc(&d->col_scale, (size_t)Rp) == KPM_OK && dalloc(&d->cmax, (size_t)Rp) == KPM_OK;
   w.dtc = d;
   if (ok) ok = dense_tc_create_blas(*d) == cudaSuccess;
   if (!ok) {

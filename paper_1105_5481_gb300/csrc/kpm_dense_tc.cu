@@ -16,8 +16,9 @@
 // accumulation holds exactly, because beta is chosen so that n 2^{2 beta} <=
 // 2^24.  The products are plain bf16 GEMMs with FP32 results (cuBLAS): for
 // each t one GEMM of X's slice t with the stacked slices A_1 .. A_{k+1-t}.
-// This file's kernels do the rest: the row and column slicing, and one
-// epilogue that adds the exact partial products level by level in FP64,
+// This file's kernels do the rest: the row and column slicing (integer
+// arithmetic on the FP64 significands), and one epilogue that adds the exact
+// partial products of each level in int32, combines the levels in FP64,
 // applies the exponents, and fuses the Chebyshev recursion (diagonal shift,
 // subtraction of v_{n-1}, in-place store) with the two moment dots of each
 // column, written as per-CTA partials in the layout of the FP64 dense step.
@@ -33,9 +34,49 @@ namespace kpm {
 
 namespace {
 
-// Row slicing of S: one CTA per row (max over the row, then the slices).
+// The balanced beta-bit digits of v 2^-f (|v| 2^-f < 1) in integer
+// arithmetic: F = round(v 2^(beta k - f)) exactly in int64 from the FP64
+// significand (|F| < 2^(beta k) <= 2^56), then a_s = round(F / 2^(beta (k-s)))
+// and F -= a_s 2^(beta (k-s)) for s = 1 .. k, so |a_1| <= 2^beta and |a_s| <=
+// 2^(beta-1) after it; every digit is an exact bf16 integer.
+__device__ __forceinline__ void split_digits(double v, int f, int beta, int k,
+                                             __nv_bfloat16* out, size_t stride) {
+  const long long bits = __double_as_longlong(v);
+  const int bexp = (int)((bits >> 52) & 0x7ff);
+  long long M = bits & 0xFFFFFFFFFFFFFLL;
+  int E;
+  if (bexp == 0) {
+    E = 1 - 1075;
+  } else {
+    M |= (1LL << 52);
+    E = bexp - 1075;
+  }
+  const int sh = E + beta * k - f;
+  long long F = 0;
+  if (M != 0) {
+    if (sh >= 0) F = M << sh;
+    else if (sh > -62) F = (M + (1LL << (-sh - 1))) >> (-sh);
+  }
+  if (bits < 0) F = -F;
+  for (int s = 1; s <= k; ++s) {
+    const int D = beta * (k - s);
+    const long long a = D > 0 ? ((F + (1LL << (D - 1))) >> D) : F;
+    F -= a << D;
+    out[(size_t)(s - 1) * stride] = __int2bfloat16_rn((int)a);
+  }
+}
+
+// Exponent f with m = g 2^f, g in [0.5, 1) (0 for m = 0): |x| <= m < 2^f.
+__device__ __forceinline__ int exponent_of(double m) {
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);
+  return e;
+}
+
+// Row slicing of S: one CTA per row (max over the row, then the digits).
+// row_scale[i] = 2^(e_i - beta (k + 1)).
 __global__ void slice_rows_kernel(int64_t n, const double* __restrict__ S, int beta, int k,
-                                  __nv_bfloat16* __restrict__ A, int* __restrict__ row_exp) {
+                                  __nv_bfloat16* __restrict__ A, double* __restrict__ row_scale) {
   const int64_t i = blockIdx.x;
   const double* row = S + i * n;
   double m = 0.0;
@@ -47,19 +88,10 @@ __global__ void slice_rows_kernel(int64_t n, const double* __restrict__ S, int b
   __syncthreads();
   m = 0.0;
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wm[w]);
-  int e = 0;
-  if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): |S_ij| 2^-e < 1
-  if (threadIdx.x == 0) row_exp[i] = e;
-  const double step = ldexp(1.0, beta);
-  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-    double r = ldexp(row[j], -e);
-    for (int s = 0; s < k; ++s) {
-      const double t = r * step;
-      const double a = rint(t);
-      A[((size_t)s * n + i) * n + j] = __double2bfloat16(a);
-      r = t - a;
-    }
-  }
+  const int e = exponent_of(m);
+  if (threadIdx.x == 0) row_scale[i] = ldexp(1.0, e - beta * (k + 1));
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
+    split_digits(row[j], e, beta, k, A + i * n + j, (size_t)n * n);
 }
 
 // Column maxima of X (n x Rp row-major) as ordered bit patterns of |x|.
@@ -73,38 +105,32 @@ __global__ void col_max_kernel(int64_t n, int Rp, const double* __restrict__ X,
   if (m > 0.0) atomicMax(cmax + j, (unsigned long long)__double_as_longlong(m));
 }
 
-// Column slicing of X into B[t][i][j] and the column exponents.
+// Column slicing of X into B[t][i][j]; col_scale[j] = 2^(f_j).
 __global__ void slice_cols_kernel(int64_t n, int Rp, const double* __restrict__ X,
                                   const unsigned long long* __restrict__ cmax, int beta, int k,
-                                  __nv_bfloat16* __restrict__ B, int* __restrict__ col_exp) {
+                                  __nv_bfloat16* __restrict__ B, double* __restrict__ col_scale) {
   const int64_t total = n * Rp;
-  const double step = ldexp(1.0, beta);
   for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e0 < total;
        e0 += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(e0 % Rp);
-    const double m = __longlong_as_double((long long)cmax[j]);
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);
-    if (e0 < Rp) col_exp[j] = e;
-    double r = ldexp(X[e0], -e);
-    for (int t = 0; t < k; ++t) {
-      const double u = r * step;
-      const double b = rint(u);
-      B[(size_t)t * total + e0] = __double2bfloat16(b);
-      r = u - b;
-    }
+    const int f = exponent_of(__longlong_as_double((long long)cmax[j]));
+    if (e0 < Rp) col_scale[j] = ldexp(1.0, f);
+    split_digits(X[e0], f, beta, k, B + e0, (size_t)total);
   }
 }
 
-// Epilogue: P_ij from the exact slice products, level by level (l = s + t
-// from k + 1 down to 2, smallest terms first), then the recursion and the
-// moment dots.  Block: 64 columns x 4 row lanes; grid (row tiles of bm rows,
-// column tiles of 64), partials of this CTA's columns as the FP64 step.
+// Epilogue: P_ij from the exact slice products.  The products of one level
+// l = s + t (at most k of them, each an integer below 2^24 in magnitude) are
+// added exactly in int32; the levels are combined in FP64 from the smallest
+// (l = k + 1) up, weighted 2^(beta (k + 1 - l)), and scaled by the row and
+// column exponents.  Then the recursion and the moment dots.  Block: 64
+// columns x 4 row lanes; grid (row tiles of bm rows, column tiles of 64),
+// partials of this CTA's columns in the layout of the FP64 dense step.
 template <int MODE>
 __global__ void __launch_bounds__(256) tc_epilogue_kernel(const StepArgs a, const float* __restrict__ C,
                                                           int k, int beta, int bm,
-                                                          const int* __restrict__ row_exp,
-                                                          const int* __restrict__ col_exp) {
+                                                          const double* __restrict__ row_scale,
+                                                          const double* __restrict__ col_scale) {
   const int64_t n = a.n;
   const int Rp = a.Rp;
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
@@ -117,22 +143,23 @@ __global__ void __launch_bounds__(256) tc_epilogue_kernel(const StepArgs a, cons
   const double du = a.sc->du;
   double da = 0.0, db = 0.0;
   if (j < Rp) {
-    const int fj = col_exp[j];
+    const double cs = col_scale[j];
     for (int64_t i = row0 + ty; i < min(n, row0 + bm); i += 4) {
       const size_t o = (size_t)i * Rp + j;
       double total = 0.0;
       for (int l = k + 1; l >= 2; --l) {
-        double lv = 0.0;
-        // terms (s, t) with s + t = l, 1 <= s, t <= k; block of C_t for s:
-        // offset of C_t = sum_{t' < t} (k + 1 - t') blocks, then s - 1
+        int lv = 0;
+        // terms (s, t) with s + t = l; C_t holds the products with A_1 ..
+        // A_{k+1-t}, at block offset sum_{t' < t} (k + 1 - t') + (s - 1)
         for (int t = max(1, l - k); t <= min(k, l - 1); ++t) {
           const int s = l - t;
           const size_t off_t = (size_t)(t - 1) * (k + 1) - (size_t)(t - 1) * t / 2;
-          lv += (double)C[(off_t + (s - 1)) * blk + o];
+          lv += __float2int_rn(C[(off_t + (s - 1)) * blk + o]);
         }
-        total += ldexp(lv, -beta * l);
+        total = fma((double)lv, __longlong_as_double((long long)(1023 + beta * (k + 1 - l)) << 52),
+                    total);
       }
-      const double p = ldexp(total, row_exp[i] + fj);
+      const double p = total * row_scale[i] * cs;
       const double x = X[o];
       double y = fma(du, x, p);
       if (MODE == MODE_FIRST) y *= 0.5;
@@ -175,7 +202,7 @@ size_t dense_tc_c_floats(int64_t n, int Rp, int k) {
 
 cudaError_t launch_dense_tc_slice_rows(const DenseTC& d, const double* S, cudaStream_t st) {
   slice_rows_kernel<<<(unsigned)d.n, 256, 0, st>>>(d.n, S, d.beta, d.k,
-                                                   reinterpret_cast<__nv_bfloat16*>(d.A), d.row_exp);
+                                                   reinterpret_cast<__nv_bfloat16*>(d.A), d.row_scale);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
@@ -191,7 +218,7 @@ cudaError_t launch_dense_tc_step(const DenseTC& d, StepMode mode, const StepArgs
       n, Rp, reinterpret_cast<const double*>(a.x), d.cmax);
   slice_cols_kernel<<<(unsigned)std::min<int64_t>((n * Rp + 255) / 256, 65535LL * 8), 256, 0, st>>>(
       n, Rp, reinterpret_cast<const double*>(a.x), d.cmax, d.beta, d.k,
-      reinterpret_cast<__nv_bfloat16*>(d.B), d.col_exp);
+      reinterpret_cast<__nv_bfloat16*>(d.B), d.col_scale);
   g_launches.fetch_add(2, std::memory_order_relaxed);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   cublasHandle_t h = reinterpret_cast<cublasHandle_t>(d.blas);
@@ -211,9 +238,9 @@ cudaError_t launch_dense_tc_step(const DenseTC& d, StepMode mode, const StepArgs
   const int bm = (int)((n + cfg.grid - 1) / cfg.grid);
   const dim3 g((unsigned)cfg.grid, (unsigned)((Rp + 63) / 64));
   if (mode == MODE_FIRST)
-    tc_epilogue_kernel<MODE_FIRST><<<g, 256, 0, st>>>(a, d.C, d.k, d.beta, bm, d.row_exp, d.col_exp);
+    tc_epilogue_kernel<MODE_FIRST><<<g, 256, 0, st>>>(a, d.C, d.k, d.beta, bm, d.row_scale, d.col_scale);
   else
-    tc_epilogue_kernel<MODE_STEP><<<g, 256, 0, st>>>(a, d.C, d.k, d.beta, bm, d.row_exp, d.col_exp);
+    tc_epilogue_kernel<MODE_STEP><<<g, 256, 0, st>>>(a, d.C, d.k, d.beta, bm, d.row_scale, d.col_scale);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }

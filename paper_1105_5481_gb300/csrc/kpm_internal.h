@@ -53,8 +53,8 @@ struct DenseTC {
   uint16_t* A = nullptr;            // bf16 [k][n][n]
   uint16_t* B = nullptr;            // bf16 [k][n][Rp]
   float* C = nullptr;               // k(k+1)/2 blocks of n x Rp
-  int* row_exp = nullptr;           // [n]
-  int* col_exp = nullptr;           // [Rp]
+  double* row_scale = nullptr;      // [n]: 2^(e_i - beta (k + 1))
+  double* col_scale = nullptr;      // [Rp]: 2^(f_j)
   unsigned long long* cmax = nullptr;  // [Rp]
 };
 void dense_tc_split(int64_t n, int* beta, int* k);
