@@ -106,6 +106,9 @@ void pfree(void* p, cudaStream_t st) {
 // Host-side fault injection for tests (kpm_testing_fail_allocations): the
 // number of dalloc calls that still succeed before one fails; -1 = off.
 std::atomic<long long> g_fail_alloc_after{-1};
+// Testing aid (kpm_testing_stall_step_pipeline): plans made while it is set
+// give the TMA-fed step a producer that issues nothing.
+std::atomic<int> g_test_stall{0};
 
 bool injected_alloc_failure() {
   long long k = g_fail_alloc_after.load();
@@ -320,6 +323,7 @@ void plan_grid(const kpm_handle_s* h, bool fp32, StepArgs& a, int* block, int* g
   *grid = (int)std::max<int64_t>(g, 1);
   a.tma_stages = a.tma_passes = a.tma_minb = 0;
   a.tma_prefetch = -1;
+  a.tma_stall = 0;
   if (!h->stencil && blk == BLOCK && ell_tma_supported(a, fp32)) {
     // the TMA-fed step (kpm_step_tma.cu): stages, passes per tile and CTAs per
     // SM and L2 prefetch distance in tiles (negative: none) from
@@ -339,6 +343,7 @@ void plan_grid(const kpm_handle_s* h, bool fp32, StepArgs& a, int* block, int* g
       a.tma_passes = P;
       a.tma_minb = B;
       a.tma_prefetch = D;
+      a.tma_stall = g_test_stall.load();
       const int occ_t = std::max(0, std::min(occ_ell_tma_f32(h->cplx, a), 8));
       const int64_t tiles = (h->n + (int64_t)(BLOCK / a.G) * P - 1) / ((int64_t)(BLOCK / a.G) * P);
       if (occ_t > 0) {
@@ -553,6 +558,20 @@ extern "C" {
 const char* kpm_last_error(void) { return t_err.c_str(); }
 
 uint64_t kpm_kernel_launches(void) { return g_launches.load(); }
+
+kpm_status kpm_testing_last_step_form(kpm_handle h, int* form) {
+  if (!h || !form) return fail(KPM_EINVAL, "NULL argument");
+  const auto& w = h->work;
+  if (w.M == 0) return fail(KPM_ENOTREADY, "no kpm_moments call has planned its launches yet");
+  if (h->dense) *form = w.dtc ? 3 : 2;
+  else *form = w.proto.tma_stages > 0 ? 1 : 0;
+  return KPM_OK;
+}
+
+kpm_status kpm_testing_stall_step_pipeline(int on) {
+  g_test_stall.store(on ? 1 : 0);
+  return KPM_OK;
+}
 
 kpm_status kpm_testing_fail_allocations(int64_t after) {
   if (after < -1) return fail(KPM_EINVAL, "after must be >= -1");

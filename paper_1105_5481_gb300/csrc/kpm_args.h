@@ -89,6 +89,7 @@ struct StepArgs {
   int tma_minb;
   int tma_prefetch;       // >= 0: L2 prefetch of the off-tile neighbour rows of the tile
                           // that many tiles ahead; < 0: none
+  int tma_stall;          // testing aid: the producer issues no copy (the waits run out)
   int* err;               // bit 2 set by a bounded wait that ran out (may be NULL)
 };
 

@@ -15,7 +15,9 @@
 // v_{n+1} = 2 H~ v_n - v_{n-1} and the dots A = <v_n|v_n>, B = Re<v_{n+1}|v_n>,
 // store v_{n+1} in place over v_{n-1}, and release the stage to the producer
 // through a second mbarrier.  The arithmetic and its order per row are those
-// of EllOp, so a row's v_{n+1} is bitwise the same.
+// of EllOp (explicitly rounded intrinsics); rows go to threads differently,
+// so the compensated FP32 moment dots are summed in another order and the
+// moments differ from the plain step's within that summation's bound.
 //
 // Every wait is bounded (about a second of clock64 cycles).  A wait that runs
 // out sets bit 2 of *a.err, stops the warp's work, and the producer waits
@@ -145,7 +147,10 @@ __global__ void __launch_bounds__(TMA_THREADS, MINB)
     // faster than the same kernel without the branch (589 vs 618 us per step
     // on the L = 160 CSR workload, alternating runs on one GPU), so it stays.
     int64_t issued = 0;
-    for (int64_t k = 0; k < my_tiles; ++k) {
+    // a.tma_stall (a testing aid): issue nothing, so that the consumers'
+    // bounded waits run out and report a timeout
+    const int64_t to_issue = a.tma_stall ? 0 : my_tiles;
+    for (int64_t k = 0; k < to_issue; ++k) {
       const int st = (int)(k % stages);
       bool ok = k < stages || mbar_wait(&empty[st], (uint32_t)((k / stages - 1) & 1));
       if (!__all_sync(0xffffffffu, ok)) {

@@ -125,6 +125,8 @@ def lib() -> C.CDLL:
         L.kpm_last_error.restype = C.c_char_p
         L.kpm_kernel_launches.restype = C.c_uint64
         L.kpm_testing_fail_allocations.argtypes = [C.c_int64]
+        L.kpm_testing_stall_step_pipeline.argtypes = [C.c_int]
+        L.kpm_testing_last_step_form.argtypes = [h, C.POINTER(C.c_int)]
         for name in ("kpm_create_stencil", "kpm_create_csr", "kpm_create_dense", "kpm_stencil_to_csr",
                      "kpm_bounds",
                      "kpm_moments", "kpm_moments_extend", "kpm_ldos_moments", "kpm_spectral_moments",
@@ -135,7 +137,8 @@ def lib() -> C.CDLL:
                      "kpm_batch_set_chunk_bytes", "kpm_batch_get_chunk_bytes",
                      "kpm_server_create",
                      "kpm_server_submit", "kpm_server_wait", "kpm_server_poll", "kpm_server_cancel",
-                     "kpm_server_stats", "kpm_testing_fail_allocations"):
+                     "kpm_server_stats", "kpm_testing_fail_allocations",
+                     "kpm_testing_stall_step_pipeline", "kpm_testing_last_step_form"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -661,3 +664,19 @@ def kpm_testing_fail_allocations(after: int):
     """Testing aid: the next `after` device allocations of the library succeed and
     the one after fails with KPM_ENOMEM (-1 disarms)."""
     _check(lib().kpm_testing_fail_allocations(int(after)))
+
+
+def kpm_testing_stall_step_pipeline(on: bool):
+    """Testing aid: plans made while set give the TMA-fed ELL step a producer that
+    issues nothing, so its bounded waits run out (KPM_ETIMEOUT)."""
+    _check(lib().kpm_testing_stall_step_pipeline(int(bool(on))))
+
+
+STEP_FORMS = {0: "fused step", 1: "TMA-fed ELL step", 2: "dense FP64 pipe", 3: "dense tensor cores"}
+
+
+def kpm_testing_last_step_form(h: Handle) -> str:
+    """Testing aid: the product form the last plan of kpm_moments on h chose."""
+    f = C.c_int()
+    _check(lib().kpm_testing_last_step_form(h.raw, C.byref(f)))
+    return STEP_FORMS[f.value]

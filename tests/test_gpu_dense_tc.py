@@ -30,12 +30,14 @@ def _moments(K, A, M, R, a, b, seed, tensor, user_v0=None):
         with K.kpm_create_dense(A) as h:
             out = [K.kpm_moments(h, M, R, a, b, seed=seed, per_vec=True, user_v0=user_v0)
                    for _ in range(2)]   # a direct call, then the captured graph
+            form = K.kpm_testing_last_step_form(h)
     finally:
         if old is None:
             del os.environ["KPM_DENSE_TENSOR"]
         else:
             os.environ["KPM_DENSE_TENSOR"] = old
     assert np.array_equal(out[0][1], out[1][1])
+    assert form == ("dense tensor cores" if tensor == "1" else "dense FP64 pipe")
     return out[0]
 
 
