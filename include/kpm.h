@@ -413,6 +413,32 @@ kpm_status kpm_batch_set_resident(kpm_batch b, int resident);
  * operator is not a stencil). */
 kpm_status kpm_batch_get_resident(kpm_batch b, int* resident, int* min_cluster);
 
+/* Staged form (staged = 1): the products of Eq. (rn) with the vector rows
+ * brought into shared memory by bulk asynchronous copies (cp.async.bulk)
+ * instead of per-thread loads.  Each instance's rows are cut into tiles of
+ * T consecutive rows (a power of two, about 4 KB x the traversal chunk of
+ * kpm_batch_set_config, 1..4); CTA k of a cluster owns a contiguous band of
+ * tiles, and one thread per CTA copies, several tiles ahead of use, the
+ * band's tiles of v_n with the halo tiles that hold neighbours one lattice
+ * line (or plane) away into a ring of shared-memory stages, and the band's
+ * tiles of v_{n-1} and of the scaled on-site terms into a second ring.  The
+ * rows are computed from shared memory; neighbours across a periodic wrap
+ * beyond the halo are read from global memory; v_{n+1} is stored in place
+ * over v_{n-1}.  The moment identities, partial sums and finalisation are
+ * unchanged.  Stencil operators with rows of at most 32 chunks (R <= 256
+ * real or 128 complex FP32, R <= 64 real or 32 complex FP64; KPM_EINVAL
+ * otherwise); untiled (setting it clears the R-tiling); 32-byte chunks.  An
+ * instance's moments depend only on C, the tile size and the instance, and
+ * agree with the other forms to rounding (the moment dots are summed in
+ * another order).  Every wait inside the kernel is bounded: one that runs
+ * out makes kpm_batch_run with host output return KPM_ETIMEOUT.  staged = 0
+ * returns to the global-memory form. */
+kpm_status kpm_batch_set_staged(kpm_batch b, int staged);
+
+/* Whether the staged form is set, and its tile rows T and v_n ring stages at
+ * the current traversal chunk (any output may be NULL). */
+kpm_status kpm_batch_get_staged(kpm_batch b, int* staged, int* tile_rows, int* stages);
+
 /* Current R-tiles, the number of instances tiled, and the largest R-tiles
  * this batch admits (min(4, G)). */
 kpm_status kpm_batch_get_rtiles(kpm_batch b, int* rtiles, int* top, int* max_rtiles);

@@ -44,6 +44,8 @@ __device__ __forceinline__ void cluster_wait_acquire() {
   asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
 }
 
+constexpr int BATCH_FLAG_TIMEOUT = 2;
+
 struct BatchTask {
   StepArgs a;         // operator, geometry, traversal (x, y, w, partial set per step)
   void* v[2];         // the two vector blocks; step s reads v[s & 1], writes v[(s + 1) & 1]
@@ -55,7 +57,8 @@ struct BatchTask {
   int M, R;
   unsigned long long seed;
   int realisation;
-  int flags;          // set by the kernel: bit0 = a moment left [-1, 1]
+  int flags;          // set by the kernel: bit0 = a moment left [-1, 1],
+                      //   bit1 = a bounded wait ran out (BATCH_FLAG_TIMEOUT)
   // R-tiling: an instance's vector columns split into `ntiles` independent
   // tasks (tile `ycol` holds columns ycol*Rt .. ycol*Rt + Rt - 1, Rt = Gt*VEC);
   // the last tile to finish averages the per-vector moments.  ntiles 0 or 1:

@@ -19,13 +19,18 @@
 
 using namespace kpm;
 
+namespace {
+constexpr int FORM_GLOBAL = 0, FORM_RESIDENT = 1, FORM_STAGED = 2;
+}
+
 struct BatchConfig {
   int C = 4;          // CTAs per cluster
   int chunk = 4;      // passes per traversal chunk
   int frac = 100;     // percent of the co-resident clusters launched
   int rtiles = 1;     // column tiles of a tiled instance (divides the chunks per row)
   int top = 0;        // the `top` instances of largest work are tiled (<= 0: all)
-  int res = 0;        // 1: vector rows resident in the clusters' shared memory
+  int res = 0;        // vector rows: 0 global memory, 1 resident in the clusters' shared
+                      // memory, 2 staged through shared-memory rings (chunk: tile size)
   int tpr = 1;        // threads per row relative to the 32-byte chunk (2: 16-byte chunks)
 };
 
@@ -125,7 +130,44 @@ int max_clusters_res(kpm_batch_s* b, int C) {
                  : max_clusters_batch_res_f64(b->cplx, a, C, cap);
 }
 
+// Tile shape of the staged form: tiles of 2^Tl rows of about 4 KB x `chunk`
+// (at least one pass of the 256 threads), 2^Sl stages of v_n (about 64 KB)
+// and 2^SWl of v_{n-1} (about 32 KB), so that two CTAs fit an SM.
+struct StgShape {
+  int Tl, Sl, SWl;
+};
+StgShape stg_shape(const kpm_batch_s* b, int chunk) {
+  const int rowB = b->G * (b->fp32 ? 32 : 16);
+  int Tl = 0;
+  while ((1 << Tl) < 256 / b->G || (1 << Tl) * rowB < 4096 * std::max(1, chunk)) ++Tl;
+  const size_t tileB = (size_t)rowB << Tl;
+  int Sl = 3, SWl = 3;
+  while (Sl > 2 && ((size_t)1 << Sl) * tileB > 64 * 1024) --Sl;
+  while (SWl > 1 && ((size_t)1 << SWl) * tileB > 32 * 1024) --SWl;
+  // KPM_BATCH_STG="Sl,SWl" sets the ring depths (log2 stages, 2..4 and 1..4)
+  if (const char* env = getenv("KPM_BATCH_STG")) {
+    int a = 0, c = 0;
+    if (sscanf(env, "%d,%d", &a, &c) == 2 && a >= 2 && a <= 4 && c >= 1 && c <= 4) {
+      Sl = a;
+      SWl = c;
+    }
+  }
+  return {Tl, Sl, SWl};
+}
+
+// Whether the staged form applies: stencil operators, rows of at most 32 chunks.
+bool staged_ok(const kpm_batch_s* b) { return b->handles[0]->stencil && b->G <= 32; }
+
+int max_clusters_stg(kpm_batch_s* b, const BatchConfig& c) {
+  if (!staged_ok(b)) return 0;
+  const StgShape sh = stg_shape(b, c.chunk);
+  const StepArgs& a = b->inst_tasks[b->order[0]].a;
+  return b->fp32 ? max_clusters_batch_stg_f32(b->cplx, a, c.C, sh.Tl, sh.Sl, sh.SWl)
+                 : max_clusters_batch_stg_f64(b->cplx, a, c.C, sh.Tl, sh.Sl, sh.SWl);
+}
+
 int cfg_clusters(kpm_batch_s* b, const BatchConfig& c) {
+  if (c.res == FORM_STAGED) return max_clusters_stg(b, c);
   return c.res ? max_clusters_res(b, c.C) : max_clusters(b, c);
 }
 
@@ -143,7 +185,9 @@ kpm_status build_graph(kpm_batch_s* b, const BatchConfig& c) {
   if (c.res && c.rtiles > 1)
     return fail(KPM_EINVAL, "the resident form runs untiled instances (R-tiles 1)");
   if (c.res && !b->handles[0]->stencil)
-    return fail(KPM_EINVAL, "the resident form takes stencil operators only");
+    return fail(KPM_EINVAL, "the resident and staged forms take stencil operators only");
+  if (c.res == FORM_STAGED && !staged_ok(b))
+    return fail(KPM_EINVAL, "the staged form takes rows of at most 32 chunks");
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
@@ -182,7 +226,13 @@ kpm_status build_graph(kpm_batch_s* b, const BatchConfig& c) {
   cudaError_t e = cudaMemsetAsync(b->d_queue, 0, (1 + (size_t)b->count) * sizeof(int), b->cap_stream);
   if (e == cudaSuccess)
     e = cudaEventRecordWithFlags(b->ev[0], b->cap_stream, cudaEventRecordExternal);
-  if (e == cudaSuccess && c.res) {
+  if (e == cudaSuccess && c.res == FORM_STAGED) {
+    const StgShape sh = stg_shape(b, c.chunk);
+    e = b->fp32 ? launch_batch_stg_f32(b->cplx, b->proto, b->d_tasks, ntasks, b->d_queue, b->grid,
+                                       c.C, sh.Tl, sh.Sl, sh.SWl, b->cap_stream)
+                : launch_batch_stg_f64(b->cplx, b->proto, b->d_tasks, ntasks, b->d_queue, b->grid,
+                                       c.C, sh.Tl, sh.Sl, sh.SWl, b->cap_stream);
+  } else if (e == cudaSuccess && c.res) {
     const int64_t cap = res_rows_cap(b, c.C);
     e = b->fp32 ? launch_batch_res_f32(b->cplx, b->proto, b->d_tasks, ntasks, b->d_queue, b->grid,
                                        c.C, cap, b->cap_stream)
@@ -489,6 +539,8 @@ kpm_status kpm_batch_run(kpm_batch b, double* mu, void* stream) {
                         cudaMemcpyDeviceToHost));
     int bad = 0;
     for (auto& t : back) bad |= t.flags;
+    if (bad & BATCH_FLAG_TIMEOUT)
+      return fail(KPM_ETIMEOUT, "a bounded wait of the staged batch kernel ran out");
     if (bad)
       return fail(KPM_EDIVERGE, "a batched instance left [-1, 1]: its bounds miss the spectrum");
   }
@@ -560,6 +612,18 @@ kpm_status kpm_batch_tune(kpm_batch b, int reps, void* stream) {
         c.C = C;
         c.frac = fr;
         c.res = 1;
+        kpm_status s_ = time_cfg(c);
+        if (s_ != KPM_OK) return s_;
+      }
+  // the staged form (stencil operators): every cluster size, tiles of about
+  // 4, 8 and 16 KB
+  if (staged_ok(b))
+    for (int C : Cs)
+      for (int ch : {1, 2, 4}) {
+        BatchConfig c;
+        c.C = C;
+        c.chunk = ch;
+        c.res = FORM_STAGED;
         kpm_status s_ = time_cfg(c);
         if (s_ != KPM_OK) return s_;
       }
@@ -663,7 +727,7 @@ kpm_status kpm_batch_set_resident(kpm_batch b, int resident) {
     return fail(KPM_EINVAL, "the resident form takes stencil operators only");
   if (resident && b->cfg.tpr != 1)
     return fail(KPM_EINVAL, "the resident form runs 32-byte chunks");
-  b->cfg.res = resident;
+  b->cfg.res = resident ? FORM_RESIDENT : FORM_GLOBAL;
   if (resident) {
     b->cfg.rtiles = 1;
     b->cfg.top = 0;
@@ -673,7 +737,7 @@ kpm_status kpm_batch_set_resident(kpm_batch b, int resident) {
 
 kpm_status kpm_batch_get_resident(kpm_batch b, int* resident, int* min_cluster) {
   if (!b) return fail(KPM_EINVAL, "batch is NULL");
-  if (resident) *resident = b->cfg.res;
+  if (resident) *resident = b->cfg.res == FORM_RESIDENT;
   if (min_cluster) {
     KPM_CUDA(cudaSetDevice(b->device));
     *min_cluster = 0;
@@ -684,6 +748,32 @@ kpm_status kpm_batch_get_resident(kpm_batch b, int* resident, int* min_cluster) 
           break;
         }
   }
+  return KPM_OK;
+}
+
+kpm_status kpm_batch_set_staged(kpm_batch b, int staged) {
+  if (!b) return fail(KPM_EINVAL, "batch is NULL");
+  if (staged != 0 && staged != 1) return fail(KPM_EINVAL, "staged must be 0 or 1");
+  if (staged && !staged_ok(b))
+    return fail(KPM_EINVAL, "the staged form takes stencil operators with rows of at most 32 chunks");
+  if (staged && b->cfg.tpr != 1)
+    return fail(KPM_EINVAL, "the staged form runs 32-byte chunks");
+  if (staged) {
+    b->cfg.res = FORM_STAGED;
+    b->cfg.rtiles = 1;
+    b->cfg.top = 0;
+  } else if (b->cfg.res == FORM_STAGED) {
+    b->cfg.res = FORM_GLOBAL;
+  }
+  return KPM_OK;
+}
+
+kpm_status kpm_batch_get_staged(kpm_batch b, int* staged, int* tile_rows, int* stages) {
+  if (!b) return fail(KPM_EINVAL, "batch is NULL");
+  if (staged) *staged = b->cfg.res == FORM_STAGED;
+  const StgShape sh = stg_shape(b, b->cfg.chunk);
+  if (tile_rows) *tile_rows = 1 << sh.Tl;
+  if (stages) *stages = 1 << sh.Sl;
   return KPM_OK;
 }
 

@@ -187,6 +187,17 @@ cudaError_t launch_batch_res_f64(bool cplx, const StepArgs& proto, BatchTask* ta
                                  int* queue, int grid, int C, int64_t rows_cap, cudaStream_t st);
 int max_clusters_batch_res_f32(bool cplx, const StepArgs& proto, int C, int64_t rows_cap);
 int max_clusters_batch_res_f64(bool cplx, const StepArgs& proto, int C, int64_t rows_cap);
+// Staged form (vector tiles copied into shared-memory rings by a producer
+// warp: tiles of 2^Tl rows, 2^Sl stages of v_n, 2^SWl of v_{n-1}; stencil
+// operators, untiled tasks)
+cudaError_t launch_batch_stg_f32(bool cplx, const StepArgs& proto, BatchTask* tasks, int ntasks,
+                                 int* queue, int grid, int C, int Tl, int Sl, int SWl,
+                                 cudaStream_t st);
+cudaError_t launch_batch_stg_f64(bool cplx, const StepArgs& proto, BatchTask* tasks, int ntasks,
+                                 int* queue, int grid, int C, int Tl, int Sl, int SWl,
+                                 cudaStream_t st);
+int max_clusters_batch_stg_f32(bool cplx, const StepArgs& proto, int C, int Tl, int Sl, int SWl);
+int max_clusters_batch_stg_f64(bool cplx, const StepArgs& proto, int C, int Tl, int Sl, int SWl);
 }  // namespace kpm
 
 // The handle (opaque to callers).

@@ -109,6 +109,9 @@ def lib() -> C.CDLL:
         L.kpm_batch_get_chunk_bytes.argtypes = [h, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.kpm_batch_set_resident.argtypes = [h, C.c_int]
         L.kpm_batch_get_resident.argtypes = [h, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.kpm_batch_set_staged.argtypes = [h, C.c_int]
+        L.kpm_batch_get_staged.argtypes = [h, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                           C.POINTER(C.c_int)]
         L.kpm_batch_destroy.argtypes = [h]
         L.kpm_batch_destroy.restype = None
         L.kpm_server_create.argtypes = [C.c_size_t, C.c_int, C.c_int, C.POINTER(h)]
@@ -556,6 +559,18 @@ def kpm_batch_get_resident(bt: Batch):
     on, cmin = C.c_int(), C.c_int()
     _check(lib().kpm_batch_get_resident(bt.raw, C.byref(on), C.byref(cmin)))
     return bool(on.value), cmin.value
+
+
+def kpm_batch_set_staged(bt: Batch, staged=True):
+    """Bring the vector tiles into shared memory by bulk asynchronous copies."""
+    _check(lib().kpm_batch_set_staged(bt.raw, int(bool(staged))))
+
+
+def kpm_batch_get_staged(bt: Batch):
+    """(staged form set, tile rows, v_n ring stages)."""
+    on, tr, st = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().kpm_batch_get_staged(bt.raw, C.byref(on), C.byref(tr), C.byref(st)))
+    return bool(on.value), tr.value, st.value
 
 
 def kpm_batch_info(bt: Batch):

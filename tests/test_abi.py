@@ -78,6 +78,8 @@ def test_batch_entry_points_reject_a_null_batch(K):
     i1, i2 = C.c_int(), C.c_int()
     assert L.kpm_batch_set_resident(None, 1) == K.KPM_EINVAL
     assert L.kpm_batch_get_resident(None, C.byref(i1), C.byref(i2)) == K.KPM_EINVAL
+    assert L.kpm_batch_set_staged(None, 1) == K.KPM_EINVAL
+    assert L.kpm_batch_get_staged(None, C.byref(i1), C.byref(i2), C.byref(i1)) == K.KPM_EINVAL
     assert L.kpm_batch_set_chunk_bytes(None, 16) == K.KPM_EINVAL
     assert L.kpm_batch_get_chunk_bytes(None, C.byref(i1), C.byref(i2)) == K.KPM_EINVAL
     assert L.kpm_batch_set_rtiles(None, 2, 0) == K.KPM_EINVAL
