@@ -576,8 +576,11 @@ kpm_status kpm_testing_fail_allocations(int64_t after);
 
 /* Testing aid (the paper has no counterpart): with on != 0, kpm_moments calls
  * that plan their launches from now on (a new handle, or a new shape) give
- * the TMA-fed padded-ELL step (FP32 vectors on a CSR handle with short rows) a
- * producer that issues no copy, so the consumers' bounded waits run out
+ * the TMA-fed padded-ELL step (FP32 vectors on a CSR handle with short rows)
+ * and the TMA-fed stencil step (FP32 vectors on a 2D or 3D stencil handle,
+ * where the environment variable KPM_STENCIL_TMA selects it) a producer that
+ * issues no copy, so
+ * the consumers' bounded waits run out
  * (after about a second per step) and the call returns KPM_ETIMEOUT with its
  * outputs invalid; the context stays usable.  on = 0 stops it for plans made
  * afterwards.  Process-wide.  Always returns KPM_OK. */
@@ -587,7 +590,8 @@ kpm_status kpm_testing_stall_step_pipeline(int on);
  * the most recent plan of kpm_moments on h chose (host output *form):
  * 0 the fused step (stencil, CSR or padded ELL), 1 the TMA-fed padded-ELL
  * step, 2 the dense product on the FP64 pipe, 3 the dense product on the
- * tensor cores.  KPM_ENOTREADY before the first kpm_moments call. */
+ * tensor cores, 4 the TMA-fed stencil step.  KPM_ENOTREADY before the first
+ * kpm_moments call. */
 kpm_status kpm_testing_last_step_form(kpm_handle h, int* form);
 
 #ifdef __cplusplus

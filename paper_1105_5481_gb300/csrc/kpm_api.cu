@@ -240,6 +240,8 @@ StepArgs base_args(const kpm_handle_s* h, int slot, int Rp, int G) {
 
 cudaError_t launch_step(bool stencil, bool fp32, bool cplx, StepMode mode, const StepArgs& a,
                         const LaunchCfg& cfg, cudaStream_t st) {
+  if (fp32 && stencil && mode == MODE_STEP && a.tma_stages > 0)
+    return launch_stencil_tma_f32(cplx, a, cfg, st);
   return fp32 ? launch_step_f32(stencil, cplx, mode, a, cfg, st)
               : launch_step_f64(stencil, cplx, mode, a, cfg, st);
 }
@@ -274,6 +276,23 @@ cudaError_t launch_op(const kpm_handle_s* h, bool fp32, StepMode mode, const Ste
 #endif
 #ifndef ELL_TMA_MINB
 #define ELL_TMA_MINB 2
+#endif
+// Default of the TMA-fed stencil step (FP32 vector blocks of at least
+// STENCIL_TMA_MIN_MB megabytes; 0 stages: the plain stencil step).  Off by
+// default: on the 3D L = 64 spin lattice it measured 77.8 us per step (2
+// stages x 2 passes, 2 CTAs per SM) against 75.9 us for the plain step, and
+// slower in every other shape tried.
+#ifndef STENCIL_TMA_STAGES
+#define STENCIL_TMA_STAGES 0
+#endif
+#ifndef STENCIL_TMA_PASSES
+#define STENCIL_TMA_PASSES 2
+#endif
+#ifndef STENCIL_TMA_MINB
+#define STENCIL_TMA_MINB 2
+#endif
+#ifndef STENCIL_TMA_MIN_MB
+#define STENCIL_TMA_MIN_MB 16
 #endif
 
 void plan_grid(const kpm_handle_s* h, bool fp32, StepArgs& a, int* block, int* grid) {
@@ -353,21 +372,56 @@ void plan_grid(const kpm_handle_s* h, bool fp32, StepArgs& a, int* block, int* g
       }
     }
   }
+  // the TMA-fed stencil step (kpm_step_stencil_tma.cu) for vector blocks of
+  // at least MB megabytes: stages, passes per tile, CTAs per SM and MB from
+  // KPM_STENCIL_TMA="stages,passes,ctas[,MB]" ("0", the default, keeps the
+  // plain step)
+  int S = STENCIL_TMA_STAGES, P = STENCIL_TMA_PASSES, B = STENCIL_TMA_MINB;
+  int min_mb = STENCIL_TMA_MIN_MB;
+  if (const char* env = getenv("KPM_STENCIL_TMA")) {
+    int s_ = 0, p_ = P, b_ = B, m_ = min_mb;
+    if (sscanf(env, "%d,%d,%d,%d", &s_, &p_, &b_, &m_) >= 1) {
+      S = s_;
+      P = p_;
+      B = b_;
+      min_mb = std::max(0, m_);
+    }
+  }
+  const size_t block_bytes = (size_t)h->n * a.G * (fp32 ? 32 : 16);
+  if (h->stencil && fp32 && blk == BLOCK && block_bytes >= ((size_t)min_mb << 20) &&
+      stencil_tma_supported(a, fp32)) {
+    if (S > 0 && P > 0) {
+      a.tma_stages = S;
+      a.tma_passes = P;
+      a.tma_minb = B;
+      a.tma_stall = g_test_stall.load();
+      const int occ_t = std::max(0, std::min(occ_stencil_tma_f32(h->cplx, a), 8));
+      const int64_t rows = (int64_t)(BLOCK / a.G) * P;
+      const int64_t tiles = (h->n + rows - 1) / rows;
+      if (occ_t > 0) {
+        *grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->num_sms * occ_t, tiles));
+      } else {
+        a.tma_stages = a.tma_passes = a.tma_minb = 0;
+      }
+    }
+  }
 }
 
 kpm_status ensure_scaled(kpm_handle_s* h, int slot, bool fp32) {
   const size_t s = fp32 ? 4 : 8;
   const size_t c = h->cplx ? 2 : 1;
   if (h->stencil) {
+    // + 16 bytes: the TMA-fed stencil step copies the last tile's hoppings and
+    // on-site terms in whole 16-byte units
     if (h->has_hop && !h->d_hs[slot]) {
       char* p = nullptr;
-      kpm_status st = dalloc(&p, (size_t)h->n * h->geom.dims * c * s);
+      kpm_status st = dalloc(&p, (size_t)h->n * h->geom.dims * c * s + 16);
       if (st != KPM_OK) return st;
       h->d_hs[slot] = p;
     }
     if (h->has_onsite && !h->d_ds[slot]) {
       char* p = nullptr;
-      kpm_status st = dalloc(&p, (size_t)h->n * s);
+      kpm_status st = dalloc(&p, (size_t)h->n * s + 16);
       if (st != KPM_OK) return st;
       h->d_ds[slot] = p;
     }
@@ -564,7 +618,7 @@ kpm_status kpm_testing_last_step_form(kpm_handle h, int* form) {
   const auto& w = h->work;
   if (w.M == 0) return fail(KPM_ENOTREADY, "no kpm_moments call has planned its launches yet");
   if (h->dense) *form = w.dtc ? 3 : 2;
-  else *form = w.proto.tma_stages > 0 ? 1 : 0;
+  else *form = w.proto.tma_stages > 0 ? (h->stencil ? 4 : 1) : 0;
   return KPM_OK;
 }
 

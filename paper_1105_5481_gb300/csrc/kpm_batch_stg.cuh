@@ -48,6 +48,7 @@
 #pragma once
 
 #include "kpm_batch_res.cuh"
+#include "kpm_fastdiv.cuh"
 #include "kpm_mbar.cuh"
 
 namespace kpm {
@@ -58,25 +59,6 @@ constexpr int STG_MAX_STAGES = 16;     // per ring (the four barrier arrays fill
 #ifndef KPM_STG_MIN_BLOCKS
 #define KPM_STG_MIN_BLOCKS 2
 #endif
-
-// Division of 31-bit numerators by a fixed divisor d >= 1 with one
-// multiply-high (Granlund and Montgomery, "Division by invariant integers
-// using multiplication", 1994, Thm. 4.2): l = ceil(log2 d),
-// m = floor(2^32 (2^l - d) / d) + 1, q = (mulhi(n, m) + n) >> l.  The sum
-// stays below 2^32 for n < 2^31.
-struct FastDiv {
-  unsigned m;
-  int l;
-};
-__host__ __device__ inline FastDiv fast_div(unsigned d) {
-  int l = 0;
-  while (l < 31 && (1u << l) < d) ++l;
-  const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
-  return {(unsigned)m, l};
-}
-__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
-  return (__umulhi(n, f.m) + n) >> f.l;
-}
 
 // Global memory access of a chunk without a compiler memory barrier: the
 // loads read v_n (not written during a product), the stores write this
@@ -103,8 +85,6 @@ __device__ __forceinline__ void stg_st_global(const CH& x, typename CH::T* p) {
                  "f"(x.p[3].x), "f"(x.p[3].y));
   }
 }
-
-__host__ __device__ inline size_t stg_round(size_t x, size_t m) { return (x + m - 1) / m * m; }
 
 // Shared-memory layout: barriers, CTA reduction scratch, rank-0 partials
 // [3 slots][C][2 Rp], then the rings.  A stream stage holds T rows of

@@ -37,6 +37,12 @@ cudaError_t launch_step_f64(bool stencil, bool cplx, StepMode mode, const StepAr
 bool ell_tma_supported(const StepArgs& a, bool fp32);
 cudaError_t launch_ell_tma_f32(bool cplx, const StepArgs& a, const LaunchCfg& cfg, cudaStream_t st);
 int occ_ell_tma_f32(bool cplx, const StepArgs& a);
+// TMA-fed stencil step (FP32 vectors, 2D/3D stencils; kpm_step_stencil_tma.cu):
+// tma_stages, tma_passes, tma_minb and tma_stall of StepArgs as for the ELL form
+bool stencil_tma_supported(const StepArgs& a, bool fp32);
+cudaError_t launch_stencil_tma_f32(bool cplx, const StepArgs& a, const LaunchCfg& cfg,
+                                   cudaStream_t st);
+int occ_stencil_tma_f32(bool cplx, const StepArgs& a);
 // occupancy-derived CTAs per SM of the step variant selected by `a`
 int occ_step_f32(bool stencil, bool cplx, const StepArgs& a, int block);
 int occ_step_f64(bool stencil, bool cplx, const StepArgs& a, int block);

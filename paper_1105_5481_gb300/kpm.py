@@ -682,12 +682,13 @@ def kpm_testing_fail_allocations(after: int):
 
 
 def kpm_testing_stall_step_pipeline(on: bool):
-    """Testing aid: plans made while set give the TMA-fed ELL step a producer that
-    issues nothing, so its bounded waits run out (KPM_ETIMEOUT)."""
+    """Testing aid: plans made while set give the TMA-fed ELL and stencil steps a
+    producer that issues nothing, so their bounded waits run out (KPM_ETIMEOUT)."""
     _check(lib().kpm_testing_stall_step_pipeline(int(bool(on))))
 
 
-STEP_FORMS = {0: "fused step", 1: "TMA-fed ELL step", 2: "dense FP64 pipe", 3: "dense tensor cores"}
+STEP_FORMS = {0: "fused step", 1: "TMA-fed ELL step", 2: "dense FP64 pipe", 3: "dense tensor cores",
+              4: "TMA-fed stencil step"}
 
 
 def kpm_testing_last_step_form(h: Handle) -> str:
