@@ -66,15 +66,21 @@ BATCH_SOURCES = STEP_SOURCES + ["paper_1105_5481_gb300/csrc/kpm_batch.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_batch_res.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_chunk16.cuh",
                                 "paper_1105_5481_gb300/csrc/kpm_batch_dispatch.cuh",
-                                "paper_1105_5481_gb300/csrc/kpm_batch_f32.cu"]
+                                "paper_1105_5481_gb300/csrc/kpm_batch_f32.cu",
+                                "paper_1105_5481_gb300/csrc/kpm_batch_stg.cuh",
+                                "paper_1105_5481_gb300/csrc/kpm_batch_stg_f32.cu",
+                                "paper_1105_5481_gb300/csrc/kpm_mbar.cuh",
+                                "paper_1105_5481_gb300/csrc/kpm_fastdiv.cuh"]
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture (steady state of consecutive launches, caches not flushed between
 # them), keyed by workload and launch configuration, with the hash of the
 # kernel sources it was taken on; reported only while the hash matches.
 MEASURED_TRAFFIC = {"cubic_spin_L64": (347.93e6, "step", "9d89b353287cea2a"),
                     "csr_spin_dilute_L160": (3394.59e6, "tma", "2ff2a33ede954230"),
-                    "batch_2d_256/C4/chunk4/clusters74/rt1/top0": (67.06e9, "batch", "3fcfd542a426a35a"),
-                    "batch_2d_256/C4/chunk2/clusters74/rt2/top8": (59.48e9, "batch", "3fcfd542a426a35a")}
+                    "batch_2d_256/C4/chunk2/clusters74/rt1/top0": (69.20e9, "batch", "f1a1fabd8beeef38"),
+                    "batch_2d_256/C4/chunk4/clusters74/rt1/top0": (68.25e9, "batch", "f1a1fabd8beeef38"),
+                    "batch_2d_256/C4/chunk2/clusters74/rt2/top8": (61.17e9, "batch", "f1a1fabd8beeef38"),
+                    "batch_2d_256/C4/chunk4/clusters74/rt1/top0/staged": (71.20e9, "batch", "f1a1fabd8beeef38")}
 
 # FP64 FMA issue rate of GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flop at the
 # sustained clock.  A dependent-chain probe measured 1.20 TFLOP/s (1.97 GHz).
@@ -308,7 +314,7 @@ def reference_arm(args):
 
 # ================================================================ ncu helper
 def profile_run(prec, workload, batch_chunk=2, batch_cluster=4, batch_chunk_bytes=32,
-                batch_rtiles=1, batch_top=0):
+                batch_rtiles=1, batch_top=0, batch_staged=False):
     """Two solves of the workload with Gershgorin bounds (no Lanczos products, so
     the only fused-step launches are those of the two solves); prec "bounds":
     three spectral-bound estimates of the 3D L=64 lattice (Gershgorin and the
@@ -338,6 +344,8 @@ def profile_run(prec, workload, batch_chunk=2, batch_cluster=4, batch_chunk_byte
             K.kpm_batch_set_chunk_bytes(bt, batch_chunk_bytes)
             K.kpm_batch_set_config(bt, batch_cluster, batch_chunk, 100)
             K.kpm_batch_set_rtiles(bt, batch_rtiles, batch_top)
+            if batch_staged:
+                K.kpm_batch_set_staged(bt, True)
             for _ in range(2):
                 mu = K.kpm_batch_run(bt)
         print(json.dumps({"profile": prec, "workload": workload, "mu0": float(mu[0])}))
@@ -719,6 +727,7 @@ def batch_result(args, K):
     info = K.kpm_batch_tune(bt, reps=1)
     info["rtiles"], info["tiled_instances"], _ = K.kpm_batch_get_rtiles(bt)
     info["resident"] = K.kpm_batch_get_resident(bt)[0]
+    info["staged"] = K.kpm_batch_get_staged(bt)[0]
     info["chunk_bytes"], info["threads_per_row"] = K.kpm_batch_get_chunk_bytes(bt)
     tune_s = time.perf_counter() - t0
     mu_host = K.kpm_batch_run(bt)  # host output: divergence check
@@ -779,6 +788,7 @@ def batch_result(args, K):
                      "traffic": measured_traffic("batch_2d_256/C%d/chunk%d/clusters%d/rt%d/top%d%s" % (
                          info["cluster"], info["chunk"], info["clusters"], info["rtiles"],
                          info["tiled_instances"], ("/resident" if info["resident"] else "") +
+                         ("/staged" if info["staged"] else "") +
                          ("/chunk16B" if info["chunk_bytes"] == 16 else ""))),
                      "bytes_per_launch": byts, "peak_kind": peak_kind,
                      "note": "algorithmic bytes of all instances per batch launch; the working "
@@ -1071,6 +1081,9 @@ def main():
                     help="--profile with the batch workload: column tiles of the largest instances")
     ap.add_argument("--batch-top", type=int, default=0,
                     help="--profile with the batch workload: instances tiled (0: all)")
+    ap.add_argument("--batch-staged", action="store_true",
+                    help="--profile with the batch workload: the staged form (tiles copied "
+                         "into shared-memory rings; --batch-chunk sets the tile size)")
     ap.add_argument("--workload", default=HEADLINE,
                     choices=[HEADLINE, "cubic_spin_L64", "batch_2d_256", "serve_poisson",
                              "square_L32_fp64", "dense_wigner_D4096", "csr_spin_dilute_L100"],
@@ -1084,7 +1097,8 @@ def main():
         return reference_arm(args)
     if args.profile:
         return profile_run(args.profile, args.workload, args.batch_chunk, args.batch_cluster,
-                           args.batch_chunk_bytes, args.batch_rtiles, args.batch_top)
+                           args.batch_chunk_bytes, args.batch_rtiles, args.batch_top,
+                           args.batch_staged)
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         return relaunch_distributed(args)
     if args.workload == "csr_spin_dilute_L100":
