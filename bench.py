@@ -542,7 +542,7 @@ def headline_leg(args):
                     "h2d_bytes_per_step": int(rp.nbytes + col.nbytes + val.nbytes),
                     "d2h_bytes_per_step": int(8 * (M + 2 * Kn)),
                     "includes": "create from pinned host CSR arrays (padded-ELL copy built on the "
-                                "host), bounds, moments, DOS, destroy"},
+                                "device), bounds, moments, DOS, destroy"},
             "replicas_combined": combined,
             "gpu_launches": launches,
             "clocks": clk,

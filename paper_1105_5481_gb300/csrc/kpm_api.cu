@@ -749,26 +749,18 @@ kpm_status kpm_create_csr(int64_t n, const int64_t* rowptr, const int32_t* col, 
   for (int64_t i = 0; i < n; ++i) wmax = std::max(wmax, rowptr[i + 1] - rowptr[i]);
   const int64_t W = std::max<int64_t>(2, (wmax + 1) / 2 * 2);
   if (wmax <= 8 && n * W <= 2 * std::max<int64_t>(nnz, 1)) {
-    std::vector<int32_t> ec((size_t)n * W);
-    std::vector<double> ev((size_t)n * W * c, 0.0);
-    for (int64_t i = 0; i < n; ++i) {
-      int64_t k = 0;
-      for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q, ++k) {
-        ec[(size_t)i * W + k] = col[q];
-        for (int z = 0; z < c; ++z) ev[((size_t)i * W + k) * c + z] = val[q * c + z];
-      }
-      for (; k < W; ++k) ec[(size_t)i * W + k] = (int32_t)i;  // value stays 0
-    }
-    // + 4 entries: the TMA-fed ELL step copies the last tile in whole 16-byte units
-    if ((st = dalloc(&h->d_ell_col, ec.size() + 4)) != KPM_OK ||
-        (st = dalloc(&h->d_ell_val, ev.size())) != KPM_OK) {
+    // built on the device from the CSR arrays just copied (padding slots point
+    // at the row itself with value 0); + 4 entries: the TMA-fed ELL step copies
+    // the last tile in whole 16-byte units
+    if ((st = dalloc(&h->d_ell_col, (size_t)n * W + 4)) != KPM_OK ||
+        (st = dalloc(&h->d_ell_val, (size_t)n * W * c)) != KPM_OK) {
       destroy_handle(h);
       return st;
     }
-    e = cudaMemcpy(h->d_ell_col, ec.data(), ec.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(h->d_ell_val, ev.data(), ev.size() * sizeof(double), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { destroy_handle(h); return cuda_fail(e, "copy ELL"); }
+    e = launch_ell_build(n, (int)W, h->cplx, h->d_rowptr, h->d_col, h->d_val, h->d_ell_col,
+                         h->d_ell_val, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { destroy_handle(h); return cuda_fail(e, "padded-ELL build"); }
     h->ell_w = (int)W;
   }
   *out = h;

@@ -956,6 +956,32 @@ cudaError_t launch_prescale_stencil(bool fp32, bool cplx, int64_t n, int dims, c
   return counted(cudaGetLastError());
 }
 
+// Padded-ELL copy of a CSR matrix already on the device: row i's entries in
+// its W slots in CSR order, the remaining slots pointing at row i with value 0.
+__global__ void ell_build_kernel(int64_t n, int W, int c, const int64_t* __restrict__ rowptr,
+                                 const int32_t* __restrict__ col, const double* __restrict__ val,
+                                 int32_t* __restrict__ ecol, double* __restrict__ eval) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q0 = rowptr[i], q1 = rowptr[i + 1];
+    for (int k = 0; k < W; ++k) {
+      const int64_t q = q0 + k;
+      const size_t o = (size_t)i * W + k;
+      const bool in = q < q1;
+      ecol[o] = in ? col[q] : (int32_t)i;
+      for (int z = 0; z < c; ++z) eval[o * c + z] = in ? val[q * c + z] : 0.0;
+    }
+  }
+}
+
+cudaError_t launch_ell_build(int64_t n, int W, bool cplx, const int64_t* rowptr, const int32_t* col,
+                             const double* val, int32_t* ecol, double* eval, cudaStream_t st) {
+  const unsigned g = blocks_for(n, 256);
+  ell_build_kernel<<<g, 256, 0, st>>>(n, W, cplx ? 2 : 1, rowptr, col, val, ecol, eval);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prescale_csr(bool fp32, bool cplx, int64_t nnz, const double* val,
                                 const RunParams* prm, bool lanczos, void* vals, ScalarBlock* sc,
                                 cudaStream_t st) {

@@ -83,6 +83,9 @@ cudaError_t launch_prescale_stencil(bool fp32, bool cplx, int64_t n, int dims, c
                                     const double* hop, double t_re, double t_im,
                                     const RunParams* prm, bool lanczos, void* hs, void* ds,
                                     ScalarBlock* sc, cudaStream_t st);
+// Padded-ELL copy (width W) of a device CSR matrix (kpm_aux.cu).
+cudaError_t launch_ell_build(int64_t n, int W, bool cplx, const int64_t* rowptr, const int32_t* col,
+                             const double* val, int32_t* ecol, double* eval, cudaStream_t st);
 cudaError_t launch_prescale_csr(bool fp32, bool cplx, int64_t nnz, const double* val,
                                 const RunParams* prm, bool lanczos, void* vals, ScalarBlock* sc,
                                 cudaStream_t st);
