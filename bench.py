@@ -666,6 +666,26 @@ def square_result(args, K):
     steps = max(args.steps, 1) * 20  # one solve is well under a millisecond
     ms, launches, clk = timed_solves(K, stream, solve, steps, max(args.warmup, 3))
     chain_ms, nsteps = K.kpm_step_timing(h)
+    form = K.kpm_testing_last_step_form(h)
+    # the same solve as a chain of dependent step launches (the form the
+    # column-resident solve replaces), on a handle planned with it turned off
+    old = os.environ.get("KPM_COLRES")
+    os.environ["KPM_COLRES"] = "0"
+    try:
+        hc = K.kpm_create_stencil(2, w["L"], onsite=w["onsite"])
+
+        def solve_chain(i):
+            K.kpm_moments(hc, M, R, a, b, seed=100 + i, precision="fp64", out=mu_d, stream=stream)
+            K.kpm_dos(mu_d, a, b, Kn, "jackson", E=E_d, rho=rho_d, stream=stream)
+
+        chain_solve_ms, _, _ = timed_solves(K, stream, solve_chain, steps, max(args.warmup, 3))
+        chain_steps_ms, _ = K.kpm_step_timing(hc)
+        hc.close()
+    finally:
+        if old is None:
+            os.environ.pop("KPM_COLRES", None)
+        else:
+            os.environ["KPM_COLRES"] = old
     batch_of_one = {}
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -701,8 +721,18 @@ def square_result(args, K):
         "roofline": {"bound": "latency", "achieved": rate, "peak": hbm, "unit": "GB/s",
                      "frac": rate / hbm, "traffic": None, "bytes_per_launch": bytes_step,
                      "launch_ms": chain_ms / nsteps, "peak_kind": peak_kind,
-                     "note": "127 dependent steps on 128 KB of vectors: each step is one "
-                             "launch's latency; achieved = the L2-resident rate"},
+                     "note": ("128 dependent products on 128 KB of vectors, all in one launch "
+                              "of 8 independent clusters (one per vector column, both vector "
+                              "blocks in shared memory): launch_ms is the average product "
+                              "inside it; achieved = the vector bytes of a product over that time"
+                              if form == "column-resident solve" else
+                              "127 dependent steps on 128 KB of vectors: each step is one "
+                              "launch's latency; achieved = the L2-resident rate")},
+        "form": form,
+        "step_chain": {"us_per_solve": chain_solve_ms * 1e3,
+                       "us_per_step": chain_steps_ms / nsteps * 1e3,
+                       "note": "the same solves as a chain of dependent fused-step launches "
+                               "(KPM_COLRES=0)"},
         "batch_of_one_moments": batch_of_one,
         "gpu_launches": launches, "clocks": clk}
 

@@ -175,7 +175,12 @@ typedef struct {
  * the S*R vectors, and optionally the per-vector moments
  * mu_per_vec[(s*R + r)*M + n] (NULL to skip).  One fused CUDA kernel per
  * matrix product (v_{n+1} = 2 H~ v_n - v_{n-1} plus the two moment dots),
- * replayed from a captured CUDA graph.  Returns KPM_EDIVERGE (after writing
+ * replayed from a captured CUDA graph.  A stencil operator small enough that
+ * one cluster of at most 16 CTAs holds one column's two vectors in shared
+ * memory with one element per thread (and every column group fits the GPU at
+ * once) instead runs all M/2 products of a realisation in one launch of
+ * independent clusters, one per group of columns (the column-resident solve;
+ * KPM_COLRES=0 in the environment keeps the chain).  Returns KPM_EDIVERGE (after writing
  * the outputs) when host outputs show |mu_n^r| > 1 + 1e-6 or a non-finite
  * value, and KPM_EINVAL when R exceeds one block of vectors (more than 1024
  * chunks of 16 bytes (FP64) or 32 bytes (FP32) per row, after rounding the
@@ -313,7 +318,9 @@ kpm_status kpm_moments_adaptive(kpm_handle h, const kpm_params* p, int K, int ke
  * moment reduction of its last realisation, measured with two CUDA events
  * recorded inside the replayed graph on the call's stream.  *step_launches
  * receives the number of fused-step kernels in that chain (M/2), so ms /
- * step_launches is the average duration of one fused step launch.  Call after
+ * step_launches is the average duration of one fused step launch (for the
+ * column-resident solve: the one launch that runs all M/2 products, and ms /
+ * step_launches the average product inside it).  Call after
  * the kpm_moments stream has completed; KPM_ENOTREADY if no call was made. */
 kpm_status kpm_step_timing(kpm_handle h, double* ms, int* step_launches);
 
@@ -590,8 +597,9 @@ kpm_status kpm_testing_stall_step_pipeline(int on);
  * the most recent plan of kpm_moments on h chose (host output *form):
  * 0 the fused step (stencil, CSR or padded ELL), 1 the TMA-fed padded-ELL
  * step, 2 the dense product on the FP64 pipe, 3 the dense product on the
- * tensor cores, 4 the TMA-fed stencil step.  KPM_ENOTREADY before the first
- * kpm_moments call. */
+ * tensor cores, 4 the TMA-fed stencil step, 5 the column-resident solve
+ * (all products of a realisation of a small stencil operator in one cluster
+ * launch).  KPM_ENOTREADY before the first kpm_moments call. */
 kpm_status kpm_testing_last_step_form(kpm_handle h, int* form);
 
 #ifdef __cplusplus

@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 
+#include "kpm_colres.h"
 #include "kpm_internal.h"
 
 namespace kpm {
@@ -207,6 +208,7 @@ void free_work(kpm_handle_s* h) {
   dfree(w.per_vec);  // w.mu points into per_vec
   dfree(w.v0stage);
   dfree(w.sb_dev);
+  dfree(w.cr_gp);
   if (w.ev[0]) cudaEventDestroy(w.ev[0]);
   if (w.ev[1]) cudaEventDestroy(w.ev[1]);
   w = kpm_handle_s::Work{};
@@ -618,6 +620,7 @@ kpm_status kpm_testing_last_step_form(kpm_handle h, int* form) {
   const auto& w = h->work;
   if (w.M == 0) return fail(KPM_ENOTREADY, "no kpm_moments call has planned its launches yet");
   if (h->dense) *form = w.dtc ? 3 : 2;
+  else if (w.cr.C > 0) *form = 5;
   else *form = w.proto.tma_stages > 0 ? (h->stencil ? 4 : 1) : 0;
   return KPM_OK;
 }
@@ -954,6 +957,48 @@ namespace kpm {
 // kpm_spectral_moments.  sb.kind != START_RANDOM replaces the random block by
 // a start block built on the device (see StartBlock); with internal = true
 // both outputs may be NULL (the caller reads w.per_vec itself).
+// Arguments of a column-resident launch over products [n0, n1) of a
+// realisation of `steps` products (vector blocks and operator of the plan).
+ColresArgs colres_args(const kpm_handle_s* h, int R, int n0, int n1, int steps, bool gen) {
+  const auto& w = h->work;
+  ColresArgs c{};
+  c.vg[0] = w.v[0];
+  c.vg[1] = w.v[1];
+  c.sc = w.proto.sc;
+  c.hs = w.proto.hs;
+  c.ds = w.proto.ds;
+  c.geom = w.proto.geom;
+  c.prm = h->d_prm;
+  c.sums = w.sums;
+  c.gp = w.cr_gp;
+  c.n = h->n;
+  c.Rp = w.Rp;
+  c.R = R;
+  c.P = w.cr.P;
+  c.cpc = w.cr.cpc;
+  c.n0 = n0;
+  c.n1 = n1;
+  c.steps = steps;
+  c.gen = gen ? 1 : 0;
+  return c;
+}
+
+// Partial scratch of the column-resident form for launches of up to nprod products.
+kpm_status colres_scratch(kpm_handle_s* h, int nprod) {
+  auto& w = h->work;
+  const size_t need = colres_partial_doubles(w.cr, nprod);
+  if (w.cr_gp_doubles >= need) return KPM_OK;
+  // a launch of an earlier call may still be using the old scratch
+  KPM_CUDA(cudaDeviceSynchronize());
+  dfree(w.cr_gp);
+  w.cr_gp = nullptr;
+  w.cr_gp_doubles = 0;
+  kpm_status sa = dalloc(&w.cr_gp, need);
+  if (sa != KPM_OK) return sa;
+  w.cr_gp_doubles = need;
+  return KPM_OK;
+}
+
 kpm_status moments_impl(kpm_handle h, const kpm_params* p, double* mu, double* mu_per_vec,
                         void* stream, const StartBlock& sb, bool internal) {
   if (!h) return fail(KPM_EINVAL, "handle is NULL");
@@ -1000,7 +1045,8 @@ kpm_status moments_impl(kpm_handle h, const kpm_params* p, double* mu, double* m
   const size_t sums_bytes = (size_t)S * steps * 2 * Rp * sizeof(double);
   const size_t out_bytes = ((size_t)S * R * M + M) * sizeof(double);
   const bool rebuild = w.Rp != Rp || w.prec != p->precision || w.M != M ||
-                       w.user_v0 != user_v0 || !w.ready || w.sums_bytes < sums_bytes;
+                       w.user_v0 != user_v0 || !w.ready || w.sums_bytes < sums_bytes ||
+                       (w.cr.C > 0 && w.cr_R != R);
   // The kernel sequence of one realisation.  The first call of a shape
   // launches it directly on the caller's stream (the solve is GPU-bound, so
   // the launches hide behind it); a second call of the same shape captures it
@@ -1015,6 +1061,16 @@ kpm_status moments_impl(kpm_handle h, const kpm_params* p, double* mu, double* m
                      : cudaEventRecord(ev, cs);
     };
     cudaError_t e = cudaSuccess;
+    if (w.cr.C > 0) {
+      // the whole realisation in one cluster launch (it draws v_0 itself)
+      e = rec(w.ev[0]);
+      if (e == cudaSuccess)
+        e = launch_colres(fp32, h->cplx, h->geom.dims, w.cr,
+                          colres_args(h, R, 0, steps, steps, !user_v0), cs);
+      if (e == cudaSuccess) e = rec(w.ev[1]);
+      if (e == cudaSuccess) e = launch_advance_realisation(h->d_prm, cs);
+      return e;
+    }
     if (!user_v0) e = launch_rng_init(fp32, h->cplx, h->n, Rp, h->d_prm, w.v[0], cs);
     StepArgs a = w.proto;
     if (e == cudaSuccess) e = rec(w.ev[0]);
@@ -1086,6 +1142,18 @@ kpm_status moments_impl(kpm_handle h, const kpm_params* p, double* mu, double* m
     int block, grid;
     plan_grid(h, fp32, proto, &block, &grid);
     w.proto = proto;
+    // small stencil operators: the column-resident solve replaces the chain
+    // of step launches (unless the TMA-fed stencil step was asked for)
+    w.cr = ColresPlan{};
+    w.cr_R = R;
+    if (h->stencil && !h->dense && proto.tma_stages == 0 &&
+        colres_plan(h->n, h->geom.dims, h->cplx, fp32, R, &w.cr)) {
+      kpm_status sa = colres_scratch(h, steps);
+      if (sa != KPM_OK) {
+        w.cr = ColresPlan{};
+        return sa;
+      }
+    }
     if (dense_tc_wanted(h, fp32)) setup_dense_tc(h, Rp);
     else free_dense_tc(w);
     dfree(w.ring);
@@ -1392,9 +1460,17 @@ kpm_status kpm_moments_extend(kpm_handle h, int M, double* mu, double* mu_per_ve
   // the same step launches as the uninterrupted chain: product n reads v_n
   // from v[n & 1] and writes v_{n+1} over v_{n-1}; the ring is reduced at the
   // same step boundaries, so the sums equal those of a single call with this M
+  if (w.cr.C > 0) {
+    // the column-resident form continues from v_{n-1}, v_n in v[] with the
+    // same per-product arithmetic and sum order
+    kpm_status sa = colres_scratch(h, steps - old_steps);
+    if (sa != KPM_OK) return sa;
+    KPM_CUDA(launch_colres(fp32, h->cplx, h->geom.dims, w.cr,
+                           colres_args(h, R, old_steps, steps, steps, false), st));
+  }
   StepArgs a = w.proto;
   const LaunchCfg cfg{w.block, grid};
-  for (int n = old_steps; n < steps; ++n) {
+  for (int n = w.cr.C > 0 ? steps : old_steps; n < steps; ++n) {
     a.x = w.v[n & 1];
     a.y = w.v[(n + 1) & 1];
     a.w = w.v[(n + 1) & 1];

@@ -47,6 +47,17 @@ int occ_stencil_tma_f32(bool cplx, const StepArgs& a);
 int occ_step_f32(bool stencil, bool cplx, const StepArgs& a, int block);
 int occ_step_f64(bool stencil, bool cplx, const StepArgs& a, int block);
 
+// Launch shape of the column-resident solve (kpm_colres.h): C = 0 when the
+// form does not apply.
+struct ColresPlan {
+  int C = 0;        // CTAs per cluster
+  int cpc = 0;      // vector columns per cluster (a power of two <= 32)
+  int groups = 0;   // clusters: ceil(R / cpc)
+  int block = 0;    // threads per CTA
+  int64_t P = 0;    // rows per CTA: ceil(N / C)
+  size_t smem = 0;  // dynamic shared memory per CTA
+};
+
 // Dense products on the bf16 tensor cores by the Ozaki splitting scheme
 // (kpm_dense_tc.cu), real FP64 dense handles: slices of S (per call) and of
 // the current vector block (per step), the exact slice products, exponents.
@@ -266,6 +277,13 @@ struct kpm_handle_s {
     int res_steps = 0, res_R = 0, res_s0 = 0;
     double res_a = 0.0, res_b = 0.0;
     unsigned long long res_seed = 0;
+    // column-resident solve (kpm_colres.cu) in place of the step chain when
+    // cr.C > 0: its plan, the column count it was made for, and the scratch
+    // of its CTA partials
+    kpm::ColresPlan cr{};
+    int cr_R = 0;
+    double* cr_gp = nullptr;
+    size_t cr_gp_doubles = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};  // recorded around the step chain in the graph
     bool timed = false;
   } work;

@@ -37,6 +37,34 @@ __device__ __forceinline__ void cplx_offsets(int64_t i, int r, int Rp, int64_t& 
   }
 }
 
+// Entry (i, r) of realisation s of the start block, r < R: Rademacher +-1
+// (real field) or a unit phase (complex field; im is left untouched for the
+// real field).
+template <typename T, bool CPLX>
+__device__ __forceinline__ void random_value(int64_t n, int R, unsigned long long seed,
+                                             unsigned long long s, int64_t i, int r, T& re,
+                                             T& im) {
+  const unsigned long long ctr = (s * (unsigned long long)R + (unsigned long long)r) *
+                                     (unsigned long long)n + (unsigned long long)i;
+  const unsigned long long z = draw(seed, 0, ctr);
+  if (CPLX) {
+    const double u = (double)(z >> 11) * 0x1.0p-53;
+    if (sizeof(T) == 8) {
+      double sv, cv;
+      sincospi(2.0 * u, &sv, &cv);
+      re = (T)cv;
+      im = (T)sv;
+    } else {
+      float sv, cv;
+      sincospif(2.0f * (float)u, &sv, &cv);
+      re = (T)cv;
+      im = (T)sv;
+    }
+  } else {
+    re = (z >> 63) ? T(-1) : T(1);
+  }
+}
+
 // Writes element e = i * Rp + r of the start block (zero for padded columns r >= R).
 template <typename T, bool CPLX>
 __device__ __forceinline__ void random_entry(T* v0, int64_t n, int Rp, int R,
@@ -51,25 +79,10 @@ __device__ __forceinline__ void random_entry(T* v0, int64_t n, int Rp, int R,
     else v0[e] = T(0);
     return;
   }
-  const unsigned long long ctr = (s * (unsigned long long)R + (unsigned long long)r) *
-                                     (unsigned long long)n + (unsigned long long)i;
-  const unsigned long long z = draw(seed, 0, ctr);
-  if (CPLX) {
-    const double u = (double)(z >> 11) * 0x1.0p-53;
-    if (sizeof(T) == 8) {
-      double sv, cv;
-      sincospi(2.0 * u, &sv, &cv);
-      v0[ore] = (T)cv;
-      v0[oim] = (T)sv;
-    } else {
-      float sv, cv;
-      sincospif(2.0f * (float)u, &sv, &cv);
-      v0[ore] = (T)cv;
-      v0[oim] = (T)sv;
-    }
-  } else {
-    v0[e] = (z >> 63) ? T(-1) : T(1);
-  }
+  T re, im = T(0);
+  random_value<T, CPLX>(n, R, seed, s, i, r, re, im);
+  v0[ore] = re;
+  if (CPLX) v0[oim] = im;
 }
 
 }  // namespace kpm

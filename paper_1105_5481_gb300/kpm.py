@@ -688,7 +688,7 @@ def kpm_testing_stall_step_pipeline(on: bool):
 
 
 STEP_FORMS = {0: "fused step", 1: "TMA-fed ELL step", 2: "dense FP64 pipe", 3: "dense tensor cores",
-              4: "TMA-fed stencil step"}
+              4: "TMA-fed stencil step", 5: "column-resident solve"}
 
 
 def kpm_testing_last_step_form(h: Handle) -> str:
