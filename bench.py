@@ -355,6 +355,9 @@ def profile_run(prec, workload, batch_chunk=2, batch_cluster=4, batch_chunk_byte
         rp, col, val = csr_inputs(K, w)
         h = K.kpm_create_csr(rp.size - 1, rp, col, val, complex_=True)
         M, R = 64, w["R"]   # a short solve: the fused steps are identical at any M
+    elif workload == "square_L32_fp64":
+        h = K.kpm_create_stencil(2, w["L"], onsite=w["onsite"])
+        M, R = w["M"], w["R"]
     else:
         h = K.kpm_create_stencil(3, w["L"], hop=w["hop"], complex_=True)
         M, R = w["M"], w["R"]

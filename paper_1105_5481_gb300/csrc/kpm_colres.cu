@@ -17,9 +17,11 @@
 // synchronisation, and the clusters never wait on one another.
 //
 // Moments: every thread adds |x|^2 and Re(conj(y) x) of its element in FP64,
-// lanes of one column are combined by an XOR butterfly, the warp results of a
-// product are summed in warp order after the product's barrier and stored as
-// the CTA's partial in global scratch; after the last product the partials
+// lanes of one column are combined by an XOR butterfly between the two halves
+// of the product's cluster barrier (arrive after v_{n+1} is written, wait
+// after the butterfly), the warp results go to one of three shared-memory
+// slots and are summed in warp order one product later, as the CTA's partial
+// in global scratch; after the last product the partials
 // are summed in rank order into the per-step sums that the finalisation
 // kernels read.  The order of every sum is fixed by (C, cpc, block), so a
 // repeated call, a replayed graph and a continued solve give the same bits.
@@ -140,6 +142,16 @@ __device__ __forceinline__ void cmac(Cx<T>& acc, T hr, T hi, const Cx<T>& x) {
 template <typename T, bool CPLX>
 using Elem = typename std::conditional<CPLX, Cx<T>, T>::type;
 
+// The two halves of the cluster barrier: the arrive publishes this thread's
+// earlier writes to the cluster, the wait returns once every thread of the
+// cluster has arrived and makes their writes visible.
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
 }  // namespace
 
 template <typename T, bool CPLX, int DIMS>
@@ -162,7 +174,7 @@ __global__ void __launch_bounds__(1024, 1) colres_kernel(const ColresArgs p) {
   E* buf0 = reinterpret_cast<E*>(sm);
   E* buf1 = buf0 + (size_t)p.P * cpc;
   const uint32_t buf_bytes = (uint32_t)((size_t)p.P * cpc * sizeof(E));
-  double* wp = reinterpret_cast<double*>(sm + colres_head_bytes(2 * (size_t)buf_bytes));  // [2][nw][2][cpc]
+  double* wp = reinterpret_cast<double*>(sm + colres_head_bytes(2 * (size_t)buf_bytes));  // [3][nw][2][cpc]
   const int nprod = p.n1 - p.n0;
 
   // the thread's operator row: neighbour addresses, bond coefficients, diagonal
@@ -210,6 +222,51 @@ __global__ void __launch_bounds__(1024, 1) colres_kernel(const ColresArgs p) {
       ab[d] = cluster_addr(buf0 + ((jb - (int64_t)qb * p.P) * cpc + c), (uint32_t)qb);
     }
   }
+
+  // CTA partial of product k (k = n - n0) by thread t < 2 cpc: the warp sums
+  // in warp order, kept in a shared-memory ring of `kr` products that goes to
+  // the global scratch only when it is full and after the last product (a
+  // global store inside the product loop would make the release half of the
+  // next cluster barrier wait for its round trip to L2)
+  double* ring = wp + (size_t)3 * nw * 2 * cpc;  // [kr][2 cpc]
+  const int kr = p.kr;
+  auto cta_partial = [&](int k) {
+    const int ps = k % 3;
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += wp[(size_t)(ps * nw + w) * 2 * cpc + t];
+    ring[(size_t)(k % kr) * 2 * cpc + t] = s;
+    if (k % kr == kr - 1 || k == nprod - 1) {
+      const int k0 = k - k % kr;
+      double* dst = p.gp + (((size_t)g * C + q) * nprod) * 2 * cpc + t;
+      for (int j = k0; j <= k; ++j) dst[(size_t)j * 2 * cpc] = ring[(size_t)(j - k0) * 2 * cpc + t];
+    }
+  };
+
+  // Bulk form of the dot sums (p.bulk_k = K > 0): every thread parks its two
+  // dot terms of each product in bb[batch & 1][k % K][t][2], no shuffle tree;
+  // once a batch of K products is complete, each (product, dot, column) sum
+  // of the batch is taken by tps adjacent lanes: lane `sub` adds the column's
+  // terms of threads u = cc + cpc (sub + tps m) in increasing u, then an XOR
+  // butterfly over the tps lanes (K = B / (2 cpc tps): the B threads cover
+  // the batch exactly).  About 2 FP64 adds per thread and product instead of
+  // the 2 log2(32 / cpc) of the per-product shuffle tree.
+  const int K = p.bulk_k, tps = p.bulk_tps;
+  double* bb = ring + (size_t)kr * 2 * cpc;  // [2][K][B][2]
+  auto bulk_reduce = [&](int b, int cnt) {
+    const int B = (int)blockDim.x;
+    const int sidx = t / tps, sub = t % tps;
+    const bool act = sidx < cnt * 2 * cpc;
+    const int pi = sidx / (2 * cpc), r = sidx % (2 * cpc);
+    double s = 0.0;
+    if (act) {
+      const int v = r / cpc, cc = r % cpc;
+      const double* base = bb + ((size_t)(b & 1) * K + pi) * B * 2;
+      for (int u = cc + cpc * sub; u < B; u += cpc * tps) s += base[2 * u + v];
+    }
+    for (int o = 1; o < tps; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (act && sub == 0)
+      p.gp[(((size_t)g * C + q) * nprod + (size_t)b * K + pi) * 2 * cpc + r] = s;
+  };
 
   // start: v_0 drawn here or loaded, or v_{n0-1} and v_{n0} of a continued solve
   if (valid) {
@@ -283,23 +340,46 @@ __global__ void __launch_bounds__(1024, 1) colres_kernel(const ColresArgs p) {
       sa = fma(xr, xr, xi * xi);
       sb = fma(yr, xr, yi * xi);
     }
+    if (K > 0) {
+      const int k = n - p.n0;
+      double* slotp = bb + ((size_t)((k / K) & 1) * K + (k % K)) * blockDim.x * 2;
+      slotp[2 * t] = sa;
+      slotp[2 * t + 1] = sb;
+      cluster_arrive_release();
+      // the previous batch (complete since the last wait; its half of bb is
+      // next written K products later, after this thread's next arrive)
+      if (k % K == 0 && k > 0) bulk_reduce(k / K - 1, K);
+      cluster_wait_acquire();
+      continue;
+    }
+    // this CTA's rows of v_{n+1} are published; the warp sums of the dots run
+    // while the slower CTAs of the cluster finish theirs
+    cluster_arrive_release();
     // lanes of one column: lane, lane ^ cpc, lane ^ 2 cpc, ...
     for (int o = cpc; o < 32; o <<= 1) {
       sa += __shfl_xor_sync(0xffffffffu, sa, o);
       sb += __shfl_xor_sync(0xffffffffu, sb, o);
     }
+    const int slot = (n - p.n0) % 3;
     if (lane < cpc) {
-      double* w = wp + ((size_t)(par * nw + warp) * 2) * cpc;
+      double* w = wp + ((size_t)(slot * nw + warp) * 2) * cpc;
       w[lane] = sa;
       w[cpc + lane] = sb;
     }
-    // v_{n+1} of every CTA and this product's warp partials are complete
-    cl.sync();
-    if (t < 2 * cpc) {
-      double s = 0.0;
-      for (int k = 0; k < nw; ++k) s += wp[(size_t)(par * nw + k) * 2 * cpc + t];
-      p.gp[(((size_t)g * C + q) * nprod + (n - p.n0)) * 2 * cpc + t] = s;
-    }
+    // v_{n+1} of every CTA is complete
+    cluster_wait_acquire();
+    // the previous product's warp sums (written before every thread's arrive
+    // of this product; their slot is next written three products later, after
+    // this thread's next arrive)
+    if (t < 2 * cpc && n > p.n0) cta_partial(n - 1 - p.n0);
+  }
+  // the last product's warp sums, or the last batch of the bulk form
+  __syncthreads();
+  if (K > 0) {
+    const int bl = (nprod - 1) / K;
+    bulk_reduce(bl, nprod - bl * K);
+  } else if (t < 2 * cpc) {
+    cta_partial(nprod - 1);
   }
 
   // v_{n1} and v_{n1-1} to the global blocks (where a continued solve reads them)
@@ -378,9 +458,62 @@ bool configure(bool fp32, bool cplx, int dims) {
 
 size_t elem_size(bool fp32, bool cplx) { return (fp32 ? 4 : 8) * (cplx ? 2 : 1); }
 
+// Products held by the shared-memory ring of CTA partials (at most 16 KB).
+int ring_products(int cpc) { return (int)(COLRES_RING_BYTES / (2 * (size_t)cpc * 8)); }
+
+// Shape of the bulk dot sums: the fewest lanes per sum (tps, a power of two
+// <= 32) whose batch of K = block / (2 cpc tps) products fits
+// COLRES_BULK_BYTES; K = 0 (the per-product shuffle tree) if none does.
+void bulk_shape(int cpc, int block, int* K, int* tps) {
+  *K = 0;
+  *tps = 1;
+  for (int l = 1; l <= 32; l *= 2) {
+    if (block % (2 * cpc * l) != 0) break;
+    const int k = block / (2 * cpc * l);
+    if ((size_t)2 * k * block * 2 * 8 <= COLRES_BULK_BYTES) {
+      *K = k;
+      *tps = l;
+      return;
+    }
+  }
+}
+
+int bulk_batch(int cpc, int block) {
+  int k, l;
+  bulk_shape(cpc, block, &k, &l);
+  return k;
+}
+
+// Estimated microseconds per product (GB300, fitted to measurements of both
+// forms on 2D/3D lattices of 512-9216 sites, R = 8-32).  Work is counted in
+// real FP64 elements per SM: the elements of a CTA times the CTAs an SM holds,
+// x3.9 for complex FP64 (four FMAs per bond; the FP64 pipe bounds it), x1.2
+// for complex FP32, x0.8 for FP32 vectors (only the dots are FP64).
+//   column-resident: 0.64 + 0.0040 w (bulk dot sums) or 0.64 + 0.0105 w
+//     (shuffle tree).  Measured: real FP64 2D L=32/48/64, R=8, bulk:
+//     0.90/1.28/1.84; tree at L=80/96: 4.93/8.32; complex FP64 3D L=8/12/16,
+//     R=16: 1.94/3.88/7.81; FP32 2D L=32/64, R=16: 0.74/1.81.
+//   step chain: 2.9 + 1.49e-5 N R (x3.9 complex FP64; FP32 vectors x0.15, x1.2
+//     more when complex), the launch
+//     latency of a dependent step plus its work.  Measured: 2D L=32/64/80/96,
+//     R=8: 2.91/3.09/3.87/3.91; L=64, R=32: 4.85; complex 3D L=12/16, R=16:
+//     4.51/7.27; FP32 2D L=64/96, R=16: 3.14/3.30; complex 3D L=16, R=32: 3.25.
+double work_factor(bool cplx, bool fp32) {
+  return (cplx ? (fp32 ? 1.2 : 3.9) : 1.0) * (fp32 ? 0.8 : 1.0);
+}
+
+double colres_us(int64_t elems, double per_sm, bool cplx, bool fp32, bool bulk) {
+  return 0.64 + (bulk ? 0.0040 : 0.0105) * (double)elems * per_sm * work_factor(cplx, fp32);
+}
+
+double chain_us(int64_t n, int R, bool cplx, bool fp32) {
+  return 2.9 + 1.49e-5 * (double)n * R * (cplx ? (fp32 ? 1.2 : 3.9) : 1.0) * (fp32 ? 0.15 : 1.0);
+}
+
 size_t smem_bytes(bool fp32, bool cplx, int64_t P, int cpc, int block) {
   return colres_head_bytes(2 * (size_t)P * cpc * elem_size(fp32, cplx)) +
-         (size_t)2 * (block / 32) * 2 * cpc * 8;
+         (size_t)3 * (block / 32) * 2 * cpc * 8 + COLRES_RING_BYTES +
+         (size_t)2 * bulk_batch(cpc, block) * block * 2 * 8;
 }
 
 int max_clusters(bool fp32, bool cplx, int dims, int C, int block, size_t smem) {
@@ -420,8 +553,14 @@ bool colres_plan(int64_t n, int dims, bool cplx, bool fp32, int R, ColresPlan* o
       forceCpc = k_;
     }
   }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
   ColresPlan best{};
-  int64_t best_cost = INT64_MAX;
+  double best_cost = 1e300;
   for (int C : {1, 2, 4, 8, 16}) {
     if (forceC && C != forceC) continue;
     const int64_t P = (n + C - 1) / C;
@@ -437,7 +576,8 @@ bool colres_plan(int64_t n, int dims, bool cplx, bool fp32, int R, ColresPlan* o
       if (fit < 1) continue;
       // every cluster resident at once: the solve is one wave; forced shapes may take more
       if (groups > fit && !forceC) continue;
-      const int64_t cost = elems;
+      const double per_sm = std::max(1.0, (double)groups * C / sms);
+      const double cost = colres_us(elems, per_sm, cplx, fp32, bulk_batch(cpc, block) > 0);
       if (cost < best_cost) {  // ties keep the smaller cluster (cheaper barrier)
         best_cost = cost;
         best.C = C;
@@ -450,6 +590,7 @@ bool colres_plan(int64_t n, int dims, bool cplx, bool fp32, int R, ColresPlan* o
     }
   }
   if (best.C == 0) return false;
+  if (!forceC && best_cost >= chain_us(n, R, cplx, fp32)) return false;
   *out = best;
   return true;
 }
@@ -474,7 +615,11 @@ cudaError_t launch_colres(bool fp32, bool cplx, int dims, const ColresPlan& pl,
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  void* args[1] = {const_cast<ColresArgs*>(&a)};
+  ColresArgs ca = a;
+  ca.kr = ring_products(pl.cpc);
+  bulk_shape(pl.cpc, pl.block, &ca.bulk_k, &ca.bulk_tps);
+  if (getenv("KPM_COLRES_TREE")) ca.bulk_k = 0;
+  void* args[1] = {&ca};
   const cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return e;

@@ -10,9 +10,15 @@ namespace kpm {
 // Largest (row, column) element count per CTA: one element per thread of a
 // CTA of at most 1024 threads.
 constexpr int64_t COLRES_MAX_ELEMS = 1024;
-// Dynamic shared memory a CTA may take (the two vector blocks and the warp
-// partials; at most 2 x 1024 x 16 + 2 x 32 x 2 x 32 x 8 bytes).
-constexpr size_t COLRES_MAX_SMEM = 96 * 1024;
+// Shared-memory buffer of the bulk dot sums (two batches of per-thread terms).
+constexpr size_t COLRES_BULK_BYTES = 32 * 1024;
+// Shared-memory ring of per-product CTA partials (flushed to the global
+// scratch when full).
+constexpr size_t COLRES_RING_BYTES = 16 * 1024;
+// Dynamic shared memory a CTA may take (the two vector blocks, the warp
+// partials, the ring and the bulk buffer: at most
+// 2 x 1024 x 16 + 3 x 32 x 2 x 32 x 8 + 16 K + 32 K bytes).
+constexpr size_t COLRES_MAX_SMEM = 128 * 1024;
 
 struct ColresArgs {
   void* vg[2];               // the N x Rp vector blocks in global memory (library layout)
@@ -31,6 +37,9 @@ struct ColresArgs {
   int steps;                 // products per realisation (row stride of sums)
   int gen;                   // n0 == 0: 1 draws v_0 in the kernel, 0 loads it from vg[0];
                              // n0 > 0 loads v_{n0} from vg[n0 & 1], v_{n0-1} from the other
+  int kr;                    // products in the shared-memory ring of CTA partials
+  int bulk_k;                // > 0: products per batch of the bulk dot sums; 0: shuffle tree
+  int bulk_tps;              // lanes per sum of the bulk dot sums
 };
 
 // Bytes of the two vector blocks, rounded up to 16 (the warp partials follow).
@@ -39,8 +48,9 @@ __host__ __device__ inline size_t colres_head_bytes(size_t vec_bytes) {
 }
 
 // The plan for an N-row stencil operator of `dims` dimensions and R columns:
-// false if no cluster shape holds every column group in one wave with at most
-// COLRES_MAX_ELEMS elements per CTA.  KPM_COLRES="0" turns the form off;
+// the cluster shape (every column group resident at once, at most
+// COLRES_MAX_ELEMS elements per CTA) of least estimated time per product, or
+// false if none is estimated faster than the chain of step launches.  KPM_COLRES="0" turns the form off;
 // KPM_COLRES="C,cpc" forces a shape (which may then take several waves).
 bool colres_plan(int64_t n, int dims, bool cplx, bool fp32, int R, ColresPlan* out);
 // Doubles of the partial scratch for a launch of nprod products.

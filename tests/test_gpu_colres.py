@@ -186,10 +186,23 @@ def test_device_start_block_local_moments(K):
     assert np.abs(got - O.ldos_exact(H, a, b, sites, 80)).max() <= TOL["fp64"]
 
 
-def test_large_lattices_keep_the_step_chain(K):
-    # 2D L=128, R=32: more elements per CTA than one per thread at any cluster
-    # shape that holds every column group at once
+@pytest.mark.parametrize("case,form", [
+    # 2D L=64 real FP64, R=8: 256 elements per CTA with the bulk dot sums
+    # (measured 1.84 us per product against 2.91-3.09 for the step chain)
+    (("square", 64, False, 8, "fp64"), FORM),
+    # complex FP64 3D L=16, R=16 (measured 7.81 against 7.27)
+    (("cube", 16, True, 16, "fp64"), "fused step"),
+    # FP32 2D L=96, R=16: 576 elements per CTA, shuffle-tree sums (10.3 against 3.3)
+    (("square", 96, False, 16, "fp32"), "fused step"),
+    # FP32 2D L=128, R=32: more elements per CTA than one per thread at one wave
+    (("square", 128, False, 32, "fp32"), "fused step")])
+def test_planner_takes_the_faster_form(K, case, form):
+    kind, L, cplx, R, prec = case
+    if kind == "square":
+        kw = dict(dims=2, L=(L, L), onsite=I.onsite_disorder(1, L * L, 1.0))
+    else:
+        kw = dict(dims=3, L=(L, L, L), hop=I.spin_hoppings((L, L, L), *I.spins(2, L ** 3)))
     with colres_env(None):
-        with K.kpm_create_stencil(2, (128, 128), onsite=I.onsite_disorder(1, 128 * 128, 1.0)) as h:
-            K.kpm_moments(h, 8, 32, 6.0, 0.0, seed=1, precision="fp32")
-            assert K.kpm_testing_last_step_form(h) == "fused step"
+        with K.kpm_create_stencil(complex_=cplx, **kw) as h:
+            K.kpm_moments(h, 8, R, 12.0, 0.0, seed=1, precision=prec)
+            assert K.kpm_testing_last_step_form(h) == form
