@@ -16,15 +16,23 @@
 // one cluster barrier (release/acquire) per product is the only
 // synchronisation, and the clusters never wait on one another.
 //
-// Moments: every thread adds |x|^2 and Re(conj(y) x) of its element in FP64,
-// lanes of one column are combined by an XOR butterfly between the two halves
-// of the product's cluster barrier (arrive after v_{n+1} is written, wait
-// after the butterfly), the warp results go to one of three shared-memory
-// slots and are summed in warp order one product later, as the CTA's partial
-// in global scratch; after the last product the partials
-// are summed in rank order into the per-step sums that the finalisation
-// kernels read.  The order of every sum is fixed by (C, cpc, block), so a
-// repeated call, a replayed graph and a continued solve give the same bits.
+// Moments: every thread adds |x|^2 and Re(conj(y) x) of its element in FP64.
+// The cluster barrier of a product is split: the arrive follows the write of
+// v_{n+1}, the wait comes after the thread has handed its dot terms on, so the
+// summing overlaps the barrier.  Two ways to sum them:
+//  - bulk (CTAs whose batch buffer fits COLRES_BULK_BYTES): the terms are
+//    parked in shared memory, and every K products a few lanes per
+//    (product, dot, column) add the batch up in thread order, about two FP64
+//    adds per thread and product;
+//  - tree (larger CTAs): an XOR butterfly over the lanes of a column, the
+//    warp results summed in warp order one product later, kept in a
+//    shared-memory ring.
+// Either way the CTA partials go to global scratch (never once per product:
+// a global store would make the next barrier's release wait for L2), and
+// after the last product they are summed in rank order into the per-step
+// sums that the finalisation kernels read.  The order of every sum is fixed
+// by (C, cpc, block), so a repeated call, a replayed graph and a continued
+// solve give the same bits.
 //
 // The operator arithmetic is that of the fused stencil step (diagonal term,
 // then the forward and backward bond of each dimension, FMAs in that order,

@@ -50,8 +50,9 @@ __host__ __device__ inline size_t colres_head_bytes(size_t vec_bytes) {
 // The plan for an N-row stencil operator of `dims` dimensions and R columns:
 // the cluster shape (every column group resident at once, at most
 // COLRES_MAX_ELEMS elements per CTA) of least estimated time per product, or
-// false if none is estimated faster than the chain of step launches.  KPM_COLRES="0" turns the form off;
-// KPM_COLRES="C,cpc" forces a shape (which may then take several waves).
+// false if none is estimated faster than the chain of step launches.
+// KPM_COLRES="0" turns the form off; KPM_COLRES="C,cpc" forces a shape (which
+// may then take several waves); KPM_COLRES_TREE set forces the shuffle tree.
 bool colres_plan(int64_t n, int dims, bool cplx, bool fp32, int R, ColresPlan* out);
 // Doubles of the partial scratch for a launch of nprod products.
 size_t colres_partial_doubles(const ColresPlan& pl, int nprod);
