@@ -175,12 +175,14 @@ typedef struct {
  * the S*R vectors, and optionally the per-vector moments
  * mu_per_vec[(s*R + r)*M + n] (NULL to skip).  One fused CUDA kernel per
  * matrix product (v_{n+1} = 2 H~ v_n - v_{n-1} plus the two moment dots),
- * replayed from a captured CUDA graph.  A stencil operator small enough that
- * one cluster of at most 16 CTAs holds one column's two vectors in shared
- * memory with one element per thread (and every column group fits the GPU at
- * once) instead runs all M/2 products of a realisation in one launch of
- * independent clusters, one per group of columns (the column-resident solve;
- * KPM_COLRES=0 in the environment keeps the chain).  Returns KPM_EDIVERGE (after writing
+ * replayed from a captured CUDA graph.  A stencil operator, or a CSR operator
+ * with a padded-ELL copy (rows of at most 8 entries), small enough that one
+ * cluster of at most 16 CTAs holds one column's two vectors in shared memory
+ * with one element per thread (and every column group fits the GPU at once)
+ * instead runs all M/2 products of a realisation in one launch of
+ * independent clusters, one per group of columns, when the planner's
+ * estimate says that is faster (the column-resident solve; KPM_COLRES=0 in
+ * the environment keeps the chain).  Returns KPM_EDIVERGE (after writing
  * the outputs) when host outputs show |mu_n^r| > 1 + 1e-6 or a non-finite
  * value, and KPM_EINVAL when R exceeds one block of vectors (more than 1024
  * chunks of 16 bytes (FP64) or 32 bytes (FP32) per row, after rounding the
@@ -598,8 +600,8 @@ kpm_status kpm_testing_stall_step_pipeline(int on);
  * 0 the fused step (stencil, CSR or padded ELL), 1 the TMA-fed padded-ELL
  * step, 2 the dense product on the FP64 pipe, 3 the dense product on the
  * tensor cores, 4 the TMA-fed stencil step, 5 the column-resident solve
- * (all products of a realisation of a small stencil operator in one cluster
- * launch).  KPM_ENOTREADY before the first kpm_moments call. */
+ * (all products of a realisation of a small stencil or padded-ELL operator in
+ * one cluster launch).  KPM_ENOTREADY before the first kpm_moments call. */
 kpm_status kpm_testing_last_step_form(kpm_handle h, int* form);
 
 #ifdef __cplusplus

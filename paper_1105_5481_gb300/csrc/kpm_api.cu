@@ -967,6 +967,8 @@ ColresArgs colres_args(const kpm_handle_s* h, int R, int n0, int n1, int steps, 
   c.sc = w.proto.sc;
   c.hs = w.proto.hs;
   c.ds = w.proto.ds;
+  c.ecol = w.proto.ell_w > 0 ? w.proto.col : nullptr;
+  c.evals = w.proto.ell_w > 0 ? w.proto.vals : nullptr;
   c.geom = w.proto.geom;
   c.prm = h->d_prm;
   c.sums = w.sums;
@@ -1142,12 +1144,13 @@ kpm_status moments_impl(kpm_handle h, const kpm_params* p, double* mu, double* m
     int block, grid;
     plan_grid(h, fp32, proto, &block, &grid);
     w.proto = proto;
-    // small stencil operators: the column-resident solve replaces the chain
-    // of step launches (unless the TMA-fed stencil step was asked for)
+    // small stencil and padded-ELL operators: the column-resident solve
+    // replaces the chain of step launches (unless a TMA-fed step was planned)
     w.cr = ColresPlan{};
     w.cr_R = R;
-    if (h->stencil && !h->dense && proto.tma_stages == 0 &&
-        colres_plan(h->n, h->geom.dims, h->cplx, fp32, R, &w.cr)) {
+    if (!h->dense && (h->stencil || (h->ell_w > 0 && h->nnz > 0)) && proto.tma_stages == 0 &&
+        colres_plan(h->n, h->stencil ? h->geom.dims : 0, h->stencil ? 0 : h->ell_w, h->cplx, fp32,
+                    R, &w.cr)) {
       kpm_status sa = colres_scratch(h, steps);
       if (sa != KPM_OK) {
         w.cr = ColresPlan{};

@@ -1,5 +1,6 @@
-// Column-resident solve: a whole realisation of a small stencil operator in
-// one launch, one thread-block cluster per group of vector columns.
+// Column-resident solve: a whole realisation of a small stencil or padded-ELL
+// (CSR rows of at most 8 entries) operator in one launch, one thread-block
+// cluster per group of vector columns.
 //
 // The columns of the random block are independent recursions (Eq. (rn) acts
 // on each |r> separately; only the moment sums of Eq. (munr) mix them), so a
@@ -10,8 +11,9 @@
 // P = ceil(N / C), one (row, column) element per thread.  A neighbour row
 // owned by another CTA of the cluster is read through distributed shared
 // memory (`ld.shared::cluster` at the address `mapa` gives for that CTA); the
-// thread's neighbour addresses, hoppings and on-site term are computed once
-// and kept in registers.  Each product writes v_{n+1} over the thread's own
+// thread's neighbour addresses (and, for a stencil, its hoppings and on-site
+// term) are computed once and kept in registers; an ELL row's values are read
+// through L1 at each product.  Each product writes v_{n+1} over the thread's own
 // element of v_{n-1}; no element is written while another CTA may read it, so
 // one cluster barrier (release/acquire) per product is the only
 // synchronisation, and the clusters never wait on one another.
@@ -34,10 +36,10 @@
 // by (C, cpc, block), so a repeated call, a replayed graph and a continued
 // solve give the same bits.
 //
-// The operator arithmetic is that of the fused stencil step (diagonal term,
-// then the forward and backward bond of each dimension, FMAs in that order,
-// Sec. II-A-2 / Eq. (rn)); the dots are accumulated in FP64 on both the FP64
-// and the FP32-vector path.
+// The operator arithmetic is that of the fused step (diagonal term, then the
+// forward and backward bond of each stencil dimension, or the ELL entries in
+// order; FMAs in that order, Sec. II-A-2 / Eq. (rn)); the dots are
+// accumulated in FP64 on both the FP64 and the FP32-vector path.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -162,9 +164,12 @@ __device__ __forceinline__ void cluster_wait_acquire() {
 
 }  // namespace
 
-template <typename T, bool CPLX, int DIMS>
+// W = 0: the stencil operator of DIMS dimensions; W > 0: a padded-ELL
+// operator of W entries per row (DIMS unused).
+template <typename T, bool CPLX, int DIMS, int W>
 __global__ void __launch_bounds__(1024, 1) colres_kernel(const ColresArgs p) {
   using E = Elem<T, CPLX>;
+  constexpr int NB = W > 0 ? W : 2 * DIMS;  // neighbour slots of a row
   cg::cluster_group cl = cg::this_cluster();
   const int q = (int)cl.block_rank();
   const int C = (int)cl.num_blocks();
@@ -185,49 +190,65 @@ __global__ void __launch_bounds__(1024, 1) colres_kernel(const ColresArgs p) {
   double* wp = reinterpret_cast<double*>(sm + colres_head_bytes(2 * (size_t)buf_bytes));  // [3][nw][2][cpc]
   const int nprod = p.n1 - p.n0;
 
-  // the thread's operator row: neighbour addresses, bond coefficients, diagonal
-  uint32_t af[DIMS], ab[DIMS];
-  T fr[DIMS], fi[DIMS], br[DIMS], bi[DIMS];
+  // The thread's operator row: the shared::cluster addresses of its neighbour
+  // elements (slot 2d the forward and 2d+1 the backward bond of dimension d
+  // of the stencil, or the W entries of the ELL row), the stencil's bond
+  // coefficients and the diagonal.  ELL values are read at each product (L1).
+  uint32_t an[NB];
+  T cr[W > 0 ? 1 : NB], ci[W > 0 ? 1 : NB];
   T hu_r, hu_i, du;
   scalars<T>(p.sc, hu_r, hu_i, du);
   T dg = du;
+  auto addr_of = [&](int64_t j) {
+    const int qj = (int)(j / p.P);
+    return cluster_addr(buf0 + ((j - (int64_t)qj * p.P) * cpc + c), (uint32_t)qj);
+  };
   if (valid) {
-    if (p.ds) dg = reinterpret_cast<const T*>(p.ds)[i];
-    int64_t rem = i;
+    if constexpr (W > 0) {
 #pragma unroll
-    for (int d = 0; d < DIMS; ++d) {
-      const int L = p.geom.L[d], s = p.geom.stride[d];
-      const int x = (int)(rem % L);
-      rem /= L;
-      const bool per = p.geom.periodic[d] != 0;
-      const bool hf = (x + 1 < L) || per, hb = (x > 0) || per;
-      const int64_t jf = (x + 1 < L) ? i + s : (per ? i - (int64_t)(L - 1) * s : i);
-      const int64_t jb = (x > 0) ? i - s : (per ? i + (int64_t)(L - 1) * s : i);
-      if (p.hs) {
-        if constexpr (CPLX) {
-          const Cx<T>* hs = reinterpret_cast<const Cx<T>*>(p.hs);
-          const Cx<T> f = hs[i * DIMS + d], bk = hs[jb * DIMS + d];
-          fr[d] = f.re;
-          fi[d] = f.im;
-          br[d] = bk.re;
-          bi[d] = -bk.im;
+      for (int k = 0; k < W; ++k) an[k] = addr_of(p.ecol[i * W + k]);
+    } else {
+      if (p.ds) dg = reinterpret_cast<const T*>(p.ds)[i];
+      int64_t rem = i;
+#pragma unroll
+      for (int d = 0; d < DIMS; ++d) {
+        const int L = p.geom.L[d], s = p.geom.stride[d];
+        const int x = (int)(rem % L);
+        rem /= L;
+        const bool per = p.geom.periodic[d] != 0;
+        const bool hf = (x + 1 < L) || per, hb = (x > 0) || per;
+        const int64_t jf = (x + 1 < L) ? i + s : (per ? i - (int64_t)(L - 1) * s : i);
+        const int64_t jb = (x > 0) ? i - s : (per ? i + (int64_t)(L - 1) * s : i);
+        T fr, fi, br, bi;
+        if (p.hs) {
+          if constexpr (CPLX) {
+            const Cx<T>* hs = reinterpret_cast<const Cx<T>*>(p.hs);
+            const Cx<T> f = hs[i * DIMS + d], bk = hs[jb * DIMS + d];
+            fr = f.re;
+            fi = f.im;
+            br = bk.re;
+            bi = -bk.im;
+          } else {
+            const T* hs = reinterpret_cast<const T*>(p.hs);
+            fr = hs[i * DIMS + d];
+            br = hs[jb * DIMS + d];
+            fi = bi = T(0);
+          }
         } else {
-          const T* hs = reinterpret_cast<const T*>(p.hs);
-          fr[d] = hs[i * DIMS + d];
-          br[d] = hs[jb * DIMS + d];
-          fi[d] = bi[d] = T(0);
+          fr = hu_r;
+          fi = hu_i;
+          br = hu_r;
+          bi = -hu_i;
         }
-      } else {
-        fr[d] = hu_r;
-        fi[d] = hu_i;
-        br[d] = hu_r;
-        bi[d] = -hu_i;
+        if (!hf) fr = fi = T(0);
+        if (!hb) br = bi = T(0);
+        cr[2 * d] = fr;
+        ci[2 * d] = fi;
+        cr[2 * d + 1] = br;
+        ci[2 * d + 1] = bi;
+        an[2 * d] = addr_of(jf);
+        an[2 * d + 1] = addr_of(jb);
       }
-      if (!hf) fr[d] = fi[d] = T(0);
-      if (!hb) br[d] = bi[d] = T(0);
-      const int qf = (int)(jf / p.P), qb = (int)(jb / p.P);
-      af[d] = cluster_addr(buf0 + ((jf - (int64_t)qf * p.P) * cpc + c), (uint32_t)qf);
-      ab[d] = cluster_addr(buf0 + ((jb - (int64_t)qb * p.P) * cpc + c), (uint32_t)qb);
     }
   }
 
@@ -326,16 +347,26 @@ __global__ void __launch_bounds__(1024, 1) colres_kernel(const ColresArgs p) {
       }
       acc.re = fma(dg, x.re, acc.re);
       if (CPLX) acc.im = fma(dg, x.im, acc.im);
-      Cx<T> xf[DIMS], xb[DIMS];
+      Cx<T> xn[NB];
 #pragma unroll
-      for (int d = 0; d < DIMS; ++d) {
-        xf[d] = ld_cluster<T, CPLX>(af[d] + off);
-        xb[d] = ld_cluster<T, CPLX>(ab[d] + off);
-      }
+      for (int k = 0; k < NB; ++k) xn[k] = ld_cluster<T, CPLX>(an[k] + off);
+      if constexpr (W > 0) {
+        // the ELL row's scaled values, in entry order (as the fused ELL step)
 #pragma unroll
-      for (int d = 0; d < DIMS; ++d) {
-        cmac<T, CPLX>(acc, fr[d], fi[d], xf[d]);
-        cmac<T, CPLX>(acc, br[d], bi[d], xb[d]);
+        for (int k = 0; k < W; ++k) {
+          T vr, vi = T(0);
+          if constexpr (CPLX) {
+            const Cx<T> v = reinterpret_cast<const Cx<T>*>(p.evals)[i * W + k];
+            vr = v.re;
+            vi = v.im;
+          } else {
+            vr = __ldg(reinterpret_cast<const T*>(p.evals) + i * W + k);
+          }
+          cmac<T, CPLX>(acc, vr, vi, xn[k]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NB; ++k) cmac<T, CPLX>(acc, cr[k], ci[k], xn[k]);
       }
       if (n == 0) {
         acc.re *= T(0.5);
@@ -423,29 +454,37 @@ __global__ void __launch_bounds__(1024, 1) colres_kernel(const ColresArgs p) {
 
 namespace {
 
-template <typename T, bool CPLX, int DIMS>
+template <typename T, bool CPLX, int DIMS, int W>
 const void* colres_fn() {
-  return reinterpret_cast<const void*>(colres_kernel<T, CPLX, DIMS>);
+  return reinterpret_cast<const void*>(colres_kernel<T, CPLX, DIMS, W>);
 }
 
-const void* pick(bool fp32, bool cplx, int dims) {
-  if (fp32) {
-    if (cplx) return dims == 1 ? colres_fn<float, true, 1>() : dims == 2 ? colres_fn<float, true, 2>()
-                                                                        : colres_fn<float, true, 3>();
-    return dims == 1 ? colres_fn<float, false, 1>() : dims == 2 ? colres_fn<float, false, 2>()
-                                                                 : colres_fn<float, false, 3>();
+template <typename T, bool CPLX>
+const void* pick_t(int dims, int W) {
+  switch (W) {
+    case 2: return colres_fn<T, CPLX, 0, 2>();
+    case 4: return colres_fn<T, CPLX, 0, 4>();
+    case 6: return colres_fn<T, CPLX, 0, 6>();
+    case 8: return colres_fn<T, CPLX, 0, 8>();
+    default: break;
   }
-  if (cplx) return dims == 1 ? colres_fn<double, true, 1>() : dims == 2 ? colres_fn<double, true, 2>()
-                                                                       : colres_fn<double, true, 3>();
-  return dims == 1 ? colres_fn<double, false, 1>() : dims == 2 ? colres_fn<double, false, 2>()
-                                                                : colres_fn<double, false, 3>();
+  return dims == 1 ? colres_fn<T, CPLX, 1, 0>() : dims == 2 ? colres_fn<T, CPLX, 2, 0>()
+                                                              : colres_fn<T, CPLX, 3, 0>();
+}
+
+// The kernel of a stencil operator of `dims` dimensions (W = 0) or of a
+// padded-ELL operator of width W (2, 4, 6 or 8).
+const void* pick(bool fp32, bool cplx, int dims, int W) {
+  if (fp32) return cplx ? pick_t<float, true>(dims, W) : pick_t<float, false>(dims, W);
+  return cplx ? pick_t<double, true>(dims, W) : pick_t<double, false>(dims, W);
 }
 
 // Once per kernel and device: 16-CTA clusters (a non-portable size) and
 // dynamic shared memory up to COLRES_MAX_SMEM.
-bool configure(bool fp32, bool cplx, int dims) {
-  static std::atomic<unsigned long long> done[12];
-  const int slot = (fp32 ? 6 : 0) + (cplx ? 3 : 0) + dims - 1;
+bool configure(bool fp32, bool cplx, int dims, int W) {
+  static std::atomic<unsigned long long> done[28];
+  const int slot = W > 0 ? 12 + (fp32 ? 8 : 0) + (cplx ? 4 : 0) + W / 2 - 1
+                         : (fp32 ? 6 : 0) + (cplx ? 3 : 0) + dims - 1;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -453,7 +492,7 @@ bool configure(bool fp32, bool cplx, int dims) {
   }
   const unsigned long long bit = 1ull << (dev & 63);
   if (done[slot].load(std::memory_order_acquire) & bit) return true;
-  const void* fn = pick(fp32, cplx, dims);
+  const void* fn = pick(fp32, cplx, dims, W);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)COLRES_MAX_SMEM) != cudaSuccess) {
@@ -514,8 +553,19 @@ double colres_us(int64_t elems, double per_sm, bool cplx, bool fp32, bool bulk) 
   return 0.64 + (bulk ? 0.0040 : 0.0105) * (double)elems * per_sm * work_factor(cplx, fp32);
 }
 
-double chain_us(int64_t n, int R, bool cplx, bool fp32) {
-  return 2.9 + 1.49e-5 * (double)n * R * (cplx ? (fp32 ? 1.2 : 3.9) : 1.0) * (fp32 ? 0.15 : 1.0);
+// Padded-ELL operators (CSR rows of at most 8 entries).  A row costs more
+// than a stencil row (its W values come from L1 at every product): x1.4 real,
+// x1.1 complex.  Their step chain is slower too: x1.1 (FP64 vectors), x1.65
+// (FP32).  Measured in us per product, column-resident against step chain:
+// real FP64 2D L=32/48/64, R=8: 1.28/1.68/2.55 against 3.17/3.25/3.28;
+// complex FP64 3D L=8/12, R=16: 2.13/3.99 against 3.25/4.29; FP32 2D
+// L=32/64, R=16: 1.06/2.20 against 4.98/5.33.
+double ell_factor(bool cplx) { return cplx ? 1.1 : 1.4; }
+
+double chain_us(int64_t n, int R, bool cplx, bool fp32, bool ell) {
+  const double t =
+      2.9 + 1.49e-5 * (double)n * R * (cplx ? (fp32 ? 1.2 : 3.9) : 1.0) * (fp32 ? 0.15 : 1.0);
+  return ell ? t * (fp32 ? 1.65 : 1.1) : t;
 }
 
 size_t smem_bytes(bool fp32, bool cplx, int64_t P, int cpc, int block) {
@@ -524,9 +574,9 @@ size_t smem_bytes(bool fp32, bool cplx, int64_t P, int cpc, int block) {
          (size_t)2 * bulk_batch(cpc, block) * block * 2 * 8;
 }
 
-int max_clusters(bool fp32, bool cplx, int dims, int C, int block, size_t smem) {
-  const void* fn = pick(fp32, cplx, dims);
-  if (!configure(fp32, cplx, dims)) return 0;
+int max_clusters(bool fp32, bool cplx, int dims, int W, int C, int block, size_t smem) {
+  const void* fn = pick(fp32, cplx, dims, W);
+  if (!configure(fp32, cplx, dims, W)) return 0;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(C);
   cfg.blockDim = dim3(block);
@@ -548,9 +598,10 @@ int max_clusters(bool fp32, bool cplx, int dims, int C, int block, size_t smem) 
 
 }  // namespace
 
-bool colres_plan(int64_t n, int dims, bool cplx, bool fp32, int R, ColresPlan* out) {
+bool colres_plan(int64_t n, int dims, int ell_w, bool cplx, bool fp32, int R, ColresPlan* out) {
   *out = ColresPlan{};
-  if (n < 1 || dims < 1 || dims > 3 || R < 1) return false;
+  if (n < 1 || R < 1) return false;
+  if (ell_w > 0 ? (ell_w > 8 || ell_w % 2 != 0) : (dims < 1 || dims > 3)) return false;
   int forceC = 0, forceCpc = 0;
   if (const char* env = getenv("KPM_COLRES")) {
     int c_ = -1, k_ = 0;
@@ -580,12 +631,13 @@ bool colres_plan(int64_t n, int dims, bool cplx, bool fp32, int R, ColresPlan* o
       const int groups = (R + cpc - 1) / cpc;
       const size_t smem = smem_bytes(fp32, cplx, P, cpc, block);
       if (smem > COLRES_MAX_SMEM) continue;
-      const int fit = max_clusters(fp32, cplx, dims, C, block, smem);
+      const int fit = max_clusters(fp32, cplx, dims, ell_w, C, block, smem);
       if (fit < 1) continue;
       // every cluster resident at once: the solve is one wave; forced shapes may take more
       if (groups > fit && !forceC) continue;
       const double per_sm = std::max(1.0, (double)groups * C / sms);
-      const double cost = colres_us(elems, per_sm, cplx, fp32, bulk_batch(cpc, block) > 0);
+      const double cost = colres_us(elems, per_sm, cplx, fp32, bulk_batch(cpc, block) > 0) *
+                          (ell_w > 0 ? ell_factor(cplx) : 1.0);
       if (cost < best_cost) {  // ties keep the smaller cluster (cheaper barrier)
         best_cost = cost;
         best.C = C;
@@ -594,11 +646,12 @@ bool colres_plan(int64_t n, int dims, bool cplx, bool fp32, int R, ColresPlan* o
         best.block = block;
         best.P = P;
         best.smem = smem;
+        best.ell_w = ell_w;
       }
     }
   }
   if (best.C == 0) return false;
-  if (!forceC && best_cost >= chain_us(n, R, cplx, fp32)) return false;
+  if (!forceC && best_cost >= chain_us(n, R, cplx, fp32, ell_w > 0)) return false;
   *out = best;
   return true;
 }
@@ -609,8 +662,9 @@ size_t colres_partial_doubles(const ColresPlan& pl, int nprod) {
 
 cudaError_t launch_colres(bool fp32, bool cplx, int dims, const ColresPlan& pl,
                           const ColresArgs& a, cudaStream_t st) {
-  const void* fn = pick(fp32, cplx, dims);
-  if (!configure(fp32, cplx, dims) || pl.smem > COLRES_MAX_SMEM) return cudaErrorInvalidConfiguration;
+  const void* fn = pick(fp32, cplx, dims, pl.ell_w);
+  if (!configure(fp32, cplx, dims, pl.ell_w) || pl.smem > COLRES_MAX_SMEM)
+    return cudaErrorInvalidConfiguration;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(pl.groups * pl.C);
   cfg.blockDim = dim3(pl.block);

@@ -26,6 +26,8 @@ struct ColresArgs {
   const void* hs;            // scaled per-bond hoppings [N][dims], or NULL (uniform)
   const void* ds;            // scaled diagonal [N], or NULL (uniform)
   StencilGeom geom;
+  const int32_t* ecol;       // padded ELL [N][W] column indices (W > 0)
+  const void* evals;         // padded ELL [N][W] scaled values (T or complex T)
   const RunParams* prm;      // seed, realisation s, s0, R
   double* sums;              // [S][steps][2][Rp]: the per-step sums over rows
   double* gp;                // scratch: [groups][C][n1 - n0][2][cpc] CTA partials
@@ -47,15 +49,17 @@ __host__ __device__ inline size_t colres_head_bytes(size_t vec_bytes) {
   return (vec_bytes + 15) / 16 * 16;
 }
 
-// The plan for an N-row stencil operator of `dims` dimensions and R columns:
+// The plan for an N-row operator (a stencil of `dims` dimensions, ell_w = 0,
+// or a padded ELL of width ell_w in {2, 4, 6, 8}) and R columns:
 // the cluster shape (every column group resident at once, at most
 // COLRES_MAX_ELEMS elements per CTA) of least estimated time per product, or
 // false if none is estimated faster than the chain of step launches.
 // KPM_COLRES="0" turns the form off; KPM_COLRES="C,cpc" forces a shape (which
 // may then take several waves); KPM_COLRES_TREE set forces the shuffle tree.
-bool colres_plan(int64_t n, int dims, bool cplx, bool fp32, int R, ColresPlan* out);
+bool colres_plan(int64_t n, int dims, int ell_w, bool cplx, bool fp32, int R, ColresPlan* out);
 // Doubles of the partial scratch for a launch of nprod products.
 size_t colres_partial_doubles(const ColresPlan& pl, int nprod);
+// dims is that of the stencil (unused for a padded-ELL plan, pl.ell_w > 0)
 cudaError_t launch_colres(bool fp32, bool cplx, int dims, const ColresPlan& pl,
                           const ColresArgs& a, cudaStream_t st);
 

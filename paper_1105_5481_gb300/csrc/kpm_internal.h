@@ -56,6 +56,7 @@ struct ColresPlan {
   int block = 0;    // threads per CTA
   int64_t P = 0;    // rows per CTA: ceil(N / C)
   size_t smem = 0;  // dynamic shared memory per CTA
+  int ell_w = 0;    // 0: stencil operator; > 0: padded-ELL operator of this width
 };
 
 // Dense products on the bf16 tensor cores by the Ozaki splitting scheme

@@ -6,7 +6,8 @@ form) on the same seeded inputs at the parity tolerances (|d mu| <= 1e-10
 FP64, <= 1e-5 FP32 vectors), against the chain of step launches it replaces,
 at every cluster shape (forced through KPM_COLRES="C,cpc"), with ragged row
 splits, CTAs without rows, column groups with padding columns, several
-realisations, a continued solve and a start block written on the device."""
+realisations, a continued solve and a start block written on the device; and
+the same for CSR operators held as a padded ELL (rows of at most 8 entries)."""
 import contextlib
 import os
 
@@ -184,6 +185,71 @@ def test_device_start_block_local_moments(K):
             got = K.kpm_ldos_moments(h, sites, 80, a, b, precision="fp64")
             assert K.kpm_testing_last_step_form(h) == FORM
     assert np.abs(got - O.ldos_exact(H, a, b, sites, 80)).max() <= TOL["fp64"]
+
+
+def _csr_handle(K, kw, cplx):
+    rp, col, val = K.kpm_stencil_to_csr(complex_=cplx, **kw)
+    return K.kpm_create_csr(rp.size - 1, rp, col, val, complex_=cplx)
+
+
+def test_csr_small_solve_matches_oracle_and_chain(K):
+    # the 2D L=32 FP64 workload as a CSR matrix (5 entries per row: a padded
+    # ELL of width 6)
+    w = I.workload("square_L32_fp64")
+    kw = dict(dims=2, L=w["L"], onsite=w["onsite"])
+    H = _oracle_H(kw)
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    R, M, seed = w["R"], w["M"], w["seed"]
+    mu_o, per_o = O.moments_doubling(H, a, b, I.rademacher_block(seed, H.n, R), M)
+    with colres_env(None):
+        with _csr_handle(K, kw, False) as h:
+            mu, per = K.kpm_moments(h, M, R, a, b, seed=seed, precision="fp64", per_vec=True)
+            assert K.kpm_testing_last_step_form(h) == FORM
+            again = K.kpm_moments(h, M, R, a, b, seed=seed, precision="fp64")
+    with colres_env("0"):
+        with _csr_handle(K, kw, False) as h:
+            chain = K.kpm_moments(h, M, R, a, b, seed=seed, precision="fp64")
+            assert K.kpm_testing_last_step_form(h) == "fused step"
+    assert np.abs(per - per_o).max() <= TOL["fp64"]
+    assert np.abs(mu - mu_o).max() <= TOL["fp64"]
+    assert np.array_equal(again, mu)
+    assert np.abs(chain - mu).max() <= 1e-13
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("C,cpc", [(1, 1), (4, 2), (16, 1), (16, 4), (4, 32)])
+def test_csr_every_cluster_shape_matches_oracle(K, C, cpc, prec):
+    # complex spin hoppings, open edge, dilution, disorder: rows of up to 7
+    # entries in a padded ELL of width 8
+    kw, cplx = _ragged()
+    H = _oracle_H(kw)
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    R, M, seed = 13, 66, 21
+    mu_o, per_o = O.moments_doubling(H, a, b, I.random_block(seed, H.n, R, cplx), M)
+    with colres_env(f"{C},{cpc}"):
+        with _csr_handle(K, kw, cplx) as h:
+            mu, per = K.kpm_moments(h, M, R, a, b, seed=seed, precision=prec, per_vec=True)
+            assert K.kpm_testing_last_step_form(h) == FORM
+    assert np.abs(per - per_o).max() <= TOL[prec]
+    assert np.abs(mu - mu_o).max() <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_csr_continued_solve_equals_one_call(K, prec):
+    kw = dict(dims=1, L=(37,), periodic=(False,), t=0.7)      # padded ELL of width 2
+    H = _oracle_H(kw)
+    a, b = O.rescale(*O.gershgorin(H), eps=0.01)
+    R, chain = 5, (40, 42, 300)
+    with colres_env(None):
+        with _csr_handle(K, kw, False) as h:
+            direct = K.kpm_moments(h, chain[-1], R, a, b, seed=4, precision=prec)
+            assert K.kpm_testing_last_step_form(h) == FORM
+            K.kpm_moments(h, chain[0], R, a, b, seed=4, precision=prec)
+            for m in chain[1:]:
+                mu = K.kpm_moments_extend(h, m)
+    assert np.array_equal(mu, direct)
+    mu_o, _ = O.moments_doubling(H, a, b, I.rademacher_block(4, H.n, R), chain[-1])
+    assert np.abs(mu - mu_o).max() <= TOL[prec]
 
 
 @pytest.mark.parametrize("case,form", [

@@ -98,9 +98,21 @@ def test_tma_step_matches_plain_step_and_oracle(K, name, R):
 
 
 def test_small_lattices_keep_the_plain_step(K):
-    # too few rows to fill the GPU with 256-thread CTAs: the plan takes smaller
-    # CTAs of the plain step instead
+    # too few rows to fill the GPU with 256-thread CTAs: a chain of steps
+    # takes smaller CTAs of the plain step instead of the TMA-fed form (and by
+    # default such a lattice runs as the column-resident solve, no chain at all)
     rp, col, val = K.kpm_stencil_to_csr(dims=2, L=(32, 32))
+    old = os.environ.get("KPM_COLRES")
+    os.environ["KPM_COLRES"] = "0"
+    try:
+        with K.kpm_create_csr(rp.size - 1, rp, col, val) as h:
+            K.kpm_moments(h, 16, 8, 4.1, 0.0, precision="fp32")
+            assert K.kpm_testing_last_step_form(h) == "fused step"
+    finally:
+        if old is None:
+            os.environ.pop("KPM_COLRES", None)
+        else:
+            os.environ["KPM_COLRES"] = old
     with K.kpm_create_csr(rp.size - 1, rp, col, val) as h:
         K.kpm_moments(h, 16, 8, 4.1, 0.0, precision="fp32")
-        assert K.kpm_testing_last_step_form(h) == "fused step"
+        assert K.kpm_testing_last_step_form(h) == "column-resident solve"
