@@ -13,6 +13,7 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "kpm_colres.h"
@@ -605,6 +606,36 @@ cudaError_t prescale_into(const kpm_handle_s* h, bool fp32, const RunParams* prm
   return launch_prescale_csr(fp32, h->cplx, h->nnz, h->d_val, prm, false, hs, sc, st);
 }
 
+// Every col[k] in [0, n): the scan of a large matrix's column indices (22 M
+// on the 3D L = 160 lattice, about 13 ms on one Grace core) split over up to
+// 16 host threads.
+bool columns_in_range(const int32_t* col, int64_t nnz, int64_t n) {
+  auto scan = [col, n](int64_t b, int64_t e) {
+    bool ok = true;
+    for (int64_t k = b; k < e; ++k) ok &= (col[k] >= 0) & (col[k] < n);
+    return ok;
+  };
+  const int64_t per = int64_t(1) << 21;
+  const int nt = (int)std::min<int64_t>(
+      std::max(1u, std::min(16u, std::thread::hardware_concurrency())), (nnz + per - 1) / per);
+  if (nt <= 1) return scan(0, nnz);
+  std::vector<char> ok(nt, 1);
+  std::vector<std::thread> th;
+  const int64_t chunk = (nnz + nt - 1) / nt;
+  int started = 1;
+  try {
+    for (int t = 1; t < nt; ++t, ++started)
+      th.emplace_back([&, t] {
+        ok[t] = scan(t * chunk, std::min(nnz, (t + 1) * chunk)) ? 1 : 0;
+      });
+  } catch (...) {
+    // no more threads: this thread scans what none was started for
+  }
+  ok[0] = scan(0, std::min(nnz, chunk)) ? 1 : 0;
+  if (started < nt && !scan(started * chunk, nnz)) ok[0] = 0;
+  for (auto& x : th) x.join();
+  return std::all_of(ok.begin(), ok.end(), [](char c) { return c != 0; });
+}
 }  // namespace kpm
 
 using namespace kpm;
@@ -723,8 +754,7 @@ kpm_status kpm_create_csr(int64_t n, const int64_t* rowptr, const int32_t* col, 
     if (rowptr[i + 1] < rowptr[i]) return fail(KPM_EINVAL, "rowptr must be non-decreasing");
   const int64_t nnz = rowptr[n];
   if (nnz > 0 && (!col || !val)) return fail(KPM_EINVAL, "col/val NULL with nnz > 0");
-  for (int64_t k = 0; k < nnz; ++k)
-    if (col[k] < 0 || col[k] >= n) return fail(KPM_EINVAL, "column index out of range");
+  if (!columns_in_range(col, nnz, n)) return fail(KPM_EINVAL, "column index out of range");
   auto* h = new kpm_handle_s();
   h->stencil = false;
   h->cplx = field == KPM_COMPLEX;
