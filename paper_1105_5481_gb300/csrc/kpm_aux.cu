@@ -767,6 +767,12 @@ __device__ __forceinline__ double damping(int n, int M, int kernel, double lambd
   return 1.0;
 }
 
+// Block size of the kernels that evaluate an FP64 transcendental per element
+// (damping coefficients, cosine table): one warp per block spreads them over
+// as many SMs as there are warps of work (GB300 issues 2 FP64 FMA per SM per
+// clock; a 256-thread block of cos/sin on one SM took about 12 us for M = 256).
+constexpr int FP64_SPREAD = 32;
+
 __global__ void dos_coef_kernel(const double* __restrict__ mu, int M, int kernel, double lambda,
                                 double* coef) {
   const double q = M_PI / (double)(M + 1);
@@ -783,24 +789,37 @@ __global__ void cos_table_kernel(int K, double* table) {
     table[j] = cospi((double)j / (2.0 * (double)K));
 }
 
-// One warp per node k: lanes stride over n; cos(pi n (2k+1)/(2K)) = table[n(2k+1) mod 4K].
+// T lanes per node k (T a power of two <= 32): lane `sub` adds the terms
+// n = sub, sub + T, ... with cos(pi n (2k+1)/(2K)) = table[n(2k+1) mod 4K]
+// (the index advanced by T (2k+1) mod 4K), then an XOR butterfly over the T
+// lanes.  The node's x_k = cos(pi (2k+1)/(2K)) = table[2k+1] and
+// sin(pi (2k+1)/(2K)) = table[(2k+1+3K) mod 4K] come from the same table, so
+// no FP64 transcendental is evaluated per node (GB300's FP64 pipe makes those
+// the larger part of the kernel otherwise).
 __global__ void dct_kernel(const double* __restrict__ coef, int M, double a, double b, int K,
-                           const double* __restrict__ table, double* E, double* rho) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= K) return;
-  const int64_t step = 2LL * warp + 1, n4 = 4LL * K;
+                           const double* __restrict__ table, double* E, double* rho, int T) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t node = gt / T;
+  const int sub = (int)(gt % T);
+  const bool act = node < K;
+  const int64_t n4 = 4LL * K;
   double acc = 0.0;
-  for (int n = lane; n < M; n += 32) {
-    const int64_t j = ((int64_t)n * step) % n4;
-    acc = fma(coef[n], table[j], acc);
+  if (act) {
+    const int64_t step = 2 * node + 1;
+    const int64_t dj = ((int64_t)T * step) % n4;
+    int64_t j = ((int64_t)sub * step) % n4;
+    for (int n = sub; n < M; n += T) {
+      acc = fma(coef[n], table[j], acc);
+      j += dj;
+      if (j >= n4) j -= n4;
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) {
-    double sx, cx;
-    sincospi(((double)warp + 0.5) / (double)K, &sx, &cx);
-    E[warp] = a * cx + b;
-    rho[warp] = acc / (M_PI * sx) / a;
+  for (int o = 1; o < T; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (act && sub == 0) {
+    const int64_t jc = 2 * node + 1;
+    const double cx = table[jc], sx = table[(jc + 3LL * K) % n4];
+    E[node] = a * cx + b;
+    rho[node] = acc / (M_PI * sx * a);
   }
 }
 
@@ -1161,11 +1180,11 @@ cudaError_t launch_stats(const double* pv, int nvec, int M, double a, double b, 
     if (e != cudaSuccess) return e;
   }
   if (!E && !rmean && !rerr) return cudaSuccess;
-  dos_coef_kernel<<<blocks_for(M, 256), 256, 0, st>>>(nullptr, M, kernel, lambda, g);
+  dos_coef_kernel<<<blocks_for(M, FP64_SPREAD), FP64_SPREAD, 0, st>>>(nullptr, M, kernel, lambda, g);
   counted(cudaSuccess);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  cos_table_kernel<<<blocks_for(4LL * K, 256), 256, 0, st>>>(K, table);
+  cos_table_kernel<<<blocks_for(4LL * K, FP64_SPREAD), FP64_SPREAD, 0, st>>>(K, table);
   counted(cudaSuccess);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1179,11 +1198,11 @@ cudaError_t launch_green(const double* mu, int M, double a, double b, int K, int
                          cudaStream_t st) {
   double* coef = work;
   double* table = work + M;
-  dos_coef_kernel<<<blocks_for(M, 256), 256, 0, st>>>(mu, M, kernel, lambda, coef);
+  dos_coef_kernel<<<blocks_for(M, FP64_SPREAD), FP64_SPREAD, 0, st>>>(mu, M, kernel, lambda, coef);
   counted(cudaSuccess);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  cos_table_kernel<<<blocks_for(4LL * K, 256), 256, 0, st>>>(K, table);
+  cos_table_kernel<<<blocks_for(4LL * K, FP64_SPREAD), FP64_SPREAD, 0, st>>>(K, table);
   counted(cudaSuccess);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1201,15 +1220,18 @@ cudaError_t launch_dos(const double* mu, int M, double a, double b, int K, int k
                        double lambda, double* E, double* rho, double* work, cudaStream_t st) {
   double* coef = work;
   double* table = work + M;
-  dos_coef_kernel<<<blocks_for(M, 256), 256, 0, st>>>(mu, M, kernel, lambda, coef);
+  dos_coef_kernel<<<blocks_for(M, FP64_SPREAD), FP64_SPREAD, 0, st>>>(mu, M, kernel, lambda, coef);
   counted(cudaSuccess);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  cos_table_kernel<<<blocks_for(4LL * K, 256), 256, 0, st>>>(K, table);
+  cos_table_kernel<<<blocks_for(4LL * K, FP64_SPREAD), FP64_SPREAD, 0, st>>>(K, table);
   counted(cudaSuccess);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  dct_kernel<<<blocks_for(32LL * K, 256), 256, 0, st>>>(coef, M, a, b, K, table, E, rho);
+  // lanes per node: enough threads for about 4 warps per SM, at most a warp
+  int T = 1;
+  while (T < 32 && (int64_t)K * T < 19456) T *= 2;
+  dct_kernel<<<blocks_for((int64_t)K * T, 256), 256, 0, st>>>(coef, M, a, b, K, table, E, rho, T);
   return counted(cudaGetLastError());
 }
 
