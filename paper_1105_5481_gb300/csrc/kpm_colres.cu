@@ -508,20 +508,28 @@ size_t elem_size(bool fp32, bool cplx) { return (fp32 ? 4 : 8) * (cplx ? 2 : 1);
 // Products held by the shared-memory ring of CTA partials (at most 16 KB).
 int ring_products(int cpc) { return (int)(COLRES_RING_BYTES / (2 * (size_t)cpc * 8)); }
 
-// Shape of the bulk dot sums: the fewest lanes per sum (tps, a power of two
-// <= 32) whose batch of K = block / (2 cpc tps) products fits
-// COLRES_BULK_BYTES; K = 0 (the per-product shuffle tree) if none does.
+// Shape of the bulk dot sums.  Small CTAs: the fewest lanes per sum (tps, a
+// power of two <= 32) whose batch of K = block / (2 cpc tps) products covers
+// the block exactly within COLRES_BULK_SMALL.  Larger CTAs: 32 lanes per sum
+// and as many products per batch as COLRES_BULK_BYTES holds (the threads
+// past K 2 cpc 32 sit the sums out).  K = 0: the per-product shuffle tree.
 void bulk_shape(int cpc, int block, int* K, int* tps) {
   *K = 0;
   *tps = 1;
   for (int l = 1; l <= 32; l *= 2) {
     if (block % (2 * cpc * l) != 0) break;
     const int k = block / (2 * cpc * l);
-    if ((size_t)2 * k * block * 2 * 8 <= COLRES_BULK_BYTES) {
+    if ((size_t)2 * k * block * 2 * 8 <= COLRES_BULK_SMALL) {
       *K = k;
       *tps = l;
       return;
     }
+  }
+  const int k = (int)std::min<size_t>((size_t)block / (2 * cpc * 32),
+                                      COLRES_BULK_BYTES / ((size_t)2 * block * 2 * 8));
+  if (k >= 1) {
+    *K = k;
+    *tps = 32;
   }
 }
 
@@ -536,10 +544,11 @@ int bulk_batch(int cpc, int block) {
 // real FP64 elements per SM: the elements of a CTA times the CTAs an SM holds,
 // x3.9 for complex FP64 (four FMAs per bond; the FP64 pipe bounds it), x1.2
 // for complex FP32, x0.8 for FP32 vectors (only the dots are FP64).
-//   column-resident: 0.64 + 0.0040 w (bulk dot sums) or 0.64 + 0.0105 w
-//     (shuffle tree).  Measured: real FP64 2D L=32/48/64, R=8, bulk:
-//     0.90/1.28/1.84; tree at L=80/96: 4.93/8.32; complex FP64 3D L=8/12/16,
-//     R=16: 1.94/3.88/7.81; FP32 2D L=32/64, R=16: 0.74/1.81.
+//   column-resident: 0.64 + 0.0040 w + 5e-6 e^2 (bulk dot sums; e the
+//     elements of a CTA: large CTAs crowd their SMs) or 0.64 + 0.0105 w
+//     (shuffle tree).  Measured: real FP64 2D L=32/48/64/80/96, R=8, bulk:
+//     0.90/1.28/1.84/3.01/4.55; tree at L=80/96: 4.93/8.32; complex FP64 3D
+//     L=8/12/16, R=16: 1.94/3.93/7.83; FP32 2D L=32/64, R=16: 0.74/1.81.
 //   step chain: 2.9 + 1.49e-5 N R (x3.9 complex FP64; FP32 vectors x0.15, x1.2
 //     more when complex), the launch
 //     latency of a dependent step plus its work.  Measured: 2D L=32/64/80/96,
@@ -550,7 +559,8 @@ double work_factor(bool cplx, bool fp32) {
 }
 
 double colres_us(int64_t elems, double per_sm, bool cplx, bool fp32, bool bulk) {
-  return 0.64 + (bulk ? 0.0040 : 0.0105) * (double)elems * per_sm * work_factor(cplx, fp32);
+  const double w = (double)elems * per_sm * work_factor(cplx, fp32);
+  return bulk ? 0.64 + 0.0040 * w + 5e-6 * (double)elems * (double)elems : 0.64 + 0.0105 * w;
 }
 
 // Padded-ELL operators (CSR rows of at most 8 entries).  A row costs more

@@ -10,15 +10,17 @@ namespace kpm {
 // Largest (row, column) element count per CTA: one element per thread of a
 // CTA of at most 1024 threads.
 constexpr int64_t COLRES_MAX_ELEMS = 1024;
-// Shared-memory buffer of the bulk dot sums (two batches of per-thread terms).
-constexpr size_t COLRES_BULK_BYTES = 32 * 1024;
+// Shared-memory buffer of the bulk dot sums (two batches of per-thread
+// terms): the exact-cover shape of small CTAs fits the first, larger CTAs
+// take batches of up to the second.
+constexpr size_t COLRES_BULK_SMALL = 32 * 1024;
+constexpr size_t COLRES_BULK_BYTES = 160 * 1024;
 // Shared-memory ring of per-product CTA partials (flushed to the global
 // scratch when full).
 constexpr size_t COLRES_RING_BYTES = 16 * 1024;
 // Dynamic shared memory a CTA may take (the two vector blocks, the warp
-// partials, the ring and the bulk buffer: at most
-// 2 x 1024 x 16 + 3 x 32 x 2 x 32 x 8 + 16 K + 32 K bytes).
-constexpr size_t COLRES_MAX_SMEM = 128 * 1024;
+// partials, the ring and the bulk buffer), within the 227 KB of an SM.
+constexpr size_t COLRES_MAX_SMEM = 220 * 1024;
 
 struct ColresArgs {
   void* vg[2];               // the N x Rp vector blocks in global memory (library layout)

@@ -256,9 +256,12 @@ def test_csr_continued_solve_equals_one_call(K, prec):
     # 2D L=64 real FP64, R=8: 256 elements per CTA with the bulk dot sums
     # (measured 1.84 us per product against 2.91-3.09 for the step chain)
     (("square", 64, False, 8, "fp64"), FORM),
+    # 2D L=80 real FP64, R=8: 400 elements per CTA, bulk sums in 160 KB
+    # batches (measured 3.01 us per product against 3.87 for the step chain)
+    (("square", 80, False, 8, "fp64"), FORM),
     # complex FP64 3D L=16, R=16 (measured 7.81 against 7.27)
     (("cube", 16, True, 16, "fp64"), "fused step"),
-    # FP32 2D L=96, R=16: 576 elements per CTA, shuffle-tree sums (10.3 against 3.3)
+    # FP32 2D L=96, R=16: 576 elements per CTA (4.58 against 3.31)
     (("square", 96, False, 16, "fp32"), "fused step"),
     # FP32 2D L=128, R=32: more elements per CTA than one per thread at one wave
     (("square", 128, False, 32, "fp32"), "fused step")])
