@@ -167,8 +167,11 @@ def test_bounds_match_oracle(K, name, csr):
     assert abs(a - oa) <= 1e-8 * span and abs(b - ob) <= 1e-8 * span
 
 
+# node counts from 5 to 25000: the DCT gives each node 32, 16, 8, 4, 2 or 1
+# lanes (the fewer the more nodes), each case against the oracle's sum
 @pytest.mark.parametrize("kernel", ["jackson", "none"])
-@pytest.mark.parametrize("M,K_", [(256, 1024), (37, 64), (1, 5), (1000, 999)])
+@pytest.mark.parametrize("M,K_", [(256, 1024), (37, 64), (1, 5), (1000, 999), (300, 1500),
+                                  (2048, 4096), (700, 6000), (128, 12000), (64, 25000)])
 def test_dos_matches_oracle(K, kernel, M, K_):
     rng = np.random.default_rng(M)
     mu = rng.uniform(-1, 1, M) * np.exp(-np.arange(M) / 50.0)
