@@ -1234,7 +1234,17 @@ kpm_status moments_impl(kpm_handle h, const kpm_params* p, double* mu, double* m
   prm.M = M;
   prm.flags = 0;
   KPM_CUDA(cudaMemcpyAsync(h->d_prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st));
-  KPM_CUDA(prescale(h, slot, fp32, false, st));
+  // the operator scaled with this call's (a, b): kept from the previous call
+  // on the same stream when that used the same (a, b)
+  if (!(h->scaled_ok[slot] && h->scaled_a[slot] == p->a && h->scaled_b[slot] == p->b &&
+        h->scaled_st[slot] == stream)) {
+    h->scaled_ok[slot] = false;
+    KPM_CUDA(prescale(h, slot, fp32, false, st));
+    h->scaled_ok[slot] = true;
+    h->scaled_a[slot] = p->a;
+    h->scaled_b[slot] = p->b;
+    h->scaled_st[slot] = stream;
+  }
   if (w.dtc) KPM_CUDA(launch_dense_tc_slice_rows(*w.dtc, (const double*)h->d_vals[slot], st));
   if (sb.kind != START_RANDOM) {
     // the start block's parameters (site indices or wave vectors) go to the
@@ -1315,13 +1325,14 @@ kpm_status moments_impl(kpm_handle h, const kpm_params* p, double* mu, double* m
     w.res_seed = (unsigned long long)p->seed;
     w.res_s0 = p->s0;
   }
-  KPM_CUDA(launch_finalize(w.sums, S, steps, R, Rp, h->n, M, w.per_vec, w.mu, h->d_prm, st));
+  // a device output receives the mean directly; a host output is copied
+  const bool mu_dev = mu && is_device_ptr(mu);
+  KPM_CUDA(launch_finalize(w.sums, S, steps, R, Rp, h->n, M, w.per_vec, mu_dev ? mu : w.mu,
+                           h->d_prm, st));
   bool host_out = false;
-  if (mu) {
-    const bool dev = is_device_ptr(mu);
-    host_out |= !dev;
-    KPM_CUDA(cudaMemcpyAsync(mu, w.mu, M * sizeof(double),
-                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (mu && !mu_dev) {
+    host_out = true;
+    KPM_CUDA(cudaMemcpyAsync(mu, w.mu, M * sizeof(double), cudaMemcpyDeviceToHost, st));
   }
   if (mu_per_vec) {
     const bool dev = is_device_ptr(mu_per_vec);

@@ -248,6 +248,11 @@ struct kpm_handle_s {
   void* d_ds[3] = {nullptr, nullptr, nullptr};
   void* d_vals[3] = {nullptr, nullptr, nullptr};
   kpm::ScalarBlock* d_sc = nullptr;  // [3]
+  // the (a, b) and stream that slots 0 and 1 were last scaled with on the
+  // device (kpm_moments skips the rescale while a call repeats them)
+  bool scaled_ok[2] = {false, false};
+  double scaled_a[2] = {0.0, 0.0}, scaled_b[2] = {0.0, 0.0};
+  void* scaled_st[2] = {nullptr, nullptr};
   kpm::RunParams* d_prm = nullptr;
   // moments workspace
   struct Work {
