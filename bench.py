@@ -350,6 +350,18 @@ def profile_run(prec, workload, batch_chunk=2, batch_cluster=4, batch_chunk_byte
                 mu = K.kpm_batch_run(bt)
         print(json.dumps({"profile": prec, "workload": workload, "mu0": float(mu[0])}))
         return 0
+    if workload == "square_L32_fp64_csr":
+        # the small configuration as a CSR matrix (padded ELL of width 6)
+        w = I.workload("square_L32_fp64")
+        rp, col, val = K.kpm_stencil_to_csr(2, w["L"], onsite=w["onsite"])
+        with K.kpm_create_csr(rp.size - 1, rp, col, val) as h:
+            _, _, a, b = K.kpm_bounds(h, 0, PAD_EPS)
+            for i in range(2):
+                mu = K.kpm_moments(h, w["M"], w["R"], a, b, seed=1000 + i, precision=prec)
+            torch.cuda.synchronize()
+        print(json.dumps({"profile": prec, "workload": workload, "mu0": float(mu[0]),
+                          "mu2": float(mu[2])}))
+        return 0
     w = I.workload(workload)
     if workload.startswith("csr_spin_dilute_L"):
         rp, col, val = csr_inputs(K, w)
@@ -1079,6 +1091,8 @@ def single_leg(args):
           "batch_2d_256": batch_result, "serve_poisson": serve_result}.get(args.workload)
     if fn is None and args.workload.startswith("dense_wigner_D"):
         fn = dense_result
+    if fn is None:
+        raise SystemExit(f"--workload {args.workload} runs only with --profile")
     r = fn(args, K)
     base = {"metric": METRIC, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "data": "synthetic", "steps": args.steps, "warmup": args.warmup}
@@ -1124,7 +1138,8 @@ def main():
                          "into shared-memory rings; --batch-chunk sets the tile size)")
     ap.add_argument("--workload", default=HEADLINE,
                     choices=[HEADLINE, "cubic_spin_L64", "batch_2d_256", "serve_poisson",
-                             "square_L32_fp64", "dense_wigner_D4096", "csr_spin_dilute_L100"],
+                             "square_L32_fp64", "dense_wigner_D4096", "csr_spin_dilute_L100",
+                             "square_L32_fp64_csr"],
                     help="csr_spin_dilute_L160 (default: the headline line with the other "
                          "configurations as extra keys) or one configuration alone")
     ap.add_argument("--profile", default=None, choices=["fp32", "fp64", "bounds"],
