@@ -12,8 +12,9 @@
 // owned by another CTA of the cluster is read through distributed shared
 // memory (`ld.shared::cluster` at the address `mapa` gives for that CTA); the
 // thread's neighbour addresses (and, for a stencil, its hoppings and on-site
-// term) are computed once and kept in registers; an ELL row's values are read
-// through L1 at each product.  Each product writes v_{n+1} over the thread's own
+// term) are computed once and kept in registers; the ELL values of a CTA's
+// rows are copied into its shared memory once.  Each product writes v_{n+1}
+// over the thread's own
 // element of v_{n-1}; no element is written while another CTA may read it, so
 // one cluster barrier (release/acquire) per product is the only
 // synchronisation, and the clusters never wait on one another.
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(1024, 1) colres_kernel(const ColresArgs p) {
   // The thread's operator row: the shared::cluster addresses of its neighbour
   // elements (slot 2d the forward and 2d+1 the backward bond of dimension d
   // of the stencil, or the W entries of the ELL row), the stencil's bond
-  // coefficients and the diagonal.  ELL values are read at each product (L1).
+  // coefficients and the diagonal.  ELL values are read from shared memory.
   uint32_t an[NB];
   T cr[W > 0 ? 1 : NB], ci[W > 0 ? 1 : NB];
   T hu_r, hu_i, du;
@@ -281,6 +282,14 @@ __global__ void __launch_bounds__(1024, 1) colres_kernel(const ColresArgs p) {
   // the 2 log2(32 / cpc) of the per-product shuffle tree.
   const int K = p.bulk_k, tps = p.bulk_tps;
   double* bb = ring + (size_t)kr * 2 * cpc;  // [2][K][B][2]
+  // ELL: the scaled values of this CTA's rows, [own][W] (x2 complex), copied
+  // once per solve so that no product reads them from global memory
+  T* evs = reinterpret_cast<T*>(bb + (size_t)2 * K * blockDim.x * 2);
+  if constexpr (W > 0) {
+    constexpr int VC = CPLX ? 2 : 1;
+    const T* src = reinterpret_cast<const T*>(p.evals) + (size_t)r0 * W * VC;
+    for (int x = t; x < own * W * VC; x += blockDim.x) evs[x] = src[x];
+  }
   auto bulk_reduce = [&](int b, int cnt) {
     const int B = (int)blockDim.x;
     const int sidx = t / tps, sub = t % tps;
@@ -356,11 +365,10 @@ __global__ void __launch_bounds__(1024, 1) colres_kernel(const ColresArgs p) {
         for (int k = 0; k < W; ++k) {
           T vr, vi = T(0);
           if constexpr (CPLX) {
-            const Cx<T> v = reinterpret_cast<const Cx<T>*>(p.evals)[i * W + k];
-            vr = v.re;
-            vi = v.im;
+            vr = evs[2 * (li * W + k)];
+            vi = evs[2 * (li * W + k) + 1];
           } else {
-            vr = __ldg(reinterpret_cast<const T*>(p.evals) + i * W + k);
+            vr = evs[li * W + k];
           }
           cmac<T, CPLX>(acc, vr, vi, xn[k]);
         }
@@ -563,14 +571,14 @@ double colres_us(int64_t elems, double per_sm, bool cplx, bool fp32, bool bulk) 
   return bulk ? 0.64 + 0.0040 * w + 5e-6 * (double)elems * (double)elems : 0.64 + 0.0105 * w;
 }
 
-// Padded-ELL operators (CSR rows of at most 8 entries).  A row costs more
-// than a stencil row (its W values come from L1 at every product): x1.4 real,
-// x1.1 complex.  Their step chain is slower too: x1.1 (FP64 vectors), x1.65
-// (FP32).  Measured in us per product, column-resident against step chain:
-// real FP64 2D L=32/48/64, R=8: 1.28/1.68/2.55 against 3.17/3.25/3.28;
-// complex FP64 3D L=8/12, R=16: 2.13/3.99 against 3.25/4.29; FP32 2D
-// L=32/64, R=16: 1.06/2.20 against 4.98/5.33.
-double ell_factor(bool cplx) { return cplx ? 1.1 : 1.4; }
+// Padded-ELL operators (CSR rows of at most 8 entries).  A row costs a
+// little more than a stencil row (W values from shared memory and arbitrary
+// neighbours): x1.15 real, x1.0 complex.  Their step chain is slower: x1.1
+// (FP64 vectors), x1.65 (FP32).  Measured in us per product, column-resident
+// against step chain: real FP64 2D L=32/48/64, R=8: 1.00/1.41/2.40 against
+// 3.15/3.23/3.28; complex FP64 3D L=8/12, R=16: 1.73/3.78 against 3.23/4.27;
+// FP32 2D L=32/64, R=16: 0.77/1.83 against 4.93/5.23.
+double ell_factor(bool cplx) { return cplx ? 1.0 : 1.15; }
 
 double chain_us(int64_t n, int R, bool cplx, bool fp32, bool ell) {
   const double t =
@@ -578,10 +586,11 @@ double chain_us(int64_t n, int R, bool cplx, bool fp32, bool ell) {
   return ell ? t * (fp32 ? 1.65 : 1.1) : t;
 }
 
-size_t smem_bytes(bool fp32, bool cplx, int64_t P, int cpc, int block) {
+size_t smem_bytes(bool fp32, bool cplx, int64_t P, int cpc, int block, int ell_w) {
   return colres_head_bytes(2 * (size_t)P * cpc * elem_size(fp32, cplx)) +
          (size_t)3 * (block / 32) * 2 * cpc * 8 + COLRES_RING_BYTES +
-         (size_t)2 * bulk_batch(cpc, block) * block * 2 * 8;
+         (size_t)2 * bulk_batch(cpc, block) * block * 2 * 8 +
+         (size_t)P * ell_w * elem_size(fp32, cplx);
 }
 
 int max_clusters(bool fp32, bool cplx, int dims, int W, int C, int block, size_t smem) {
@@ -639,7 +648,7 @@ bool colres_plan(int64_t n, int dims, int ell_w, bool cplx, bool fp32, int R, Co
       if (elems > COLRES_MAX_ELEMS) break;
       const int block = (int)std::max<int64_t>(32, (elems + 31) / 32 * 32);
       const int groups = (R + cpc - 1) / cpc;
-      const size_t smem = smem_bytes(fp32, cplx, P, cpc, block);
+      const size_t smem = smem_bytes(fp32, cplx, P, cpc, block, ell_w);
       if (smem > COLRES_MAX_SMEM) continue;
       const int fit = max_clusters(fp32, cplx, dims, ell_w, C, block, smem);
       if (fit < 1) continue;
